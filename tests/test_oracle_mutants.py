@@ -1,0 +1,97 @@
+"""Planted mistakes in the oracle (CPU only): each mutant is a copy of the oracle source
+with one plausible error (a dropped term, a swapped cost, a wrong index, a reversed
+tie-break), compiled to a temporary library. The pins must reject every mutant."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_00830_gb300 import workloads as W
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "fastged_oracle.c")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_traces.json")
+
+MUTANTS = {
+    "drop_edge_substitution": ("if (e1 != e2) cost += c[C_ESUB]; }", "}"),
+    "deleted_neighbour_free": ("if (e1) cost += c[C_EDEL];\n            continue;", "continue;"),
+    "edel_eins_swapped": ("else if (e1) cost += c[C_EDEL];                      /* e1 -> eps */",
+                          "else if (e1) cost += c[C_EINS];"),
+    "deletion_keeps_edges": ("if (ogo_edge(g1, i, k)) cost += c[C_EDEL];   /* its edges go with it */", ";"),
+    "wrong_image_index": ("int e2 = ogo_edge(g2, j, map[k]);", "int e2 = ogo_edge(g2, j, k < g2->n ? k : 0);"),
+    "child_order_reversed": ("if (a->j != b->j) return a->j < b->j ? -1 : 1;",
+                             "if (a->j != b->j) return a->j > b->j ? -1 : 1;"),
+    "parent_order_reversed": ("if (a->parent != b->parent) return a->parent < b->parent ? -1 : 1;",
+                              "if (a->parent != b->parent) return a->parent > b->parent ? -1 : 1;"),
+    "keep_worst": ("if (a->ped != b->ped) return a->ped < b->ped ? -1 : 1;",
+                   "if (a->ped != b->ped) return a->ped > b->ped ? -1 : 1;"),
+    "leaf_edge_insert_both_ends": ("(!used[a] || !used[b])) total += c[C_EINS];",
+                                   "(!used[a] && !used[b])) total += c[C_EINS];"),
+    "leaf_tie_last_slot": ("if (total < best) { best = total; best_s = s; }",
+                           "if (total <= best) { best = total; best_s = s; }"),
+    "keep_one_fewer": ("newL > (size_t)K) newL = (size_t)K;",
+                       "newL >= (size_t)K) newL = K > 1 ? (size_t)K - 1 : 1;"),
+    "vertex_sub_inverted": ("else if (g1->alpha[a] != g2->alpha[map[a]]) cost += c[C_VSUB];",
+                            "else if (g1->alpha[a] == g2->alpha[map[a]]) cost += c[C_VSUB];"),
+    "square_edge_sub_always": ("if (e1 && e2) cost += (e1 != e2) ? c[C_ESUB] : 0;",
+                               "if (e1 && e2) cost += c[C_ESUB];"),
+    "full_cost_ins_del_swapped": ("if (pre[u] < 0) cost += c[C_VINS];", "if (pre[u] < 0) cost += c[C_VDEL];"),
+}
+
+
+def _graph(d):
+    e = np.array(d["edges"], dtype=np.int32).reshape(-1, 2)
+    el = None if d.get("elabel") is None else np.array(d["elabel"], dtype=np.int32)
+    return W.Graph(n=d["n"], vlabel=np.array(d["vlabel"], dtype=np.int32), edges=e, elabel=el)
+
+
+def _pins_pass(lib) -> bool:
+    """A compact run of the pins; False as soon as one disagrees."""
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        g1, g2 = _graph(case["g1"]), _graph(case["g2"])
+        if O.brute_ged(g1, g2, case["cost"], lib=lib)[0] != case["exact"]:
+            return False
+        if O.brute_square(g1, g2, case["cost"], lib=lib) != case["exact"]:
+            return False
+        for exp in case.get("kbest", []):
+            cost, mp, nev = O.kbest(g1, g2, case["cost"], exp["K"], lib=lib)
+            if (cost, list(mp), nev) != (exp["cost"], exp["map"], exp["n_evals"]):
+                return False
+            if "leaf_ped" in exp:
+                ped, lm = O.kbest_leaves(g1, g2, case["cost"], exp["K"], lib=lib)
+                if list(ped) != exp["leaf_ped"] or lm.tolist() != exp["leaf_map"]:
+                    return False
+    for seed in range(12):
+        st = W.Stream(seed, 93)
+        g1 = W.random_small(st, 1, 5, 0.5, 3, 2)
+        g2 = W.random_small(st, 1, 4, 0.5, 3, 2)
+        c = tuple(int(x) for x in st.randint(1, 6, 6))
+        ged = O.brute_ged(g1, g2, c, lib=lib)[0]
+        if ged != O.brute_square(g1, g2, c, lib=lib):
+            return False
+        Kx = max(sum(math.comb(i, j) * math.perm(g2.n, j) for j in range(min(i, g2.n) + 1))
+                 for i in range(g1.n + 1))
+        cost, mp, _ = O.kbest(g1, g2, c, Kx, lib=lib)
+        if cost != ged or O.full_cost(g1, g2, c, mp, lib=lib) != cost:
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes():
+    assert _pins_pass(None)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = O._bind(O.compile_c(str(path), str(tmp_path / "libmutant.so")))
+    assert not _pins_pass(lib), f"pins did not catch mutant {name}"
