@@ -1,0 +1,180 @@
+/*
+ * fastged.h -- C ABI of the GB300 (sm_103a) K-Best graph edit distance library.
+ *
+ * The library computes, for every (g1, g2) pair of a batch, the K-Best upper bound on the
+ * graph edit distance of Dabah & Herten, "Efficient Accelerated Graph Edit Distance
+ * Computation on GPU":
+ *   - GED is the minimum total cost over edit paths transforming g1 into g2 (Sec. 2.2);
+ *   - edit operations are vertex-centric: substitution v -> u, deletion v -> eps,
+ *     insertion eps -> u, with edge operations implied by the vertex map (Sec. 2.3, 2.3.1);
+ *   - the search (Algorithm 1) branches the g1 vertices in index order; each kept node
+ *     spawns one substitution child per g2 vertex still free (R_V2) and one deletion
+ *     child (Sec. 4.1.1); a child's partial edit distance PED is its parent's plus the new
+ *     vertex operation and the edge operations it implies against vertices already mapped
+ *     (Sec. 4.1.2, Algorithm 2); only the best K children survive each level (Sec. 4.2);
+ *     once every g1 vertex is processed the free g2 vertices and their edges are inserted
+ *     (Sec. 4.4) and the cheapest completed leaf is returned with its vertex map.
+ *
+ * Ties are broken deterministically: the kept list of a level is the first K entries of
+ * the order (PED, parent slot, child index j), with j = 0..n2-1 the substitution by u_j
+ * and j = n2 the deletion; kept nodes are stored in that order (slot = rank). The final
+ * argmin takes the lowest slot among equal costs. Every result is bit-exact with the
+ * serial CPU oracle that restates Algorithm 1.
+ *
+ * Graphs are simple, undirected, labelled, without loops (Sec. 2.1). Costs are the six
+ * non-negative integers of the paper's experimental setup (Sec. 5); substitution costs
+ * are charged only when the two labels differ (Sec. 2.4).
+ *
+ * Threading: a handle may be used by one host thread at a time. Distinct handles are
+ * independent. Error messages are kept per calling thread.
+ *
+ * Memory: every pointer argument of fastged_batch / fastged_batch_ex / fastged_plan_* is
+ * a HOST pointer owned by the caller; the library never keeps a caller pointer after a
+ * call returns. Device memory, streams, CUDA graphs and pinned staging buffers belong to
+ * the handle (or plan / server) and are released by the matching destroy / stop call.
+ * Outputs are written only when the call returns FASTGED_OK.
+ */
+#ifndef FASTGED_H
+#define FASTGED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FASTGED_VERSION 10000
+
+/* status codes (0 = success, negative = failure; see fastged_last_error for details) */
+#define FASTGED_OK               0
+#define FASTGED_ERR_INVALID_ARG -1   /* a size, label, index, edge or cost is out of range */
+#define FASTGED_ERR_OOM         -2   /* device or pinned host memory could not be obtained */
+#define FASTGED_ERR_CUDA        -3   /* a CUDA runtime call or kernel failed               */
+#define FASTGED_ERR_TIMEOUT     -4   /* a bounded wait ran out (serving / fault injection)  */
+#define FASTGED_ERR_BUSY        -5   /* serving: admission refused, request queue is full  */
+#define FASTGED_ERR_STOPPED     -6   /* serving: the server is stopped                      */
+
+/* limits of this build */
+#define FASTGED_MAX_N      1024      /* vertices per graph                                  */
+#define FASTGED_MAX_K      65536     /* beam width                                          */
+#define FASTGED_MAX_ELABEL 255       /* edge labels are 0..255                              */
+
+/* Cost model (Sec. 2.4; the six explicit costs of Sec. 5). All entries must be >= 0.
+ * v_sub / e_sub are charged only when the two vertex / edge labels differ. */
+typedef struct {
+    int32_t v_sub, v_del, v_ins;
+    int32_t e_sub, e_del, e_ins;
+} fastged_cost_model;
+
+/* One graph (Sec. 2.1). n vertices 0..n-1 with labels vlabel[n] (any int32; only equality
+ * matters). m undirected edges as edges[2*k], edges[2*k+1] (endpoints in 0..n-1, distinct;
+ * either order; no duplicates). elabel[m] holds the edge labels (0..FASTGED_MAX_ELABEL) or
+ * is NULL for unlabelled edges (every edge then has label 0). */
+typedef struct {
+    int32_t n;
+    const int32_t *vlabel;
+    int32_t m;
+    const int32_t *edges;
+    const int32_t *elabel;
+} fastged_graph;
+
+/* A batch: n_graphs graphs and n_pairs pairs; pairs[2*p] is the source g1 and
+ * pairs[2*p+1] the target g2 of pair p (the paper's direction, Sec. 5). A graph may
+ * appear in many pairs. */
+typedef struct {
+    int32_t n_graphs;
+    const fastged_graph *graphs;
+    int32_t n_pairs;
+    const int32_t *pairs;
+} fastged_pair_list;
+
+#define FASTGED_FORM_BATCHED 0   /* one persistent launch per size class over a work queue */
+#define FASTGED_FORM_PLAIN   1   /* one launch per pair, in pair order, on one stream       */
+
+typedef struct {
+    int32_t form;            /* FASTGED_FORM_BATCHED (default) or FASTGED_FORM_PLAIN          */
+    int32_t variant;         /* 0 (default): complete the K kept leaves;                      */
+                             /* 1: complete every successor of the last level (never worse)   */
+    const int32_t *k_per_pair; /* optional host array [n_pairs] of per-pair K (1..K); NULL =  */
+                             /* the K argument for every pair                                 */
+    int32_t hist_window;     /* 0 = default. Width (2..256) of the PED histogram window of    */
+                             /* the selection step; small values force its exact fallback     */
+                             /* path (a testing knob; results do not depend on it)            */
+    int32_t block_threads;   /* 0 = autotuned; else 128, 256 or 512 threads per team          */
+    int32_t use_cuda_graph;  /* plans only: 1 (default when 0 is not given explicitly via     */
+                             /* FASTGED_NO_GRAPH) replays a captured CUDA graph               */
+} fastged_options;
+
+typedef struct fastged_handle fastged_handle;
+typedef struct fastged_plan fastged_plan;
+typedef struct fastged_server fastged_server;
+
+/* Library version (FASTGED_VERSION). */
+int fastged_version(void);
+
+/* Last error message of the calling thread ("" when none). The handle argument may be
+ * NULL; messages are per thread, not per handle. The string stays valid until the next
+ * fastged call on the same thread. */
+const char *fastged_last_error(const fastged_handle *h);
+
+/* Creates a handle on the current CUDA device with the given cost model (Sec. 2.4).
+ * Returns FASTGED_ERR_INVALID_ARG for a NULL argument or a negative cost,
+ * FASTGED_ERR_CUDA when no device is usable. *out receives the handle on success. */
+int fastged_create(const fastged_cost_model *cost, fastged_handle **out);
+
+/* Releases the handle and everything it owns. NULL is ignored. */
+void fastged_destroy(fastged_handle *h);
+
+/* K-Best GED of every pair (Algorithm 1) with host inputs and outputs.
+ *   K            beam width, 1..FASTGED_MAX_K
+ *   out_cost     [n_pairs] GED upper bound of each pair
+ *   out_mapping  [sum over pairs of n1] concatenated in pair order: for pair p, entry k is
+ *                the g2 vertex that v_k of g1 is substituted by, or -1 when v_k is deleted
+ * The call blocks until results are on the host. */
+int fastged_batch(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                  int32_t *out_cost, int32_t *out_mapping);
+
+/* As fastged_batch, with options (NULL = defaults) and an optional out_nevals[n_pairs]
+ * (may be NULL): the number of successors scored at every level plus leaves completed. */
+int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                     const fastged_options *opt, int32_t *out_cost, int32_t *out_mapping,
+                     int64_t *out_nevals);
+
+/* Device-resident plan: the batch is validated, flattened and copied to the device once;
+ * fastged_plan_run then re-runs the whole device path (bitset packing, the K-Best levels,
+ * completion) from the resident inputs. Outputs stay on the device until fastged_plan_read. */
+int fastged_plan_create(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                        const fastged_options *opt, fastged_plan **out);
+
+/* Enqueues one run of the plan on `stream` (a cudaStream_t; NULL = the plan's own stream)
+ * and returns without waiting. */
+int fastged_plan_run(fastged_plan *p, void *stream);
+
+/* Waits for the plan's last run and copies its results to host memory (any of the three
+ * pointers may be NULL). Checks the device-side error flag first. */
+int fastged_plan_read(fastged_plan *p, int32_t *out_cost, int32_t *out_mapping,
+                      int64_t *out_nevals);
+
+typedef struct {
+    int32_t n_pairs;
+    int32_t n_classes;        /* size classes (one persistent launch each)                 */
+    int32_t launches_per_run; /* kernels launched by one fastged_plan_run                  */
+    int32_t graph_replay;     /* 1 if runs replay a captured CUDA graph                    */
+    int64_t input_bytes;      /* resident input bytes (flattened graphs, tables)           */
+    int64_t device_bytes;     /* all device bytes the plan holds                           */
+    int64_t output_bytes;     /* bytes fastged_plan_read copies back (cost, map, evals)    */
+    int32_t block_threads[8]; /* per class                                                 */
+    int32_t grid[8];          /* per class                                                 */
+    int32_t words[8];         /* per class: 64-bit words per bitset                        */
+    int32_t smem_bytes[8];    /* per class: dynamic shared memory per team                 */
+} fastged_plan_stats;
+
+int fastged_plan_info(const fastged_plan *p, fastged_plan_stats *out);
+
+/* Releases the plan (waits for its last run). NULL is ignored. */
+void fastged_plan_destroy(fastged_plan *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTGED_H */

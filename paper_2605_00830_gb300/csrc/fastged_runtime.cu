@@ -1,0 +1,724 @@
+// fastged_runtime.cu -- host runtime behind the C ABI of include/fastged.h.
+//
+// A call flows as: validate + flatten the caller's graphs into one pinned staging buffer
+// -> one host-to-device copy -> zero the bitset pools -> pack kernel (S0) -> one persistent
+// K-Best launch per size class, each on its own stream, pulling pairs heaviest-first from
+// a device work queue (S1-S5) -> one device-to-host copy of costs, evaluation counts,
+// vertex maps and the error flag.
+//
+// Size classes group pairs by the number of 64-bit words a g2 bitset needs (1, 2, 4, 8, 16)
+// and by the width of a stored vertex-map entry (8 or 16 bits). Each class gets a region
+// plan: the per-team working set is split into regions placed in shared memory in order
+// of access frequency; what does not fit goes to a per-team slice of global scratch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fastged.h"
+#include "fastged_internal.h"
+#include "fastged_runtime.h"
+
+namespace fastged {
+cudaError_t launch_kbest(int W, bool wide_map, const KParams &p, int grid, int block,
+                         size_t smem, cudaStream_t st);
+cudaError_t kbest_occupancy(int W, bool wide_map, int block, size_t smem, int *out);
+cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
+size_t team_shared_static_bytes();
+}  // namespace fastged
+
+using namespace fastged;
+
+// ------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+int fastged::set_error(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+void fastged::clear_error() { g_err.clear(); }
+
+static int cuda_fail(cudaError_t e, const char *what)
+{
+    const int code = (e == cudaErrorMemoryAllocation) ? FASTGED_ERR_OOM : FASTGED_ERR_CUDA;
+    return set_error(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+// ------------------------------------------------------------------------------------
+// buffers
+// ------------------------------------------------------------------------------------
+int DevBuf::ensure(size_t n)
+{
+    if (n <= cap) return 0;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (n == 0) return 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc");
+    }
+    cap = n;
+    return 0;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+int PinBuf::ensure(size_t n)
+{
+    if (n <= cap) return 0;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (n == 0) return 0;
+    cudaError_t e = cudaMallocHost(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    cap = n;
+    return 0;
+}
+
+void PinBuf::release()
+{
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int words_class(int n)
+{
+    const int w = (n + 63) / 64;
+    if (w <= 1) return 1;
+    if (w <= 2) return 2;
+    if (w <= 4) return 4;
+    if (w <= 8) return 8;
+    return 16;
+}
+
+// ------------------------------------------------------------------------------------
+// handle
+// ------------------------------------------------------------------------------------
+extern "C" int fastged_version(void) { return FASTGED_VERSION; }
+
+extern "C" const char *fastged_last_error(const fastged_handle *) { return g_err.c_str(); }
+
+extern "C" int fastged_create(const fastged_cost_model *cost, fastged_handle **out)
+{
+    clear_error();
+    if (!cost || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
+    const int32_t *cv = &cost->v_sub;
+    for (int k = 0; k < 6; ++k)
+        if (cv[k] < 0) return set_error(FASTGED_ERR_INVALID_ARG, "negative cost");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    fastged_handle *h = new fastged_handle();
+    h->cost = *cost;
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    for (int k = 0; k < kMaxClasses && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&h->class_stream[k], cudaStreamNonBlocking);
+    for (int k = 0; k < kMaxClasses + 1 && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        fastged_destroy(h);
+        return cuda_fail(e, "stream/event creation");
+    }
+    *out = h;
+    return FASTGED_OK;
+}
+
+extern "C" void fastged_destroy(fastged_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < kMaxClasses; ++k)
+        if (h->class_stream[k]) {
+            cudaStreamSynchronize(h->class_stream[k]);
+            cudaStreamDestroy(h->class_stream[k]);
+        }
+    for (int k = 0; k < kMaxClasses + 1; ++k)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    h->dev_in.release();
+    h->dev_work.release();
+    h->pin.release();
+    delete h;
+}
+
+// ------------------------------------------------------------------------------------
+// flattening + validation
+// ------------------------------------------------------------------------------------
+static fastged_options default_options()
+{
+    fastged_options o;
+    memset(&o, 0, sizeof(o));
+    o.use_cuda_graph = 1;
+    return o;
+}
+
+static void plan_layout(ClassPlan &cp, int B, int block, size_t budget)
+{
+    Layout &L = cp.lay;
+    const int NW = block / 32;
+    const int W = cp.W;
+    const size_t msz = cp.wide ? 2 : 1;
+    L.kmax = cp.kmax;
+    L.n1max = cp.n1max;
+    L.n2max = cp.n2max;
+    L.n2s = (int)align_up((size_t)std::max(cp.n2max, 1) + 1, 4);
+    L.mrow = (int)align_up((size_t)std::max(cp.n1max, 1) * msz, 16);
+    L.B = B;
+    size_t sz[RG_COUNT];
+    const size_t km = (size_t)cp.kmax;
+    sz[RG_HIST] = (size_t)kHistMax * NW * 4;
+    sz[RG_BBASE] = (size_t)kHistMax * 4;
+    sz[RG_CROW] = (size_t)L.n2s * 4;
+    sz[RG_ALPHA2] = (size_t)L.n2s * 4;
+    sz[RG_A2T] = (size_t)W * L.n2s * 8;
+    sz[RG_L2T] = (size_t)B * W * L.n2s * 8;
+    sz[RG_SBASE] = km * 4;
+    sz[RG_PED0] = km * 4;
+    sz[RG_PED1] = km * 4;
+    sz[RG_SEL] = km * 4;
+    sz[RG_SELPED] = km * 4;
+    sz[RG_IMG0] = km * W * 8;
+    sz[RG_IMG1] = km * W * 8;
+    sz[RG_P] = km * W * 8;
+    sz[RG_PL] = (size_t)B * km * W * 8;
+    sz[RG_CAND] = km * ((size_t)cp.n2max + 1) * 4;
+    sz[RG_MAP0] = km * L.mrow;
+    sz[RG_MAP1] = km * L.mrow;
+    sz[RG_TMP] = km * 4;
+    static const int prio[RG_COUNT] = {RG_HIST, RG_BBASE, RG_CROW, RG_ALPHA2, RG_SBASE,
+                                       RG_PED0, RG_PED1, RG_SEL, RG_SELPED, RG_A2T,
+                                       RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CAND,
+                                       RG_MAP0, RG_MAP1, RG_TMP};
+    size_t s_used = 0, g_used = 0;
+    L.smem_mask = 0;
+    for (int k = 0; k < RG_COUNT; ++k) {
+        const int r = prio[k];
+        const size_t a = align_up(sz[r], 16);
+        if (s_used + a <= budget) {
+            L.off[r] = (int64_t)s_used;
+            L.smem_mask |= 1u << r;
+            s_used += a;
+        } else {
+            L.off[r] = (int64_t)g_used;
+            g_used += a;
+        }
+    }
+    L.smem_bytes = (int64_t)s_used;
+    L.slice_bytes = (int64_t)align_up(g_used, 256);
+}
+
+static size_t layout_total(const ClassPlan &cp, int B, int block)
+{
+    ClassPlan t = cp;
+    plan_layout(t, B, block, (size_t)1 << 40);
+    return (size_t)t.lay.smem_bytes;
+}
+
+// Chooses threads per team and the shared-memory budget of a class.
+static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
+{
+    int block = forced_block;
+    if (block == 0) block = cp.kmax <= 32 ? 128 : 256;
+    const size_t stat = team_shared_static_bytes() + 1024;   // + per-block reservation
+    const size_t per_sm = (size_t)h->smem_per_sm;
+    const size_t max_dyn = (size_t)h->smem_optin - team_shared_static_bytes();
+    const size_t total = layout_total(cp, B, block);
+    size_t budget;
+    if (total + stat <= per_sm / 2 && total <= max_dyn) {
+        budget = total;                                   // all in shared memory
+    } else {
+        budget = std::min(max_dyn, per_sm / 2 - stat);    // keep two teams per SM
+    }
+    plan_layout(cp, B, block, budget);
+    int occ = 0;
+    cudaError_t e = kbest_occupancy(cp.W, cp.wide, block, (size_t)cp.lay.smem_bytes, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ < 1) return set_error(FASTGED_ERR_CUDA, "team does not fit on an SM");
+    cp.block = block;
+    cp.smem = (size_t)cp.lay.smem_bytes;
+    const int64_t want = (int64_t)h->sm_count * occ;
+    cp.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)cp.order.size()));
+    return FASTGED_OK;
+}
+
+int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
+                     const fastged_options &opt, Batch &b)
+{
+    if (!pl) return set_error(FASTGED_ERR_INVALID_ARG, "null pair list");
+    if (K < 1 || K > FASTGED_MAX_K) return set_error(FASTGED_ERR_INVALID_ARG, "K out of range");
+    if (pl->n_graphs < 0 || pl->n_pairs < 0)
+        return set_error(FASTGED_ERR_INVALID_ARG, "negative count");
+    if ((pl->n_graphs > 0 && !pl->graphs) || (pl->n_pairs > 0 && !pl->pairs))
+        return set_error(FASTGED_ERR_INVALID_ARG, "null graphs or pairs");
+    if (opt.variant != 0 && opt.variant != 1)
+        return set_error(FASTGED_ERR_INVALID_ARG, "variant must be 0 or 1");
+    if (opt.variant == 1) return set_error(FASTGED_ERR_INVALID_ARG, "variant 1 not built yet");
+    if (opt.hist_window != 0 && (opt.hist_window < 2 || opt.hist_window > kHistMax))
+        return set_error(FASTGED_ERR_INVALID_ARG, "hist_window out of range");
+    if (opt.block_threads != 0 && opt.block_threads != 128 && opt.block_threads != 256 &&
+        opt.block_threads != 512)
+        return set_error(FASTGED_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+
+    const int ng = pl->n_graphs, np = pl->n_pairs;
+    b.n_graphs = ng;
+    b.n_pairs = np;
+    b.K = K;
+    b.opt = opt;
+    b.has_kpp = opt.k_per_pair != nullptr;
+    b.meta.resize(ng);
+    int64_t nv = 0, ne = 0, adjw = 0;
+    int maxlab = 0;
+    bool labelled = false;
+    for (int g = 0; g < ng; ++g) {
+        const fastged_graph &G = pl->graphs[g];
+        if (G.n < 0 || G.n > FASTGED_MAX_N)
+            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": n out of range");
+        if (G.m < 0 || (int64_t)G.m > (int64_t)G.n * (G.n - 1) / 2)
+            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": m out of range");
+        if ((G.n > 0 && !G.vlabel) || (G.m > 0 && !G.edges))
+            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": null array");
+        GraphMeta &M = b.meta[g];
+        M.n = G.n;
+        M.m = G.m;
+        M.W = std::max(1, (G.n + 63) / 64);
+        M.pad = 0;
+        M.lab_off = nv;
+        M.edge_off = ne;
+        M.adj_off = adjw;
+        nv += G.n;
+        ne += G.m;
+        adjw += (int64_t)G.n * M.W;
+        if (G.elabel && G.m > 0) {
+            labelled = true;
+            for (int k = 0; k < G.m; ++k) {
+                const int l = G.elabel[k];
+                if (l < 0 || l > FASTGED_MAX_ELABEL)
+                    return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": edge label out of range");
+                maxlab = std::max(maxlab, l);
+            }
+        }
+    }
+    int B = 0;
+    while ((1 << B) <= maxlab) ++B;   // planes needed for labels 0..maxlab
+    b.B = B;
+    b.labelled = labelled && B > 0;
+    for (int g = 0; g < ng; ++g) b.meta[g].plane_off = b.meta[g].adj_off * B;
+    b.n_vlab = nv;
+    b.n_edges = ne;
+    b.adj_words = adjw;
+    b.plane_words = adjw * B;
+
+    // pairs: validation, cost bound, classes
+    const fastged_cost_model &c = h->cost;
+    const int32_t *kpp = opt.k_per_pair;
+    b.map_off.resize(np);
+    int64_t mtot = 0;
+    int cls_of[32];
+    for (int k = 0; k < 32; ++k) cls_of[k] = -1;
+    b.classes.clear();
+    std::vector<int> pair_class(np);
+    for (int p = 0; p < np; ++p) {
+        const int a = pl->pairs[2 * p], d = pl->pairs[2 * p + 1];
+        if (a < 0 || a >= ng || d < 0 || d >= ng)
+            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": graph index out of range");
+        const int kp = kpp ? kpp[p] : K;
+        if (kp < 1 || kp > K)
+            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": per-pair K out of range");
+        const GraphMeta &g1 = b.meta[a], &g2 = b.meta[d];
+        const long long bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
+                                (long long)g2.n * c.v_ins +
+                                (long long)g1.m * std::max(c.e_sub, c.e_del) +
+                                (long long)g2.m * c.e_ins;
+        if (bound >= (long long)INT32_MAX)
+            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": costs can overflow int32");
+        b.map_off[p] = mtot;
+        mtot += g1.n;
+        const int W = words_class(g2.n);
+        const bool wide = g2.n >= 255;
+        const int key = (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0);
+        if (cls_of[key] < 0) {
+            cls_of[key] = (int)b.classes.size();
+            ClassPlan cp;
+            cp.W = W;
+            cp.wide = wide || W >= 8;
+            b.classes.push_back(cp);
+        }
+        ClassPlan &cp = b.classes[cls_of[key]];
+        cp.n1max = std::max(cp.n1max, g1.n);
+        cp.n2max = std::max(cp.n2max, g2.n);
+        cp.kmax = std::max(cp.kmax, kp);
+        cp.order.push_back(p);
+        pair_class[p] = cls_of[key];
+    }
+    b.map_total = mtot;
+    // heaviest pairs first inside each class (longest-processing-time order)
+    for (auto &cp : b.classes) {
+        std::vector<std::pair<long long, int>> wk(cp.order.size());
+        for (size_t k = 0; k < cp.order.size(); ++k) {
+            const int p = cp.order[k];
+            const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
+            const long long kp = kpp ? kpp[p] : K;
+            wk[k] = {-(long long)g1.n * std::min<long long>(kp, 1 + (long long)g2.n * g1.n) * (g2.n + 1),
+                     p};
+        }
+        std::sort(wk.begin(), wk.end());
+        for (size_t k = 0; k < wk.size(); ++k) cp.order[k] = wk[k].second;
+        int rc = tune_class(h, cp, B, opt.block_threads);
+        if (rc) return rc;
+    }
+    if ((int)b.classes.size() > kMaxClasses)
+        return set_error(FASTGED_ERR_INVALID_ARG, "too many size classes");
+
+    // staging layout (one pinned buffer, one copy)
+    size_t o = 0;
+    b.off_meta = o;   o = align_up(o + sizeof(GraphMeta) * (size_t)ng, 256);
+    b.off_vlab = o;   o = align_up(o + 4 * (size_t)nv, 256);
+    b.off_edges = o;  o = align_up(o + 8 * (size_t)ne, 256);
+    b.off_elab = o;   o = align_up(o + (b.labelled ? 4 * (size_t)ne : 0), 256);
+    b.off_pairs = o;  o = align_up(o + 8 * (size_t)np, 256);
+    b.off_order = o;  o = align_up(o + 4 * (size_t)np, 256);
+    b.off_mapoff = o; o = align_up(o + 8 * (size_t)np, 256);
+    b.off_kpp = o;    o = align_up(o + (kpp ? 4 * (size_t)np : 0), 256);
+    b.in_bytes = o;
+    int rc = h->pin.ensure(std::max<size_t>(b.in_bytes, 256));
+    if (rc) return rc;
+    uint8_t *S = (uint8_t *)h->pin.p;
+    memcpy(S + b.off_meta, b.meta.data(), sizeof(GraphMeta) * (size_t)ng);
+    int32_t *vl = (int32_t *)(S + b.off_vlab);
+    int32_t *ed = (int32_t *)(S + b.off_edges);
+    int32_t *el = (int32_t *)(S + b.off_elab);
+    for (int g = 0; g < ng; ++g) {
+        const fastged_graph &G = pl->graphs[g];
+        const GraphMeta &M = b.meta[g];
+        if (G.n) memcpy(vl + M.lab_off, G.vlabel, 4 * (size_t)G.n);
+        int32_t *dst = ed + 2 * M.edge_off;
+        for (int k = 0; k < G.m; ++k) {
+            const int u = G.edges[2 * k], v = G.edges[2 * k + 1];
+            if (u < 0 || v < 0 || u >= G.n || v >= G.n || u == v)
+                return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": bad edge endpoint or self-loop");
+            dst[2 * k] = u;
+            dst[2 * k + 1] = v;
+        }
+        if (b.labelled) {
+            if (G.elabel) memcpy(el + M.edge_off, G.elabel, 4 * (size_t)G.m);
+            else memset(el + M.edge_off, 0, 4 * (size_t)G.m);
+        }
+    }
+    memcpy(S + b.off_pairs, pl->pairs, 8 * (size_t)np);
+    {
+        int32_t *ord = (int32_t *)(S + b.off_order);
+        int64_t q = 0;
+        for (auto &cp : b.classes) {
+            cp.order_off = q;
+            memcpy(ord + q, cp.order.data(), 4 * cp.order.size());
+            q += (int64_t)cp.order.size();
+        }
+    }
+    memcpy(S + b.off_mapoff, b.map_off.data(), 8 * (size_t)np);
+    if (kpp) memcpy(S + b.off_kpp, kpp, 4 * (size_t)np);
+
+    // device work region: [status | cost | nevals | map] then pools, queues, scratch
+    size_t w = 0;
+    b.woff_err = w;    w = align_up(w + 16, 256);
+    b.woff_cost = w;   w = align_up(w + 4 * (size_t)np, 256);
+    b.woff_nev = w;    w = align_up(w + 8 * (size_t)np, 256);
+    b.woff_map = w;    w = align_up(w + 4 * (size_t)mtot, 256);
+    b.out_bytes = w;   // one device-to-host copy covers [0, out_bytes)
+    b.woff_queue = w;  w = align_up(w + 4 * ((size_t)np + kMaxClasses), 256);
+    b.woff_pool = w;   w = align_up(w + 8 * (size_t)(b.adj_words + b.plane_words), 256);
+    size_t scratch = 0;
+    for (auto &cp : b.classes) {
+        cp.scratch_off = scratch;
+        scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)cp.grid, 256);
+    }
+    b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
+    b.work_bytes = w;
+    return FASTGED_OK;
+}
+
+// Fills the kernel parameters of class k for a batch whose inputs sit at `in` and whose
+// work region sits at `wk` on the device.
+static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8_t *in,
+                           uint8_t *wk)
+{
+    const ClassPlan &cp = b.classes[k];
+    KParams p;
+    memset(&p, 0, sizeof(p));
+    p.gmeta = (const GraphMeta *)(in + b.off_meta);
+    p.adj = (const uint64_t *)(wk + b.woff_pool);
+    p.planes = (const uint64_t *)(wk + b.woff_pool) + b.adj_words;
+    p.vlab = (const int32_t *)(in + b.off_vlab);
+    p.pairs = (const int32_t *)(in + b.off_pairs);
+    p.order = (const int32_t *)(in + b.off_order) + cp.order_off;
+    p.n_order = (int32_t)cp.order.size();
+    p.kpp = b.has_kpp ? (const int32_t *)(in + b.off_kpp) : nullptr;
+    p.K = b.K;
+    p.hwin = b.opt.hist_window ? b.opt.hist_window : kHistMax;
+    p.variant = b.opt.variant;
+    p.cost.vsub = h->cost.v_sub;
+    p.cost.vdel = h->cost.v_del;
+    p.cost.vins = h->cost.v_ins;
+    p.cost.esub = h->cost.e_sub;
+    p.cost.edel = h->cost.e_del;
+    p.cost.eins = h->cost.e_ins;
+    p.queue_head = (int32_t *)(wk + b.woff_queue) + k;
+    p.err = (int32_t *)(wk + b.woff_err);
+    p.out_cost = (int32_t *)(wk + b.woff_cost);
+    p.out_map = (int32_t *)(wk + b.woff_map);
+    p.map_off = (const int64_t *)(in + b.off_mapoff);
+    p.out_nevals = (int64_t *)(wk + b.woff_nev);
+    p.gscratch = wk + b.woff_scratch + cp.scratch_off;
+    p.lay = cp.lay;
+    return p;
+}
+
+// Enqueues the device path of a batch: zero pools and queues, pack, one launch per class.
+int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk,
+                     cudaStream_t st, int *launches)
+{
+    int nl = 0;
+    CK(cudaMemsetAsync(wk + b.woff_err, 0, 16, st));
+    CK(cudaMemsetAsync(wk + b.woff_queue, 0, b.woff_scratch - b.woff_queue, st));
+    PackParams pp;
+    pp.gmeta = (const GraphMeta *)(in + b.off_meta);
+    pp.n_graphs = b.n_graphs;
+    pp.edges = (const int32_t *)(in + b.off_edges);
+    pp.elabel = b.labelled ? (const int32_t *)(in + b.off_elab) : nullptr;
+    pp.B = b.B;
+    pp.adj = (uint64_t *)(wk + b.woff_pool);
+    pp.planes = (uint64_t *)(wk + b.woff_pool) + b.adj_words;
+    pp.err = (int32_t *)(wk + b.woff_err);
+    if (b.n_graphs > 0) {
+        CK(launch_pack(pp, b.n_graphs, st));
+        ++nl;
+    }
+    const int nc = (int)b.classes.size();
+    if (b.opt.form == FASTGED_FORM_PLAIN) {
+        // one launch per pair, in pair order, single team, on the caller's stream
+        std::vector<int> cls(b.n_pairs), pos(b.n_pairs);
+        for (int k = 0; k < nc; ++k)
+            for (size_t q = 0; q < b.classes[k].order.size(); ++q) {
+                cls[b.classes[k].order[q]] = k;
+                pos[b.classes[k].order[q]] = (int)q;
+            }
+        int32_t *qbase = (int32_t *)(wk + b.woff_queue) + kMaxClasses;
+        for (int pr = 0; pr < b.n_pairs; ++pr) {
+            const int k = cls[pr];
+            const ClassPlan &cp = b.classes[k];
+            KParams p = make_params(h, b, k, in, wk);
+            p.order += pos[pr];
+            p.n_order = 1;
+            p.queue_head = qbase + pr;
+            CK(launch_kbest(cp.W, cp.wide, p, 1, cp.block, cp.smem, st));
+            ++nl;
+        }
+    } else if (nc == 1) {
+        const ClassPlan &cp = b.classes[0];
+        KParams p = make_params(h, b, 0, in, wk);
+        CK(launch_kbest(cp.W, cp.wide, p, cp.grid, cp.block, cp.smem, st));
+        ++nl;
+    } else if (nc > 1) {
+        CK(cudaEventRecord(h->ev[kMaxClasses], st));
+        for (int k = 0; k < nc; ++k) {
+            const ClassPlan &cp = b.classes[k];
+            CK(cudaStreamWaitEvent(h->class_stream[k], h->ev[kMaxClasses], 0));
+            KParams p = make_params(h, b, k, in, wk);
+            CK(launch_kbest(cp.W, cp.wide, p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
+            ++nl;
+            CK(cudaEventRecord(h->ev[k], h->class_stream[k]));
+            CK(cudaStreamWaitEvent(st, h->ev[k], 0));
+        }
+    }
+    if (launches) *launches = nl;
+    return FASTGED_OK;
+}
+
+int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *out_cost,
+                            int32_t *out_mapping, int64_t *out_nevals)
+{
+    const int32_t err = *(const int32_t *)(host_out + b.woff_err);
+    if (err & kErrDuplicateEdge) return set_error(FASTGED_ERR_INVALID_ARG, "duplicate edge in a graph");
+    if (err) return set_error(FASTGED_ERR_CUDA, "device error flag " + std::to_string(err));
+    if (out_cost) memcpy(out_cost, host_out + b.woff_cost, 4 * (size_t)b.n_pairs);
+    if (out_nevals) memcpy(out_nevals, host_out + b.woff_nev, 8 * (size_t)b.n_pairs);
+    if (out_mapping) memcpy(out_mapping, host_out + b.woff_map, 4 * (size_t)b.map_total);
+    return FASTGED_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// one-shot batch
+// ------------------------------------------------------------------------------------
+extern "C" int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                                const fastged_options *opt, int32_t *out_cost,
+                                int32_t *out_mapping, int64_t *out_nevals)
+{
+    clear_error();
+    if (!h) return set_error(FASTGED_ERR_INVALID_ARG, "null handle");
+    const fastged_options o = opt ? *opt : default_options();
+    Batch &b = h->batch;
+    int rc = flatten(h, pairs, K, o, b);
+    if (rc) return rc;
+    if (b.n_pairs == 0) return FASTGED_OK;
+    if ((rc = h->dev_in.ensure(b.in_bytes))) return rc;
+    if ((rc = h->dev_work.ensure(b.work_bytes))) return rc;
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(h->dev_in.p, h->pin.p, b.in_bytes, cudaMemcpyHostToDevice, st));
+    rc = enqueue(h, b, (uint8_t *)h->dev_in.p, (uint8_t *)h->dev_work.p, st, nullptr);
+    if (rc) return rc;
+    // results come back through the (already consumed) staging buffer
+    if ((rc = h->pin.ensure(std::max(b.in_bytes, b.out_bytes)))) return rc;
+    CK(cudaMemcpyAsync(h->pin.p, h->dev_work.p, b.out_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return finish_outputs(b, (const uint8_t *)h->pin.p, out_cost, out_mapping, out_nevals);
+}
+
+extern "C" int fastged_batch(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                             int32_t *out_cost, int32_t *out_mapping)
+{
+    return fastged_batch_ex(h, pairs, K, nullptr, out_cost, out_mapping, nullptr);
+}
+
+// ------------------------------------------------------------------------------------
+// device-resident plans
+// ------------------------------------------------------------------------------------
+extern "C" int fastged_plan_create(fastged_handle *h, const fastged_pair_list *pairs,
+                                   int32_t K, const fastged_options *opt, fastged_plan **out)
+{
+    clear_error();
+    if (!h || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
+    const fastged_options o = opt ? *opt : default_options();
+    fastged_plan *p = new fastged_plan();
+    p->h = h;
+    int rc = flatten(h, pairs, K, o, p->b);
+    if (rc) { delete p; return rc; }
+    p->b.opt.k_per_pair = nullptr;   // copied into the staging buffer; never dereferenced
+    if ((rc = p->dev_in.ensure(std::max<size_t>(p->b.in_bytes, 256))) ||
+        (rc = p->dev_work.ensure(p->b.work_bytes)) ||
+        (rc = p->pin_out.ensure(std::max<size_t>(p->b.out_bytes, 256)))) {
+        fastged_plan_destroy(p);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(p->dev_in.p, h->pin.p, p->b.in_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        fastged_plan_destroy(p);
+        return cuda_fail(e, "plan upload");
+    }
+    p->use_graph = o.use_cuda_graph != 0 && o.form != FASTGED_FORM_PLAIN;
+    *out = p;
+    return FASTGED_OK;
+}
+
+extern "C" int fastged_plan_run(fastged_plan *p, void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FASTGED_ERR_INVALID_ARG, "null plan");
+    const Batch &b = p->b;
+    cudaStream_t st = stream ? (cudaStream_t)stream : p->stream;
+    p->last_stream = st;
+    if (b.n_pairs == 0) return FASTGED_OK;
+    uint8_t *in = (uint8_t *)p->dev_in.p, *wk = (uint8_t *)p->dev_work.p;
+    if (!p->use_graph) {
+        int nl = 0;
+        int rc = enqueue(p->h, b, in, wk, st, &nl);
+        p->launches = nl;
+        return rc;
+    }
+    if (!p->exec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        int rc = enqueue(p->h, b, in, wk, p->stream, &nl);
+        cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        p->launches = nl;
+    }
+    CK(cudaGraphLaunch(p->exec, st));
+    return FASTGED_OK;
+}
+
+extern "C" int fastged_plan_read(fastged_plan *p, int32_t *out_cost, int32_t *out_mapping,
+                                 int64_t *out_nevals)
+{
+    clear_error();
+    if (!p) return set_error(FASTGED_ERR_INVALID_ARG, "null plan");
+    const Batch &b = p->b;
+    if (b.n_pairs == 0) return FASTGED_OK;
+    cudaStream_t st = p->last_stream ? p->last_stream : p->stream;
+    CK(cudaMemcpyAsync(p->pin_out.p, p->dev_work.p, b.out_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return finish_outputs(b, (const uint8_t *)p->pin_out.p, out_cost, out_mapping, out_nevals);
+}
+
+extern "C" int fastged_plan_info(const fastged_plan *p, fastged_plan_stats *out)
+{
+    clear_error();
+    if (!p || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
+    memset(out, 0, sizeof(*out));
+    const Batch &b = p->b;
+    out->n_pairs = b.n_pairs;
+    out->n_classes = (int32_t)b.classes.size();
+    out->launches_per_run = p->launches;
+    out->graph_replay = p->use_graph ? 1 : 0;
+    out->input_bytes = (int64_t)b.in_bytes;
+    out->device_bytes = (int64_t)(b.in_bytes + b.work_bytes);
+    out->output_bytes = (int64_t)b.out_bytes;
+    for (size_t k = 0; k < b.classes.size() && k < 8; ++k) {
+        out->block_threads[k] = b.classes[k].block;
+        out->grid[k] = b.classes[k].grid;
+        out->words[k] = b.classes[k].W;
+        out->smem_bytes[k] = (int32_t)b.classes[k].smem;
+    }
+    return FASTGED_OK;
+}
+
+extern "C" void fastged_plan_destroy(fastged_plan *p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->last_stream && p->last_stream != p->stream) cudaStreamSynchronize(p->last_stream);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    p->dev_in.release();
+    p->dev_work.release();
+    p->pin_out.release();
+    delete p;
+}

@@ -1,0 +1,98 @@
+// fastged_runtime.h -- host-side objects behind the opaque handles of include/fastged.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fastged.h"
+#include "fastged_internal.h"
+
+namespace fastged {
+
+constexpr int kMaxClasses = 8;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n);   // grow-only; returns a fastged status
+    void release();
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n);
+    void release();
+};
+
+// One size class: pairs whose g2 bitsets need W words and whose stored vertex-map entries
+// are 8 (wide = false) or 16 bits wide.
+struct ClassPlan {
+    int W = 1;
+    bool wide = false;
+    int n1max = 0, n2max = 0, kmax = 1;
+    std::vector<int32_t> order;   // pair indices, heaviest first
+    int64_t order_off = 0;        // offset of this class's order in the device order array
+    Layout lay{};
+    int block = 256;
+    int grid = 1;
+    size_t smem = 0;
+    size_t scratch_off = 0;       // offset of this class's scratch in the scratch area
+};
+
+// A validated, flattened batch: staging offsets (input region) and device work offsets.
+struct Batch {
+    int n_graphs = 0, n_pairs = 0, K = 1, B = 0;
+    bool labelled = false;
+    bool has_kpp = false;
+    fastged_options opt{};
+    std::vector<GraphMeta> meta;
+    std::vector<int64_t> map_off;
+    int64_t n_vlab = 0, n_edges = 0, adj_words = 0, plane_words = 0, map_total = 0;
+    std::vector<ClassPlan> classes;
+    // input region (pinned staging == device input buffer)
+    size_t off_meta = 0, off_vlab = 0, off_edges = 0, off_elab = 0, off_pairs = 0,
+           off_order = 0, off_mapoff = 0, off_kpp = 0, in_bytes = 0;
+    // work region
+    size_t woff_err = 0, woff_cost = 0, woff_nev = 0, woff_map = 0, out_bytes = 0,
+           woff_queue = 0, woff_pool = 0, woff_scratch = 0, work_bytes = 0;
+};
+
+int set_error(int code, const std::string &msg);
+void clear_error();
+int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
+            const fastged_options &opt, Batch &b);
+int enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk, cudaStream_t st,
+            int *launches);
+int finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *out_cost,
+                   int32_t *out_mapping, int64_t *out_nevals);
+
+}  // namespace fastged
+
+struct fastged_handle {
+    fastged_cost_model cost{};
+    int device = 0;
+    int sm_count = 1;
+    int smem_optin = 48 * 1024;
+    int smem_per_sm = 100 * 1024;
+    cudaStream_t stream = nullptr;
+    cudaStream_t class_stream[fastged::kMaxClasses] = {};
+    cudaEvent_t ev[fastged::kMaxClasses + 1] = {};
+    fastged::DevBuf dev_in, dev_work;
+    fastged::PinBuf pin;
+    fastged::Batch batch;
+};
+
+struct fastged_plan {
+    fastged_handle *h = nullptr;
+    fastged::Batch b;
+    fastged::DevBuf dev_in, dev_work;
+    fastged::PinBuf pin_out;
+    cudaStream_t stream = nullptr;
+    cudaStream_t last_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    int launches = 0;
+};

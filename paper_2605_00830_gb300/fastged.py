@@ -1,0 +1,310 @@
+"""Thin Python binding of the libfastged C ABI (include/fastged.h).
+
+Only argument marshalling lives here: every step of the K-Best path runs in the library's
+sm_103a kernels. The binding loads the in-tree library and fails loudly when it is missing;
+there is no CPU fallback. Names follow the C ABI (fastged_create, fastged_batch, ...).
+
+Graph batches are marshalled without Python loops: the graphs of a workload are
+concatenated into three flat arrays and the array of fastged_graph structs is filled with
+numpy from base addresses and offsets.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+FASTGED_OK = 0
+FASTGED_ERR_INVALID_ARG = -1
+FASTGED_ERR_OOM = -2
+FASTGED_ERR_CUDA = -3
+FASTGED_ERR_TIMEOUT = -4
+FASTGED_ERR_BUSY = -5
+FASTGED_ERR_STOPPED = -6
+FASTGED_FORM_BATCHED = 0
+FASTGED_FORM_PLAIN = 1
+
+EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
+            "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
+            "fastged_plan_read", "fastged_plan_info", "fastged_plan_destroy"]
+
+
+class FastGEDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fastged error {code}: {msg}")
+        self.code = code
+
+
+class CostModel(ctypes.Structure):
+    _fields_ = [("v_sub", ctypes.c_int32), ("v_del", ctypes.c_int32), ("v_ins", ctypes.c_int32),
+                ("e_sub", ctypes.c_int32), ("e_del", ctypes.c_int32), ("e_ins", ctypes.c_int32)]
+
+
+class GraphC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("vlabel", ctypes.c_void_p), ("m", ctypes.c_int32),
+                ("edges", ctypes.c_void_p), ("elabel", ctypes.c_void_p)]
+
+
+class PairList(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_int32), ("graphs", ctypes.c_void_p),
+                ("n_pairs", ctypes.c_int32), ("pairs", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("k_per_pair", ctypes.c_void_p), ("hist_window", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("launches_per_run", ctypes.c_int32), ("graph_replay", ctypes.c_int32),
+                ("input_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("output_bytes", ctypes.c_int64), ("block_threads", ctypes.c_int32 * 8),
+                ("grid", ctypes.c_int32 * 8), ("words", ctypes.c_int32 * 8),
+                ("smem_bytes", ctypes.c_int32 * 8)]
+
+
+_GRAPH_DTYPE = np.dtype({"names": ["n", "vlabel", "m", "edges", "elabel"],
+                         "formats": ["<i4", "<u8", "<i4", "<u8", "<u8"],
+                         "offsets": [0, 8, 16, 24, 32], "itemsize": 40})
+assert ctypes.sizeof(GraphC) == 40 and ctypes.sizeof(Options) == 32
+
+_LIB = None
+
+
+def load(path: Optional[str] = None, build_if_missing: bool = True):
+    """Load libfastged (building it in-tree first when asked). Raises when it is absent."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or _build.lib_path()
+    if not os.path.exists(p):
+        if not build_if_missing:
+            raise RuntimeError(f"libfastged not built ({p}); run __graft_entry__.build()")
+        p = _build.build()
+    lib = ctypes.CDLL(p)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.fastged_version.restype = ctypes.c_int
+    lib.fastged_last_error.argtypes = [vp]
+    lib.fastged_last_error.restype = ctypes.c_char_p
+    lib.fastged_create.argtypes = [ctypes.POINTER(CostModel), ctypes.POINTER(vp)]
+    lib.fastged_destroy.argtypes = [vp]
+    lib.fastged_destroy.restype = None
+    lib.fastged_batch.argtypes = [vp, ctypes.POINTER(PairList), i32, vp, vp]
+    lib.fastged_batch_ex.argtypes = [vp, ctypes.POINTER(PairList), i32, ctypes.POINTER(Options),
+                                     vp, vp, vp]
+    lib.fastged_plan_create.argtypes = [vp, ctypes.POINTER(PairList), i32,
+                                        ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.fastged_plan_run.argtypes = [vp, vp]
+    lib.fastged_plan_read.argtypes = [vp, vp, vp, vp]
+    lib.fastged_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
+    lib.fastged_plan_destroy.argtypes = [vp]
+    lib.fastged_plan_destroy.restype = None
+    for name in EXPORTED:
+        if name in ("fastged_destroy", "fastged_plan_destroy", "fastged_last_error",
+                    "fastged_version"):
+            continue
+        getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _check(lib, rc: int):
+    if rc != FASTGED_OK:
+        msg = lib.fastged_last_error(None)
+        raise FastGEDError(rc, msg.decode() if msg else "")
+
+
+class Marshalled:
+    """A workload's graphs and pairs in the C layout, kept alive for the duration of calls."""
+
+    def __init__(self, graphs, pairs):
+        ng = len(graphs)
+        self.n = np.fromiter((g.n for g in graphs), dtype=np.int32, count=ng)
+        self.m = np.fromiter((g.edges.shape[0] for g in graphs), dtype=np.int32, count=ng)
+        self.vl = (np.concatenate([np.asarray(g.vlabel, dtype=np.int32) for g in graphs])
+                   if ng else np.zeros(0, np.int32))
+        self.ed = (np.concatenate([np.asarray(g.edges, dtype=np.int32).reshape(-1) for g in graphs])
+                   if ng else np.zeros(0, np.int32))
+        labelled = [g.elabel is not None for g in graphs]
+        self.el = None
+        if any(labelled):
+            self.el = np.concatenate([np.asarray(g.elabel, dtype=np.int32) if g.elabel is not None
+                                      else np.zeros(g.edges.shape[0], np.int32) for g in graphs])
+        self.vl = np.ascontiguousarray(self.vl)
+        self.ed = np.ascontiguousarray(self.ed)
+        voff = np.zeros(ng, dtype=np.uint64)
+        eoff = np.zeros(ng, dtype=np.uint64)
+        if ng:
+            voff[1:] = np.cumsum(self.n[:-1], dtype=np.uint64)
+            eoff[1:] = np.cumsum(self.m[:-1], dtype=np.uint64)
+        self.gs = np.zeros(ng, dtype=_GRAPH_DTYPE)
+        self.gs["n"] = self.n
+        self.gs["m"] = self.m
+        vbase = self.vl.ctypes.data if self.vl.size else 0
+        ebase = self.ed.ctypes.data if self.ed.size else 0
+        self.gs["vlabel"] = np.where(self.n > 0, vbase + voff * 4, 0)
+        self.gs["edges"] = np.where(self.m > 0, ebase + eoff * 8, 0)
+        if self.el is not None and self.el.size:
+            self.gs["elabel"] = np.where(self.m > 0, self.el.ctypes.data + eoff * 4, 0)
+        self.pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.pl = PairList(ng, self.gs.ctypes.data if ng else None, self.pairs.shape[0],
+                           self.pairs.ctypes.data if self.pairs.size else None)
+        self.n1 = self.n[self.pairs[:, 0]] if self.pairs.size else np.zeros(0, np.int32)
+        self.map_off = np.zeros(self.pairs.shape[0] + 1, dtype=np.int64)
+        if self.pairs.size:
+            self.map_off[1:] = np.cumsum(self.n1, dtype=np.int64)
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.pairs.shape[0])
+
+
+def marshal(w) -> Marshalled:
+    """Marshal a Workload (cached on the object)."""
+    mm = getattr(w, "_marshalled", None)
+    if mm is None:
+        mm = Marshalled(w.graphs, w.pairs)
+        try:
+            w._marshalled = mm
+        except AttributeError:
+            pass
+    return mm
+
+
+def make_options(form: int = FASTGED_FORM_BATCHED, variant: int = 0, k_per_pair=None,
+                 hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1):
+    kpp = None
+    if k_per_pair is not None:
+        kpp = np.ascontiguousarray(np.asarray(k_per_pair, dtype=np.int32))
+    o = Options(form, variant, kpp.ctypes.data if kpp is not None else None, hist_window,
+                block_threads, use_cuda_graph)
+    o._keep = kpp
+    return o
+
+
+def fastged_version() -> int:
+    return int(load().fastged_version())
+
+
+def fastged_last_error() -> str:
+    return load().fastged_last_error(None).decode()
+
+
+def fastged_create(cost: Sequence[int]) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib, lib.fastged_create(ctypes.byref(CostModel(*[int(x) for x in cost])),
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def fastged_destroy(h: int) -> None:
+    load().fastged_destroy(h)
+
+
+def _outputs(mm: Marshalled):
+    return (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+            np.zeros(mm.n_pairs, np.int64))
+
+
+def fastged_batch(h: int, mm: Marshalled, K: int, out_cost: np.ndarray, out_mapping: np.ndarray):
+    lib = load()
+    _check(lib, lib.fastged_batch(h, ctypes.byref(mm.pl), int(K), out_cost.ctypes.data,
+                                  out_mapping.ctypes.data if out_mapping.size else None))
+
+
+def fastged_batch_ex(h: int, mm: Marshalled, K: int, opt: Optional[Options],
+                     out_cost: np.ndarray, out_mapping: np.ndarray,
+                     out_nevals: Optional[np.ndarray]):
+    lib = load()
+    _check(lib, lib.fastged_batch_ex(h, ctypes.byref(mm.pl), int(K),
+                                     ctypes.byref(opt) if opt is not None else None,
+                                     out_cost.ctypes.data,
+                                     out_mapping.ctypes.data if out_mapping.size else None,
+                                     out_nevals.ctypes.data if out_nevals is not None else None))
+
+
+def fastged_plan_create(h: int, mm: Marshalled, K: int, opt: Optional[Options] = None) -> int:
+    lib = load()
+    p = ctypes.c_void_p()
+    _check(lib, lib.fastged_plan_create(h, ctypes.byref(mm.pl), int(K),
+                                        ctypes.byref(opt) if opt is not None else None,
+                                        ctypes.byref(p)))
+    return p.value
+
+
+def fastged_plan_run(plan: int, stream: int = 0) -> None:
+    lib = load()
+    _check(lib, lib.fastged_plan_run(plan, stream or None))
+
+
+def fastged_plan_read(plan: int, out_cost, out_mapping, out_nevals) -> None:
+    lib = load()
+    _check(lib, lib.fastged_plan_read(
+        plan, out_cost.ctypes.data if out_cost is not None else None,
+        out_mapping.ctypes.data if out_mapping is not None and out_mapping.size else None,
+        out_nevals.ctypes.data if out_nevals is not None else None))
+
+
+def fastged_plan_info(plan: int) -> dict:
+    lib = load()
+    st = PlanStats()
+    _check(lib, lib.fastged_plan_info(plan, ctypes.byref(st)))
+    nc = st.n_classes
+    return {"n_pairs": st.n_pairs, "n_classes": nc, "launches_per_run": st.launches_per_run,
+            "graph_replay": st.graph_replay, "input_bytes": st.input_bytes,
+            "device_bytes": st.device_bytes, "output_bytes": st.output_bytes,
+            "block_threads": list(st.block_threads[:nc]), "grid": list(st.grid[:nc]),
+            "words": list(st.words[:nc]), "smem_bytes": list(st.smem_bytes[:nc])}
+
+
+def fastged_plan_destroy(plan: int) -> None:
+    load().fastged_plan_destroy(plan)
+
+
+def split_maps(mm: Marshalled, flat: np.ndarray):
+    return [flat[mm.map_off[p]:mm.map_off[p + 1]] for p in range(mm.n_pairs)]
+
+
+class FastGED:
+    """Convenience wrapper: one handle (cost model) on the current device."""
+
+    def __init__(self, cost: Sequence[int]):
+        self.cost = tuple(int(x) for x in cost)
+        self.h = fastged_create(self.cost)
+
+    def close(self):
+        if self.h:
+            fastged_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, w, K: Optional[int] = None, **opts) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(costs[n_pairs], flat maps, nevals[n_pairs]) for a Workload."""
+        mm = marshal(w)
+        if K is None:
+            K = w.K
+        if "k_per_pair" not in opts and w.k_per_pair is not None:
+            opts["k_per_pair"] = w.k_per_pair
+            K = max(K, int(np.max(w.k_per_pair)))
+        cost, maps, nev = _outputs(mm)
+        fastged_batch_ex(self.h, mm, K, make_options(**opts), cost, maps, nev)
+        return cost, maps, nev

@@ -1,0 +1,215 @@
+"""GPU parity: the sm_103a path through the C ABI against the CPU oracle, bit-exact on
+cost, vertex map and evaluation count (costs are integers, so the tolerance is zero)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_00830_gb300 import fastged as F
+from paper_2605_00830_gb300 import workloads as W
+from parity_util import assert_parity, assert_valid_paths, gpu_run, single
+
+pytestmark = pytest.mark.gpu
+
+
+def test_config1_full():
+    w = W.config1()
+    assert_parity(w, gpu_run(w))
+
+
+def test_config2_prefix():
+    w = W.config2(400)
+    assert_parity(w, gpu_run(w))
+
+
+def test_config3_prefix():
+    w = W.config3(24)
+    assert_parity(w, gpu_run(w))
+
+
+def test_config4_shaped_small():
+    """Large sparse shape at reduced size: BA graphs, perturbed copies, 16-bit vertex maps
+    (n2 >= 255) and several 64-bit words per bitset."""
+    w = W.config4(6, seed=41, n_range=(150, 320))
+    w.K = 48
+    assert_parity(w, gpu_run(w))
+
+
+def test_config4_full_size_sample():
+    """One full-size large sparse pair (the smallest of a 64-pair draw) at K = 1024."""
+    w = W.config4(64)
+    p = int(np.argmin([w.graphs[2 * k].n for k in range(64)]))
+    ws = W.subset(w, [p])
+    assert_parity(ws, gpu_run(ws))
+
+
+@pytest.mark.parametrize("hw", [2, 3, 17])
+def test_exact_selection_fallback(hw):
+    """A tiny histogram window pushes almost every level onto the exact fallback of the
+    selection; results must not change."""
+    w = W.config2(120)
+    assert_parity(w, gpu_run(w, hist_window=hw))
+    w1 = W.config1(60)
+    assert_parity(w1, gpu_run(w1, hist_window=hw))
+
+
+def test_large_costs():
+    """Costs spread far beyond the histogram window (fallback on real data)."""
+    w = W.config2(80)
+    w.cost = (1000, 3001, 2999, 700, 1500, 901)
+    assert_parity(w, gpu_run(w))
+
+
+@pytest.mark.parametrize("bt", [128, 256, 512])
+def test_block_sizes(bt):
+    w = W.config2(150)
+    assert_parity(w, gpu_run(w, block_threads=bt))
+
+
+def test_plain_form_equals_batched():
+    w = W.config2(200)
+    a = gpu_run(w)
+    b = gpu_run(w, form=F.FASTGED_FORM_PLAIN)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_per_pair_k():
+    w = W.config2(90)
+    st = W.Stream(77, 1)
+    kpp = st.randint(1, 100, w.n_pairs).astype(np.int32)
+    w.k_per_pair = kpp
+    gpu = gpu_run(w, K=100)
+    mm = F.marshal(w)
+    cost, maps, nev = gpu
+    for p in range(w.n_pairs):
+        g1, g2 = w.graphs[2 * p], w.graphs[2 * p + 1]
+        rc, rm, rn = O.kbest(g1, g2, w.cost, int(kpp[p]))
+        assert (int(cost[p]), int(nev[p])) == (rc, rn)
+        assert np.array_equal(maps[mm.map_off[p]:mm.map_off[p + 1]], rm)
+
+
+def _edge_graphs():
+    st = W.Stream(5, 55)
+    out = {}
+    e = W.empty_graph()
+    g = W.random_small(st, 6, 6, 0.5, 3, 2)
+    out["empty_source"] = (e, g)
+    out["empty_target"] = (g, e)
+    out["both_empty"] = (e, e)
+    one = W.Graph(1, np.array([2], np.int32), np.zeros((0, 2), np.int32))
+    out["single_vertex"] = (one, g)
+    for n in (63, 64, 65, 127, 128, 129, 254, 255, 256):
+        a = W.erdos_renyi(W.Stream(n, 1), n, 0.08, 5)
+        b = W.erdos_renyi(W.Stream(n, 2), n, 0.08, 5)
+        out[f"n{n}"] = (a, b)
+    # all labels equal: maximal ties
+    a = W.erdos_renyi(W.Stream(9, 1), 12, 0.3, 1)
+    b = W.erdos_renyi(W.Stream(9, 2), 14, 0.3, 1)
+    out["all_equal_labels"] = (a, b)
+    # complete graphs
+    iu = np.triu_indices(9, 1)
+    k9 = W.Graph(9, np.zeros(9, np.int32), np.stack(iu, 1).astype(np.int32))
+    iu = np.triu_indices(7, 1)
+    k7 = W.Graph(7, np.zeros(7, np.int32), np.stack(iu, 1).astype(np.int32))
+    out["complete"] = (k9, k7)
+    # n1 > n2 and n1 < n2
+    out["n1_gt_n2"] = (W.erdos_renyi(W.Stream(3, 1), 20, 0.2, 3),
+                       W.erdos_renyi(W.Stream(3, 2), 7, 0.3, 3))
+    out["n1_lt_n2"] = (W.erdos_renyi(W.Stream(4, 1), 7, 0.3, 3),
+                       W.erdos_renyi(W.Stream(4, 2), 20, 0.2, 3))
+    # many edge labels (8 bit-planes)
+    a = W.random_small(W.Stream(6, 1), 15, 15, 0.4, 3, 256)
+    b = W.random_small(W.Stream(6, 2), 15, 15, 0.4, 3, 256)
+    out["elabels_255"] = (a, b)
+    return out
+
+
+@pytest.mark.parametrize("K", [1, 2, 7, 64, 5000])
+@pytest.mark.parametrize("name", sorted(_edge_graphs()))
+def test_edge_cases(name, K):
+    g1, g2 = _edge_graphs()[name]
+    if max(g1.n, g2.n) > 100 and K > 64:
+        K = 96
+    for cost in (W.UNIT_COSTS, W.SETTING1_COSTS, (3, 1, 2, 5, 1, 4)):
+        w = single([(g1, g2), (g2, g1)], cost, K)
+        assert_parity(w, gpu_run(w))
+
+
+def test_batch_mixed_classes():
+    """One batch mixing every size class (1..16 words, 8- and 16-bit maps) and labelled /
+    unlabelled graphs; each pair must match the oracle as if it ran alone."""
+    g = _edge_graphs()
+    pairs = [g[k] for k in ("n63", "n129", "n255", "n256", "complete", "elabels_255",
+                            "empty_source", "n1_gt_n2")]
+    big = W.config4(1, seed=9, n_range=(600, 640))
+    pairs.append((big.graphs[0], big.graphs[1]))
+    w = single(pairs, W.UNIT_COSTS, 24)
+    assert_parity(w, gpu_run(w))
+
+
+def test_plan_replay_matches_batch_and_is_repeatable():
+    w = W.config2(300)
+    ref = gpu_run(w)
+    mm = F.marshal(w)
+    with F.FastGED(w.cost) as g:
+        plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options())
+        outs = []
+        for _ in range(3):
+            F.fastged_plan_run(plan)
+            c, m, n = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+                       np.zeros(mm.n_pairs, np.int64))
+            F.fastged_plan_read(plan, c, m, n)
+            outs.append((c, m, n))
+        info = F.fastged_plan_info(plan)
+        F.fastged_plan_destroy(plan)
+    assert info["graph_replay"] == 1 and info["launches_per_run"] >= 2
+    for o in outs:
+        for x, y in zip(o, ref):
+            assert np.array_equal(x, y)
+
+
+def test_config2_full_batch_bench_configuration():
+    """The full 20,000-pair molecule-like batch in the launch configuration the benchmark
+    times (plan + CUDA-graph replay): a seeded sample of pairs is checked bit-exactly
+    against the oracle, and every pair against the edit-path properties."""
+    w = W.config2()
+    mm = F.marshal(w)
+    with F.FastGED(w.cost) as g:
+        plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options())
+        F.fastged_plan_run(plan)
+        c, m, n = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+                   np.zeros(mm.n_pairs, np.int64))
+        F.fastged_plan_read(plan, c, m, n)
+        F.fastged_plan_destroy(plan)
+    idx = sorted(set(W.Stream(2024, 8).randint(0, w.n_pairs - 1, 300).tolist()))
+    assert_parity(w, (c, m, n), idx=idx)
+    assert_valid_paths(w, (c, m, n))
+
+
+def test_invalid_inputs():
+    g = W.erdos_renyi(W.Stream(1, 1), 6, 0.5, 2)
+    h = W.erdos_renyi(W.Stream(1, 2), 5, 0.5, 2)
+    dup = W.Graph(g.n, g.vlabel, np.concatenate([g.edges, g.edges[:1]]))
+    loop = W.Graph(g.n, g.vlabel, np.concatenate([g.edges, np.array([[2, 2]], np.int32)]))
+    outside = W.Graph(g.n, g.vlabel, np.array([[0, 9]], np.int32))
+    big = W.Graph(1025, np.zeros(1025, np.int32), np.zeros((0, 2), np.int32))
+    badlab = W.Graph(g.n, g.vlabel, g.edges, np.full(g.m, 300, np.int32))
+    with F.FastGED(W.UNIT_COSTS) as fg:
+        for bad in (dup, loop, outside, big, badlab):
+            w = single([(bad, h)], W.UNIT_COSTS, 4)
+            with pytest.raises(F.FastGEDError) as ei:
+                fg.run(w)
+            assert ei.value.code == F.FASTGED_ERR_INVALID_ARG
+        w = single([(g, h)], W.UNIT_COSTS, 4)
+        for K in (0, -3, 70000):
+            with pytest.raises(F.FastGEDError):
+                fg.run(w, K=K)
+        # an invalid call leaves the handle usable
+        cost, _, _ = fg.run(w)
+        assert cost[0] == O.kbest(g, h, W.UNIT_COSTS, 4)[0]
+    with pytest.raises(F.FastGEDError):
+        F.FastGED((1, -1, 1, 1, 1, 1))
+    with pytest.raises(F.FastGEDError):
+        big_cost = (1 << 29,) * 6
+        with F.FastGED(big_cost) as fg:
+            fg.run(single([(g, h)], big_cost, 4))
