@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the K-Best GED path on one GB300: GED pairs/s at fixed K.
+
+Workload (one step): the 20,000-pair molecule-like batch (10-40 vertices, tree + ring
+edges, Zipf vertex labels, 3 edge labels, the paper's setting-1 costs, K = 100), seeded
+and synthetic. One step is one pass of the whole device path over the batch: bitset
+packing, every K-Best level of every pair, leaf completion and argmin.
+
+  value      pairs/s with the batch resident in HBM (device-resident plan replayed as a
+             CUDA graph), CUDA events on the launching stream, L2 flushed between steps
+  e2e        the same metric through fastged_batch_ex with host inputs and outputs
+             (flattening, host-to-device copy, kernels, device-to-host copy)
+  roofline   the K-Best kernel's integer ops per launch / its event-timed duration,
+             against the measured LOP3/IADD rate of this GPU (the path is ALU bound)
+  plain_form the same arithmetic launched once per pair on one stream (a bounded sample)
+  cpu_baseline  the CPU oracle on a bounded sample, on every host core
+
+--impl reference times the CPU oracle (the only reference this method has) on the same
+metric and workload, one bounded sample per step.
+Multi-GPU (torchrun): every rank solves its own seeded 20,000-pair batch (weak scaling,
+no data-path collective); the barrier and the max over ranks bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GED pairs/s & edit-path evals/s at fixed K vs plain form; serve p50/p99 ms"
+UNIT = "pairs/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--plain-sample", type=int, default=2000)
+    ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-form, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank: int, n_pairs: int):
+    from paper_2605_00830_gb300 import workloads as W
+    seed = 2 if rank == 0 else 2 + 7919 * rank
+    return W.config2(n_pairs, seed=seed)
+
+
+def config_dict(w, extra=None):
+    d = {"workload": "molecule-like batch: 20,000 pairs, 10-40 vertices, K=100, setting-1 costs",
+         "name": w.name, "n_pairs": w.n_pairs, "K": w.K, "cost": list(w.cost),
+         "l2": "flushed (256 MB write) between timed steps", "seed": 2}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def int_ops_per_eval(W: int, B: int, fold: bool) -> int:
+    """32-bit integer operations of one successor evaluation as the bitset formula states
+    it: per 64-bit word AND, XOR (or ANDN, ANDN), POPC (2 POPC + 1 ADD on 32-bit lanes);
+    per word and label plane an XOR and an OR, then two ANDs and a POPC; plus the used-bit
+    test (2) and the cost sum (4)."""
+    word = 7 if fold else 11
+    lab = (4 * B + 5) if B > 0 else 0
+    return (word + lab) * W + 6
+
+
+def run_cpu_oracle(w, idx, threads):
+    from oracle import oracle as O
+    t = time.perf_counter()
+    res = O.kbest_workload(w, idx, threads=threads)
+    return time.perf_counter() - t, res
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(0, args.pairs)
+    threads = os.cpu_count() or 1
+    sample = list(range(min(args.cpu_sample, w.n_pairs)))
+    for _ in range(args.warmup):
+        run_cpu_oracle(w, sample[:200], threads)
+    tot = 0.0
+    evals = 0
+    for _ in range(args.steps):
+        dt, res = run_cpu_oracle(w, sample, threads)
+        tot += dt
+        evals += sum(r[2] for r in res)
+    value = len(sample) * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": config_dict(w, {"parallelism": "host threads"}),
+            "evals_per_s": evals / tot,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {len(sample)} pairs of the batch per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2605_00830_gb300 import fastged as F
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    F.load()
+
+    w = workload(rank, args.pairs)
+    mm = F.marshal(w)
+    g = F.FastGED(w.cost)
+    plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    c_out = np.zeros(mm.n_pairs, np.int32)
+    m_out = np.zeros(int(mm.map_off[-1]), np.int32)
+    n_out = np.zeros(mm.n_pairs, np.int64)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        F.fastged_plan_run(plan, stream.cuda_stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kms = []
+    for s in range(args.steps):
+        flush.zero_()
+        e0[s].record(stream)
+        F.fastged_plan_run(plan, stream.cuda_stream)
+        e1[s].record(stream)
+        kms.append(F.fastged_plan_kernel_ms(plan))
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    clk = clocks.stop()
+    tot_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        torch.distributed.barrier()
+    F.fastged_plan_read(plan, c_out, m_out, n_out)
+    info = F.fastged_plan_info(plan)
+    evals = int(n_out.sum())
+    value = mm.n_pairs * ws * args.steps / (tot_ms / 1e3)
+
+    # roofline of the K-Best launches (ALU bound)
+    fold = w.cost[4] == w.cost[5]
+    B = 0
+    labs = [int(gr.elabel.max()) for gr in w.graphs if gr.elabel is not None and gr.m > 0]
+    if labs:
+        B = max(labs).bit_length()
+    # substitution successors only (deletions and completions do no bitset work): every
+    # level expands at most K nodes, each with one deletion child, so this is a lower bound
+    n1s = mm.n1.astype(np.int64)
+    subs = evals - int(((n1s + 1) * w.K).sum())
+    ops = int_ops_per_eval(1, B, fold) * subs
+    kernel_ms = float(np.mean(kms))
+    peak = F.fastged_measure_int_peak() if rank == 0 else {"lop3": 0, "iadd": 0, "popc": 0}
+    alu_peak = min(peak["lop3"], peak["iadd"])
+    achieved = ops / (kernel_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": config_dict(w, {"parallelism": f"replicas{ws}" if ws > 1 else "1 GPU"}),
+            "evals_per_s": evals * ws * args.steps / (tot_ms / 1e3),
+            "evals_per_step": evals,
+            "kernel_ms": kernel_ms,
+            "gpu_launches": info["launches_per_run"] * args.steps,
+            "plan": info,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                         "unit": "Tops/s (32-bit integer)", "frac": achieved / alu_peak,
+                         "traffic": None,
+                         "ops_per_eval": int_ops_per_eval(1, B, fold),
+                         "peak_source": "measured in-run: LOP3/IADD probe kernels (min of the two)",
+                         "popc_peak": peak["popc"] / 1e12},
+            "clocks": clk}
+    if rank == 0 and not args.no_extras:
+        # e2e through the public API with host buffers
+        cst, mp, nv = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+                       np.zeros(mm.n_pairs, np.int64))
+        opt = F.make_options()
+        F.fastged_batch_ex(g.h, mm, w.K, opt, cst, mp, nv)
+        e2e_t = 0.0
+        n_e2e = max(1, min(args.steps, 5))
+        for _ in range(n_e2e):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            F.fastged_batch_ex(g.h, mm, w.K, opt, cst, mp, nv)
+            e2e_t += time.perf_counter() - t
+        assert np.array_equal(cst, c_out)
+        line["e2e"] = {"value": mm.n_pairs * n_e2e / e2e_t, "unit": UNIT,
+                       "h2d_bytes_per_step": info["input_bytes"],
+                       "d2h_bytes_per_step": info["output_bytes"], "steps": n_e2e}
+        # plain per-pair form on a bounded sample
+        from paper_2605_00830_gb300 import workloads as W
+        ws_ = W.subset(w, range(min(args.plain_sample, w.n_pairs)))
+        mms = F.marshal(ws_)
+        pplan = F.fastged_plan_create(g.h, mms, w.K, F.make_options(form=F.FASTGED_FORM_PLAIN,
+                                                                     use_cuda_graph=0))
+        F.fastged_plan_run(pplan, stream.cuda_stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        F.fastged_plan_run(pplan, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        F.fastged_plan_destroy(pplan)
+        plain = mms.n_pairs / (pms / 1e3)
+        line["plain_form"] = {"value": plain, "unit": UNIT, "sample_pairs": mms.n_pairs,
+                              "batched_over_plain": value / ws / plain}
+        # CPU oracle on a bounded sample, all host cores
+        threads = os.cpu_count() or 1
+        idx = list(range(min(args.cpu_sample, w.n_pairs)))
+        dt, _ = run_cpu_oracle(w, idx, threads)
+        line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"first {len(idx)} of the 20,000 pairs"}
+    F.fastged_plan_destroy(plan)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -101,8 +101,8 @@ typedef struct {
                              /* the selection step; small values force its exact fallback     */
                              /* path (a testing knob; results do not depend on it)            */
     int32_t block_threads;   /* 0 = autotuned; else 128, 256 or 512 threads per team          */
-    int32_t use_cuda_graph;  /* plans only: 1 (default when 0 is not given explicitly via     */
-                             /* FASTGED_NO_GRAPH) replays a captured CUDA graph               */
+    int32_t use_cuda_graph;  /* plans only: 1 = capture the run once and replay it as a CUDA  */
+                             /* graph, 0 = launch directly (a NULL options pointer means 1)   */
 } fastged_options;
 
 typedef struct fastged_handle fastged_handle;
@@ -171,8 +171,20 @@ typedef struct {
 
 int fastged_plan_info(const fastged_plan *p, fastged_plan_stats *out);
 
+/* Device time (ms) of the K-Best launches of the plan's last run: from the end of the
+ * bitset packing to the end of the last size class, measured with CUDA events recorded on
+ * the run's stream (inside the replayed graph when the plan replays one). Waits for the run. */
+int fastged_plan_kernel_ms(fastged_plan *p, float *ms);
+
 /* Releases the plan (waits for its last run). NULL is ignored. */
 void fastged_plan_destroy(fastged_plan *p);
+
+/* Integer-pipe throughput of the current device (no counterpart in the paper; it is the
+ * measured peak the benchmark compares the successor evaluation against). Runs three
+ * short probe kernels issuing independent 32-bit LOP3, IADD and POPC chains on every SM
+ * and writes the device-wide rate of each (instructions x lanes per second); any output
+ * pointer may be NULL. Allocates and frees a 16 KB device buffer. */
+int fastged_measure_int_peak(double *lop3_per_s, double *iadd_per_s, double *popc_per_s);
 
 #ifdef __cplusplus
 }

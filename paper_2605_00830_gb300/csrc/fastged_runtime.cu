@@ -508,7 +508,7 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
 
 // Enqueues the device path of a batch: zero pools and queues, pack, one launch per class.
 int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk,
-                     cudaStream_t st, int *launches)
+                     cudaStream_t st, int *launches, cudaEvent_t t0, cudaEvent_t t1)
 {
     int nl = 0;
     CK(cudaMemsetAsync(wk + b.woff_err, 0, 16, st));
@@ -527,6 +527,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
         ++nl;
     }
     const int nc = (int)b.classes.size();
+    if (t0) CK(cudaEventRecord(t0, st));
     if (b.opt.form == FASTGED_FORM_PLAIN) {
         // one launch per pair, in pair order, single team, on the caller's stream
         std::vector<int> cls(b.n_pairs), pos(b.n_pairs);
@@ -563,6 +564,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));
         }
     }
+    if (t1) CK(cudaEventRecord(t1, st));
     if (launches) *launches = nl;
     return FASTGED_OK;
 }
@@ -634,6 +636,8 @@ extern "C" int fastged_plan_create(fastged_handle *h, const fastged_pair_list *p
     }
     cudaError_t e = cudaMemcpy(p->dev_in.p, h->pin.p, p->b.in_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->t1);
     if (e != cudaSuccess) {
         fastged_plan_destroy(p);
         return cuda_fail(e, "plan upload");
@@ -654,7 +658,7 @@ extern "C" int fastged_plan_run(fastged_plan *p, void *stream)
     uint8_t *in = (uint8_t *)p->dev_in.p, *wk = (uint8_t *)p->dev_work.p;
     if (!p->use_graph) {
         int nl = 0;
-        int rc = enqueue(p->h, b, in, wk, st, &nl);
+        int rc = enqueue(p->h, b, in, wk, st, &nl, p->t0, p->t1);
         p->launches = nl;
         return rc;
     }
@@ -662,7 +666,7 @@ extern "C" int fastged_plan_run(fastged_plan *p, void *stream)
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         int nl = 0;
-        int rc = enqueue(p->h, b, in, wk, p->stream, &nl);
+        int rc = enqueue(p->h, b, in, wk, p->stream, &nl, p->t0, p->t1);
         cudaError_t e = cudaStreamEndCapture(p->stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -710,6 +714,17 @@ extern "C" int fastged_plan_info(const fastged_plan *p, fastged_plan_stats *out)
     return FASTGED_OK;
 }
 
+extern "C" int fastged_plan_kernel_ms(fastged_plan *p, float *ms)
+{
+    clear_error();
+    if (!p || !ms) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
+    *ms = 0.f;
+    if (p->b.n_pairs == 0) return FASTGED_OK;
+    CK(cudaEventSynchronize(p->t1));
+    CK(cudaEventElapsedTime(ms, p->t0, p->t1));
+    return FASTGED_OK;
+}
+
 extern "C" void fastged_plan_destroy(fastged_plan *p)
 {
     if (!p) return;
@@ -717,6 +732,8 @@ extern "C" void fastged_plan_destroy(fastged_plan *p)
     if (p->last_stream && p->last_stream != p->stream) cudaStreamSynchronize(p->last_stream);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->t0) cudaEventDestroy(p->t0);
+    if (p->t1) cudaEventDestroy(p->t1);
     p->dev_in.release();
     p->dev_work.release();
     p->pin_out.release();

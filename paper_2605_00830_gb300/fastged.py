@@ -30,7 +30,8 @@ FASTGED_FORM_PLAIN = 1
 
 EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
             "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
-            "fastged_plan_read", "fastged_plan_info", "fastged_plan_destroy"]
+            "fastged_plan_read", "fastged_plan_info", "fastged_plan_kernel_ms",
+            "fastged_plan_destroy", "fastged_measure_int_peak"]
 
 
 class FastGEDError(RuntimeError):
@@ -103,8 +104,11 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_plan_run.argtypes = [vp, vp]
     lib.fastged_plan_read.argtypes = [vp, vp, vp, vp]
     lib.fastged_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
+    lib.fastged_plan_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.fastged_plan_destroy.argtypes = [vp]
     lib.fastged_plan_destroy.restype = None
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.fastged_measure_int_peak.argtypes = [dp, dp, dp]
     for name in EXPORTED:
         if name in ("fastged_destroy", "fastged_plan_destroy", "fastged_last_error",
                     "fastged_version"):
@@ -265,8 +269,23 @@ def fastged_plan_info(plan: int) -> dict:
             "words": list(st.words[:nc]), "smem_bytes": list(st.smem_bytes[:nc])}
 
 
+def fastged_plan_kernel_ms(plan: int) -> float:
+    lib = load()
+    ms = ctypes.c_float(0.0)
+    _check(lib, lib.fastged_plan_kernel_ms(plan, ctypes.byref(ms)))
+    return float(ms.value)
+
+
 def fastged_plan_destroy(plan: int) -> None:
     load().fastged_plan_destroy(plan)
+
+
+def fastged_measure_int_peak() -> dict:
+    """Device-wide 32-bit LOP3 / IADD / POPC rates (ops per second)."""
+    lib = load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib, lib.fastged_measure_int_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"lop3": a.value, "iadd": b.value, "popc": c.value}
 
 
 def split_maps(mm: Marshalled, flat: np.ndarray):
