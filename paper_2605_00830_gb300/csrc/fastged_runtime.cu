@@ -527,7 +527,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
         ++nl;
     }
     const int nc = (int)b.classes.size();
-    if (t0) CK(cudaEventRecord(t0, st));
+    if (t0) CK(cudaEventRecordWithFlags(t0, st, cudaEventRecordExternal));
     if (b.opt.form == FASTGED_FORM_PLAIN) {
         // one launch per pair, in pair order, single team, on the caller's stream
         std::vector<int> cls(b.n_pairs), pos(b.n_pairs);
@@ -564,7 +564,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));
         }
     }
-    if (t1) CK(cudaEventRecord(t1, st));
+    if (t1) CK(cudaEventRecordWithFlags(t1, st, cudaEventRecordExternal));
     if (launches) *launches = nl;
     return FASTGED_OK;
 }

@@ -523,29 +523,39 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
 // ------------------------------------------------------------------------------------
 // launch wrappers (host side of this translation unit)
 // ------------------------------------------------------------------------------------
+// Opts the kernel into the device's full dynamic shared memory (needed above 48 KB) before
+// it is launched or queried for occupancy.
+template <int W, typename MapT>
+static cudaError_t ensure_smem_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kbest_kernel<W, MapT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)sizeof(TeamShared));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <int W, typename MapT>
 static cudaError_t launch_one(const KParams &p, int grid, int block, size_t smem,
                               cudaStream_t st)
 {
-    static bool attr_done[2] = {false, false};   // per process; one device per process here
-    auto fn = kbest_kernel<W, MapT>;
-    const int which = sizeof(MapT) == 1 ? 0 : 1;
-    if (!attr_done[which]) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             optin - (int)sizeof(TeamShared));
-        if (e != cudaSuccess) return e;
-        attr_done[which] = true;
-    }
-    fn<<<grid, block, smem, st>>>(p);
+    cudaError_t e = ensure_smem_attr<W, MapT>();
+    if (e != cudaSuccess) return e;
+    kbest_kernel<W, MapT><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 template <int W, typename MapT>
 static cudaError_t occupancy_one(int block, size_t smem, int *out)
 {
+    cudaError_t e = ensure_smem_attr<W, MapT>();
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_kernel<W, MapT>, block, smem);
 }
 
