@@ -92,6 +92,9 @@ struct TeamShared {
     int delcost;
     int cnt;
     int mx;
+    int maxb;     // largest histogram bucket touched at this level
+    int thr;      // bucket holding the K-th smallest PED (fast path)
+    int wmaxb[kMaxWarps];
     int wlt[kMaxWarps];
     int weq[kMaxWarps];
     unsigned long long wbest[kMaxWarps];
@@ -105,12 +108,30 @@ struct Regions {
     uint8_t *map0, *map1;
 };
 
+// A kept child is stored in the selection list as (parent slot << 11) | j, j = 0..n2.
+constexpr int kSelShift = 11;
+
+#ifdef FASTGED_PHASE_TIMERS
+// profiling builds only: cycles thread 0 of every team spends in each phase
+__device__ unsigned long long g_phase_cycles[8];
+#define PHASE_MARK(k)                                        \
+    do {                                                     \
+        if (threadIdx.x == 0) {                              \
+            const long long t_ = clock64();                  \
+            ph[k] += t_ - ph_last;                           \
+            ph_last = t_;                                    \
+        }                                                    \
+    } while (0)
+#else
+#define PHASE_MARK(k) do { } while (0)
+#endif
+
 // Exact fallback of the selection when the kept set reaches past the histogram window:
 // the K-th smallest PED is found by bisection over block-wide counts, the kept candidates
 // are compacted stably in enumeration order, then ranked by (PED, enumeration index).
 template <int W, typename MapT>
-__device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShared &S, int L, int stride,
-                             int newL, int lo)
+__device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShared &S, int L,
+                                             int stride, int newL, int lo)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x, NW = T >> 5;
@@ -145,7 +166,7 @@ __device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShare
     }
     const int thr = lo;
 
-    // per-warp counts of PED < thr and PED == thr over the warp's contiguous range
+    // per-warp counts of PED < thr and PED == thr over the warp's contiguous slot range
     const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
     const int c_lo = s_lo * stride, c_hi = s_hi * stride;
     int nlt = 0, neq = 0;
@@ -188,14 +209,15 @@ __device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShare
             const int pb = R.cand[R.tmp[b]];
             rank += (pb < pa) || (pb == pa && b < a);
         }
-        R.sel[rank] = ca;
+        const int s = ca / stride;
+        R.sel[rank] = (s << kSelShift) | (ca - s * stride);
         R.selped[rank] = pa;
     }
 }
 
 template <int W, typename MapT>
-__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, MapT> R, TeamShared &S,
-                           const int pair)
+__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, MapT> R,
+                                           TeamShared &S, const int pair)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x, NW = T >> 5;
@@ -212,8 +234,15 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
     const CostModel c = p.cost;
     const int hwin = p.hwin;
     const bool fold_ie = (c.eins == c.edel);
+    // small bitsets keep the target vertex's rows in registers for a whole level
+    constexpr bool HOIST = (W <= 2);
+    constexpr int HW = HOIST ? W : 1;
+#ifdef FASTGED_PHASE_TIMERS
+    long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long ph_last = clock64();
+#endif
 
-    // stage g2: transposed adjacency and label planes, vertex labels
+    // stage g2: transposed adjacency and label planes, vertex labels; clear the histogram
     {
         const uint64_t *adj2 = p.adj + m2.adj_off;
         for (int idx = tid; idx < W * n2; idx += T) {
@@ -228,9 +257,13 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
             }
         }
         for (int u = tid; u < n2; u += T) R.alpha2[u] = p.vlab[m2.lab_off + u];
+        for (int x = tid; x < hwin * NW; x += T) R.hist[x] = 0;
         // root node: empty lambda, R_V2 = V2, PED 0
         for (int w = tid; w < W; w += T) R.img0[w] = 0ull;
-        if (tid == 0) R.ped0[0] = 0;
+        if (tid == 0) {
+            R.ped0[0] = 0;
+            S.maxb = -1;
+        }
     }
     long long nevals = 0;
     int L = 1;
@@ -239,9 +272,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
     uint64_t *imgc = R.img0, *imgn = R.img1;
     int32_t *pedc = R.ped0, *pedn = R.ped1;
     __syncthreads();
+    PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
-
         // ---- S1 cost row + S2 per-node vectors -------------------------------------
         const uint64_t *row1 = p.adj + m1.adj_off + (int64_t)i * W1;
         const uint64_t *pl1 = p.planes + m1.plane_off + (int64_t)i * W1;
@@ -249,13 +282,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
         {
             const int a1 = p.vlab[m1.lab_off + i];
             for (int j = tid; j < n2; j += T) R.crow[j] = (R.alpha2[j] != a1) ? c.vsub : 0;
-            for (int x = tid; x < hwin * NW; x += T) R.hist[x] = 0;
-            if (tid == 0) {
-                int d = 0;
-                for (int w = 0; w < W1; ++w) d += __popcll(row1[w] & low_mask(i, w));
-                S.delcost = c.vdel + c.edel * d;   // v_i -> eps takes its edges to v_0..v_{i-1}
-                S.pbase = pedc[0];                 // kept list is sorted: slot 0 has the least PED
-            }
+            // clear the buckets the previous level touched
+            for (int x = tid; x < (S.maxb + 1) * NW; x += T) R.hist[x] = 0;
             for (int s = tid; s < L; s += T) {
                 uint64_t *Ps = R.P + (int64_t)s * W;
 #pragma unroll
@@ -283,66 +311,101 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
             }
         }
         __syncthreads();
+        if (tid == 0) {
+            int d = 0;
+            for (int w = 0; w < W1; ++w) d += __popcll(row1[w] & low_mask(i, w));
+            S.delcost = c.vdel + c.edel * d;   // v_i -> eps takes its edges to v_0..v_{i-1}
+            S.pbase = pedc[0];                 // kept list is sorted: slot 0 has the least PED
+        }
+        __syncthreads();
+        PHASE_MARK(1);
 
         // ---- S3 successor evaluation + per-warp PED histogram -----------------------
+        // lane <-> target vertex u_j (j = jb + lane); the warp walks its contiguous slots
         const int pbase = S.pbase, delcost = S.delcost;
         const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
-        const int c_lo = s_lo * stride, c_hi = s_hi * stride;
-        const int q32 = 32 / stride, r32 = 32 % stride;
         int32_t *hcol = R.hist + warp;
-        {
-            int s = s_lo + lane / stride, j = lane % stride;
-            for (int cb = c_lo; cb < c_hi; cb += 32) {
-                const int cc = cb + lane;
-                int ped = INT_MAX;
-                if (cc < c_hi) {
-                    if (j == n2) {
-                        ped = pedc[s] + delcost;
-                    } else {
-                        const uint64_t *im = imgc + (int64_t)s * W;
-                        if (!((im[j >> 6] >> (j & 63)) & 1ull)) {
-                            const uint64_t *Ps = R.P + (int64_t)s * W;
-                            int x = 0, y = 0, z = 0;
+        int wmaxb = -1;
+        for (int jb = 0; jb < stride; jb += 32) {
+            const int j = jb + lane;
+            const bool is_sub = j < n2, is_del = (j == n2);
+            uint64_t a[HW], l0[HW], l1[HW];
+            int cj = 0;
 #pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                const uint64_t a = R.a2t[w * N2S + j];
-                                const uint64_t ai = a & im[w];
-                                const uint64_t pw = Ps[w];
-                                if (fold_ie) {
-                                    x += __popcll(ai ^ pw);
+            for (int w = 0; w < HW; ++w) { a[w] = 0ull; l0[w] = 0ull; l1[w] = 0ull; }
+            if (is_sub) {
+                cj = R.crow[j];
+                if (HOIST) {
+#pragma unroll
+                    for (int w = 0; w < HW; ++w) {
+                        a[w] = R.a2t[w * N2S + j];
+                        if (B > 0) l0[w] = R.l2t[(0 * W + w) * N2S + j];
+                        if (B > 1) l1[w] = R.l2t[(1 * W + w) * N2S + j];
+                    }
+                }
+            }
+            const uint64_t jbit = 1ull << (j & 63);
+            const int jw = j >> 6;
+            for (int s = s_lo; s < s_hi; ++s) {
+                int ped = INT_MAX;
+                if (is_del) {
+                    ped = pedc[s] + delcost;
+                } else if (is_sub) {
+                    const uint64_t *im = imgc + (int64_t)s * W;
+                    if (!(im[jw] & jbit)) {
+                        const uint64_t *Ps = R.P + (int64_t)s * W;
+                        int x = 0, y = 0, z = 0;
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            const uint64_t aw = HOIST ? a[HOIST ? w : 0] : R.a2t[w * N2S + j];
+                            const uint64_t ai = aw & im[w];
+                            const uint64_t pw = Ps[w];
+                            if (fold_ie) {
+                                x += __popcll(ai ^ pw);
+                            } else {
+                                x += __popcll(ai & ~pw);
+                                y += __popcll(pw & ~aw);
+                            }
+                            if (B > 0) {
+                                uint64_t ld;
+                                if (HOIST && B <= 2) {
+                                    ld = R.PL[((int64_t)0 * KM + s) * W + w] ^ l0[HOIST ? w : 0];
+                                    if (B > 1)
+                                        ld |= R.PL[((int64_t)1 * KM + s) * W + w] ^ l1[HOIST ? w : 0];
                                 } else {
-                                    x += __popcll(ai & ~pw);
-                                    y += __popcll(pw & ~a);
-                                }
-                                if (B) {
-                                    uint64_t ld = 0ull;
+                                    ld = 0ull;
                                     for (int b = 0; b < B; ++b)
                                         ld |= R.PL[((int64_t)b * KM + s) * W + w] ^
                                               R.l2t[(b * W + w) * N2S + j];
-                                    z += __popcll(a & pw & ld);
                                 }
+                                z += __popcll(aw & pw & ld);
                             }
-                            ped = R.sbase[s] + R.crow[j] + c.eins * x + c.edel * y + c.esub * z;
                         }
+                        ped = R.sbase[s] + cj + c.eins * x + c.edel * y + c.esub * z;
                     }
-                    R.cand[cc] = ped;
                 }
+                if (j < stride) R.cand[s * stride + j] = ped;
                 int bkt = -1;
                 if (ped != INT_MAX) {
                     const int d = ped - pbase;
                     bkt = d < hwin - 1 ? d : hwin - 1;
+                    wmaxb = bkt > wmaxb ? bkt : wmaxb;
                 }
                 const unsigned mm = __match_any_sync(0xffffffffu, bkt);
                 if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
-                s += q32;
-                j += r32;
-                if (j >= stride) { j -= stride; ++s; }
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmaxb = max(wmaxb, __shfl_xor_sync(0xffffffffu, wmaxb, o));
+        if (lane == 0) S.wmaxb[warp] = wmaxb;
         __syncthreads();
+        PHASE_MARK(2);
 
         // ---- S4 selection: scan of the (bucket, warp) histogram ---------------------
-        for (int b = tid; b < hwin; b += T) {
+        int maxb = -1;
+        for (int w = 0; w < NW; ++w) maxb = max(maxb, S.wmaxb[w]);
+        const int nb = maxb + 1;   // >= 1: every node has a deletion child
+        for (int b = tid; b < nb; b += T) {
             int run = 0;
             for (int w = 0; w < NW; ++w) {
                 const int v = R.hist[b * NW + w];
@@ -353,11 +416,11 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
         }
         __syncthreads();
         if (warp == 0) {
-            const int per = (hwin + 31) >> 5;
+            const int per = (nb + 31) >> 5;
             int loc = 0;
             for (int k = 0; k < per; ++k) {
                 const int b = lane * per + k;
-                if (b < hwin) loc += R.bbase[b];
+                if (b < nb) loc += R.bbase[b];
             }
             int incl = loc;
 #pragma unroll
@@ -365,72 +428,97 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += v;
             }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int nl = min(K, total);
             int run = incl - loc;
             for (int k = 0; k < per; ++k) {
                 const int b = lane * per + k;
-                if (b < hwin) {
+                if (b < nb) {
                     const int v = R.bbase[b];
                     R.bbase[b] = run;
+                    if (run < nl && run + v >= nl) S.thr = b;   // exactly one bucket crosses
                     run += v;
                 }
             }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            __syncwarp();
             if (lane == 0) {
-                const int nl = min(K, total);
                 S.newL = nl;
-                S.fast = (R.bbase[hwin - 1] >= nl);   // the overflow bucket keeps nothing
+                S.maxb = maxb;
                 nevals += total;
             }
         }
         __syncthreads();
         const int newL = S.newL;
-        if (S.fast) {
-            // stable counting sort: position = #(smaller PED) + #(equal PED earlier)
-            for (int cb = c_lo; cb < c_hi; cb += 32) {
-                const int cc = cb + lane;
-                const int ped = cc < c_hi ? R.cand[cc] : INT_MAX;
-                int bkt = -1;
-                if (ped != INT_MAX && ped - pbase < hwin - 1) bkt = ped - pbase;
-                const unsigned mm = __match_any_sync(0xffffffffu, bkt);
-                if (bkt >= 0) {
-                    const int pos = R.bbase[bkt] + hcol[bkt * NW] + __popc(mm & lanemask_lt());
-                    if (pos < newL) {
-                        R.sel[pos] = cc;
-                        R.selped[pos] = ped;
+        const int thr = S.thr;
+        if (thr < hwin - 1) {
+            // stable counting sort restricted to buckets <= thr: position = #(smaller PED)
+            // + #(equal PED earlier in (slot, j) order)
+            for (int s = s_lo; s < s_hi; ++s) {
+                for (int jb = 0; jb < stride; jb += 32) {
+                    const int j = jb + lane;
+                    const int ped = j < stride ? R.cand[s * stride + j] : INT_MAX;
+                    int bkt = -1;
+                    if (ped != INT_MAX && ped - pbase <= thr) bkt = ped - pbase;
+                    if (__ballot_sync(0xffffffffu, bkt >= 0) == 0u) continue;
+                    const unsigned mm = __match_any_sync(0xffffffffu, bkt);
+                    if (bkt >= 0) {
+                        const int pos = R.bbase[bkt] + hcol[bkt * NW] + __popc(mm & lanemask_lt());
+                        if (pos < newL) {
+                            R.sel[pos] = (s << kSelShift) | j;
+                            R.selped[pos] = ped;
+                        }
                     }
+                    __syncwarp();
+                    if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
+                    __syncwarp();
                 }
-                __syncwarp();
-                if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
-                __syncwarp();
             }
         } else {
             select_exact<W, MapT>(R, S, L, stride, newL, pbase + hwin - 1);
         }
         __syncthreads();
+        PHASE_MARK(3);
 
         // ---- kept children, in key order (slot = rank) -----------------------------
         {
-            const int nw32 = (int)((i * (int)sizeof(MapT) + 3) >> 2);
-            for (int r = warp; r < newL; r += NW) {
-                const int cc = R.sel[r];
-                const int s = cc / stride, j = cc - s * stride;
-                const uint32_t *src = (const uint32_t *)(mapc + (int64_t)s * mrow);
-                uint32_t *dst = (uint32_t *)(mapn + (int64_t)r * mrow);
-                for (int t = lane; t < nw32; t += 32) dst[t] = src[t];
-                for (int w = lane; w < W; w += 32) {
-                    uint64_t v = imgc[(int64_t)s * W + w];
-                    if (j < n2 && (j >> 6) == w) v |= 1ull << (j & 63);
-                    imgn[(int64_t)r * W + w] = v;
-                }
-                __syncwarp();
-                if (lane == 0) {
+            const int nvec = (int)((i * (int)sizeof(MapT) + 15) >> 4);
+            if (mrow <= 128) {
+                for (int r = tid; r < newL; r += T) {
+                    const int v = R.sel[r];
+                    const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
+                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
+                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
+                    for (int t = 0; t < nvec; ++t) dst[t] = src[t];
                     ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        uint64_t x = imgc[(int64_t)s * W + w];
+                        if (j < n2 && (j >> 6) == w) x |= 1ull << (j & 63);
+                        imgn[(int64_t)r * W + w] = x;
+                    }
                     pedn[r] = R.selped[r];
+                }
+            } else {
+                for (int r = warp; r < newL; r += NW) {
+                    const int v = R.sel[r];
+                    const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
+                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
+                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
+                    for (int t = lane; t < nvec; t += 32) dst[t] = src[t];
+                    for (int w = lane; w < W; w += 32) {
+                        uint64_t x = imgc[(int64_t)s * W + w];
+                        if (j < n2 && (j >> 6) == w) x |= 1ull << (j & 63);
+                        imgn[(int64_t)r * W + w] = x;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
+                        pedn[r] = R.selped[r];
+                    }
                 }
             }
         }
         __syncthreads();
+        PHASE_MARK(4);
         { uint8_t *t = mapc; mapc = mapn; mapn = t; }
         { uint64_t *t = imgc; imgc = imgn; imgn = t; }
         { int32_t *t = pedc; pedc = pedn; pedn = t; }
@@ -477,7 +565,12 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
             om[k] = (v == DEL) ? -1 : (int32_t)v;
         }
         __syncthreads();
+        PHASE_MARK(5);
     }
+#ifdef FASTGED_PHASE_TIMERS
+    if (tid == 0)
+        for (int k = 0; k < 6; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
+#endif
 }
 
 template <int W, typename MapT>
@@ -599,3 +692,18 @@ cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
 size_t team_shared_static_bytes() { return sizeof(TeamShared); }
 
 }  // namespace fastged
+
+#ifdef FASTGED_PHASE_TIMERS
+// profiling builds only: reads (and optionally clears) the per-phase cycle counters
+extern "C" int fastged_debug_phase_cycles(unsigned long long *out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, fastged::g_phase_cycles, sizeof(unsigned long long) * 8) !=
+        cudaSuccess)
+        return -3;
+    if (reset) {
+        unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        cudaMemcpyToSymbol(fastged::g_phase_cycles, z, sizeof(z));
+    }
+    return 0;
+}
+#endif
