@@ -189,7 +189,10 @@ def ours(args):
     mm = F.marshal(w)
     g = F.FastGED(w.cost)
     plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options())
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the legacy default stream has handle 0, which the C ABI reads as
+    # "the plan's own stream"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     c_out = np.zeros(mm.n_pairs, np.int32)
     m_out = np.zeros(int(mm.map_off[-1]), np.int32)

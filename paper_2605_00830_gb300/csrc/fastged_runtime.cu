@@ -508,8 +508,11 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
 
 // Enqueues the device path of a batch: zero pools and queues, pack, one launch per class.
 int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk,
-                     cudaStream_t st, int *launches, cudaEvent_t t0, cudaEvent_t t1)
+                     cudaStream_t st, int *launches, cudaEvent_t t0, cudaEvent_t t1,
+                     bool capturing)
 {
+    // inside stream capture the timing events must become graph nodes
+    const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     int nl = 0;
     CK(cudaMemsetAsync(wk + b.woff_err, 0, 16, st));
     CK(cudaMemsetAsync(wk + b.woff_queue, 0, b.woff_scratch - b.woff_queue, st));
@@ -527,7 +530,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
         ++nl;
     }
     const int nc = (int)b.classes.size();
-    if (t0) CK(cudaEventRecordWithFlags(t0, st, cudaEventRecordExternal));
+    if (t0) CK(cudaEventRecordWithFlags(t0, st, evflag));
     if (b.opt.form == FASTGED_FORM_PLAIN) {
         // one launch per pair, in pair order, single team, on the caller's stream
         std::vector<int> cls(b.n_pairs), pos(b.n_pairs);
@@ -564,7 +567,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));
         }
     }
-    if (t1) CK(cudaEventRecordWithFlags(t1, st, cudaEventRecordExternal));
+    if (t1) CK(cudaEventRecordWithFlags(t1, st, evflag));
     if (launches) *launches = nl;
     return FASTGED_OK;
 }
@@ -666,7 +669,7 @@ extern "C" int fastged_plan_run(fastged_plan *p, void *stream)
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         int nl = 0;
-        int rc = enqueue(p->h, b, in, wk, p->stream, &nl, p->t0, p->t1);
+        int rc = enqueue(p->h, b, in, wk, p->stream, &nl, p->t0, p->t1, true);
         cudaError_t e = cudaStreamEndCapture(p->stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");

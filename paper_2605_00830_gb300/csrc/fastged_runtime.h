@@ -65,7 +65,8 @@ void clear_error();
 int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const fastged_options &opt, Batch &b);
 int enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk, cudaStream_t st,
-            int *launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+            int *launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr,
+            bool capturing = false);
 int finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *out_cost,
                    int32_t *out_mapping, int64_t *out_nevals);
 
