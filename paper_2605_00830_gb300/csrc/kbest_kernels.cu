@@ -624,12 +624,14 @@ static cudaError_t ensure_smem_attr()
     static bool done = false;
     if (done) return cudaSuccess;
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_kernel<W, MapT>);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kbest_kernel<W, MapT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)sizeof(TeamShared));
+                                 optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -689,7 +691,8 @@ cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
     return cudaGetLastError();
 }
 
-size_t team_shared_static_bytes() { return sizeof(TeamShared); }
+// upper bound of the kernels' static shared memory (the team's scalars)
+size_t team_shared_static_bytes() { return sizeof(TeamShared) + 256; }
 
 }  // namespace fastged
 
