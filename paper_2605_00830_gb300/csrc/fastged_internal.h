@@ -35,8 +35,9 @@ struct GraphMeta {
 };
 
 enum Region : int {
-    RG_HIST = 0, RG_BBASE, RG_CROW, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1,
-    RG_SEL, RG_SELPED, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CAND, RG_MAP0, RG_MAP1, RG_TMP,
+    RG_HIST = 0, RG_BBASE, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1,
+    RG_SEL, RG_SELPED, RG_FOFF, RG_KLIST, RG_KPED, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_FLIST,
+    RG_CAND, RG_MAP0, RG_MAP1,
     RG_COUNT
 };
 
@@ -47,6 +48,8 @@ struct Layout {
     int32_t n1max, n2max;      // largest graphs of the class
     int32_t n2s;               // row stride (elements) of the transposed g2 tables
     int32_t mrow;              // bytes per stored vertex map
+    int32_t fs;                // entries per free-vertex list (n2max + 1)
+    int32_t word_bytes;        // 4 or 8: bytes per bitset word
     int32_t B;                 // edge-label planes
     int64_t smem_bytes;        // dynamic shared memory per team
     int64_t slice_bytes;       // global scratch bytes per team

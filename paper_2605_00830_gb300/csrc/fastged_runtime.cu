@@ -25,9 +25,11 @@
 #include "fastged_runtime.h"
 
 namespace fastged {
-cudaError_t launch_kbest(int W, bool wide_map, const KParams &p, int grid, int block,
-                         size_t smem, cudaStream_t st);
-cudaError_t kbest_occupancy(int W, bool wide_map, int block, size_t smem, int *out);
+cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
+                         int block, size_t smem, cudaStream_t st);
+cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
+                            int *out);
+bool kbest_has_smem_variant(int W, bool wide, bool w32);
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
 }  // namespace fastged
@@ -192,37 +194,43 @@ static void plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     const int NW = block / 32;
     const int W = cp.W;
     const size_t msz = cp.wide ? 2 : 1;
+    const size_t wb = cp.w32 ? 4 : 8;
     L.kmax = cp.kmax;
     L.n1max = cp.n1max;
     L.n2max = cp.n2max;
     L.n2s = (int)align_up((size_t)std::max(cp.n2max, 1) + 1, 4);
     L.mrow = (int)align_up((size_t)std::max(cp.n1max, 1) * msz, 16);
+    L.fs = cp.n2max + 1;
+    L.word_bytes = (int)wb;
     L.B = B;
     size_t sz[RG_COUNT];
     const size_t km = (size_t)cp.kmax;
     sz[RG_HIST] = (size_t)kHistMax * NW * 4;
     sz[RG_BBASE] = (size_t)kHistMax * 4;
-    sz[RG_CROW] = (size_t)L.n2s * 4;
     sz[RG_ALPHA2] = (size_t)L.n2s * 4;
-    sz[RG_A2T] = (size_t)W * L.n2s * 8;
-    sz[RG_L2T] = (size_t)B * W * L.n2s * 8;
+    sz[RG_A2T] = (size_t)W * L.n2s * wb;
+    sz[RG_L2T] = (size_t)B * W * L.n2s * wb;
     sz[RG_SBASE] = km * 4;
     sz[RG_PED0] = km * 4;
     sz[RG_PED1] = km * 4;
     sz[RG_SEL] = km * 4;
     sz[RG_SELPED] = km * 4;
-    sz[RG_IMG0] = km * W * 8;
-    sz[RG_IMG1] = km * W * 8;
-    sz[RG_P] = km * W * 8;
-    sz[RG_PL] = (size_t)B * km * W * 8;
+    sz[RG_FOFF] = km * 4;
+    sz[RG_KLIST] = km * 4;
+    sz[RG_KPED] = km * 4;
+    sz[RG_IMG0] = km * W * wb;
+    sz[RG_IMG1] = km * W * wb;
+    sz[RG_P] = km * W * wb;
+    sz[RG_PL] = (size_t)B * km * W * wb;
+    sz[RG_FLIST] = km * (size_t)L.fs * msz;
     sz[RG_CAND] = km * ((size_t)cp.n2max + 1) * 4;
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
-    sz[RG_TMP] = km * 4;
-    static const int prio[RG_COUNT] = {RG_HIST, RG_BBASE, RG_CROW, RG_ALPHA2, RG_SBASE,
-                                       RG_PED0, RG_PED1, RG_SEL, RG_SELPED, RG_A2T,
-                                       RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CAND,
-                                       RG_MAP0, RG_MAP1, RG_TMP};
+    // shared memory is filled in order of access frequency; the rest goes to global scratch
+    static const int prio[RG_COUNT] = {RG_HIST, RG_BBASE, RG_ALPHA2, RG_SBASE, RG_PED0,
+                                       RG_PED1, RG_SEL, RG_SELPED, RG_FOFF, RG_KLIST, RG_KPED,
+                                       RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
+                                       RG_FLIST, RG_CAND, RG_MAP0, RG_MAP1};
     size_t s_used = 0, g_used = 0;
     L.smem_mask = 0;
     for (int k = 0; k < RG_COUNT; ++k) {
@@ -264,8 +272,10 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
         budget = std::min(max_dyn, per_sm / 2 - stat);    // keep two teams per SM
     }
     plan_layout(cp, B, block, budget);
+    cp.all_smem = cp.lay.slice_bytes == 0 && kbest_has_smem_variant(cp.W, cp.wide, cp.w32);
     int occ = 0;
-    cudaError_t e = kbest_occupancy(cp.W, cp.wide, block, (size_t)cp.lay.smem_bytes, &occ);
+    cudaError_t e = kbest_occupancy(cp.W, cp.wide, cp.w32, cp.all_smem, block,
+                                    (size_t)cp.lay.smem_bytes, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (occ < 1) return set_error(FASTGED_ERR_CUDA, "team does not fit on an SM");
     cp.block = block;
@@ -369,12 +379,14 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         mtot += g1.n;
         const int W = words_class(g2.n);
         const bool wide = g2.n >= 255;
-        const int key = (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0);
+        const bool w32 = g2.n <= 32;
+        const int key = w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0);
         if (cls_of[key] < 0) {
             cls_of[key] = (int)b.classes.size();
             ClassPlan cp;
             cp.W = W;
             cp.wide = wide || W >= 8;
+            cp.w32 = w32;
             b.classes.push_back(cp);
         }
         ClassPlan &cp = b.classes[cls_of[key]];
@@ -547,13 +559,13 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             p.order += pos[pr];
             p.n_order = 1;
             p.queue_head = qbase + pr;
-            CK(launch_kbest(cp.W, cp.wide, p, 1, cp.block, cp.smem, st));
+            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, 1, cp.block, cp.smem, st));
             ++nl;
         }
     } else if (nc == 1) {
         const ClassPlan &cp = b.classes[0];
         KParams p = make_params(h, b, 0, in, wk);
-        CK(launch_kbest(cp.W, cp.wide, p, cp.grid, cp.block, cp.smem, st));
+        CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, cp.grid, cp.block, cp.smem, st));
         ++nl;
     } else if (nc > 1) {
         CK(cudaEventRecord(h->ev[kMaxClasses], st));
@@ -561,7 +573,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             const ClassPlan &cp = b.classes[k];
             CK(cudaStreamWaitEvent(h->class_stream[k], h->ev[kMaxClasses], 0));
             KParams p = make_params(h, b, k, in, wk);
-            CK(launch_kbest(cp.W, cp.wide, p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
+            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
             ++nl;
             CK(cudaEventRecord(h->ev[k], h->class_stream[k]));
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));

@@ -87,29 +87,35 @@ __global__ void pack_kernel(const PackParams pp)
 struct TeamShared {
     int pair;
     int newL;
-    int fast;
     int pbase;
     int delcost;
     int cnt;
     int mx;
     int maxb;     // largest histogram bucket touched at this level
-    int thr;      // bucket holding the K-th smallest PED (fast path)
+    int thr;      // bucket holding the K-th smallest PED
     int wmaxb[kMaxWarps];
+    int wn[kMaxWarps];    // candidates each warp scored at this level
     int wlt[kMaxWarps];
     int weq[kMaxWarps];
     unsigned long long wbest[kMaxWarps];
 };
 
-template <int W, typename MapT>
+template <typename Word>
 struct Regions {
-    int32_t *hist, *bbase, *crow, *alpha2, *sbase, *sel, *selped, *tmp, *cand;
+    int32_t *hist, *bbase, *alpha2, *sbase, *sel, *selped, *foff, *klist, *kped, *cand;
     int32_t *ped0, *ped1;
-    uint64_t *a2t, *l2t, *img0, *img1, *P, *PL;
-    uint8_t *map0, *map1;
+    Word *a2t, *l2t, *img0, *img1, *P, *PL;
+    uint8_t *map0, *map1, *flist;
 };
 
 // A kept child is stored in the selection list as (parent slot << 11) | j, j = 0..n2.
 constexpr int kSelShift = 11;
+
+__device__ __forceinline__ int popcw(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int popcw(uint64_t x) { return __popcll(x); }
+
+// mask of lanes <= this lane
+__device__ __forceinline__ unsigned lanemask_le() { return 0xffffffffu >> (31 - (threadIdx.x & 31)); }
 
 #ifdef FASTGED_PHASE_TIMERS
 // profiling builds only: cycles thread 0 of every team spends in each phase
@@ -126,23 +132,70 @@ __device__ unsigned long long g_phase_cycles[8];
 #define PHASE_MARK(k) do { } while (0)
 #endif
 
-// Exact fallback of the selection when the kept set reaches past the histogram window:
-// the K-th smallest PED is found by bisection over block-wide counts, the kept candidates
-// are compacted stably in enumeration order, then ranked by (PED, enumeration index).
-template <int W, typename MapT>
-__device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShared &S, int L,
-                                             int stride, int newL, int lo)
+// Slot owning the candidate stored at index c: the last slot whose first candidate is at
+// or before c (first-candidate offsets increase with the slot).
+template <typename Word>
+__device__ __forceinline__ int slot_of(const Regions<Word> &R, int L, int c)
 {
+    int lo = 0, hi = L - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (R.foff[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stable compaction of the kept successors of this warp, in enumeration order: every
+// candidate with PED < T, and the first q with PED == T counted over the whole team.
+// keep_before / eq_before: kept / tied candidates of the warps before this one.
+template <typename Word>
+__device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, int n, int T,
+                                            int q, int keep_before, int eq_before)
+{
+    const int lane = threadIdx.x & 31;
+    for (int kb = 0; kb < n; kb += 32) {
+        const int k = kb + lane;
+        const int v = k < n ? R.cand[base + k] : INT_MAX;
+        if (__ballot_sync(0xffffffffu, v <= T) == 0u) continue;
+        const bool is_eq = (v == T);
+        const unsigned eqb = __ballot_sync(0xffffffffu, is_eq);
+        const int eq_rank = eq_before + __popc(eqb & lanemask_lt());
+        const bool keep = (v < T) || (is_eq && eq_rank < q);
+        const unsigned kbm = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = keep_before + __popc(kbm & lanemask_lt());
+            R.klist[pos] = base + k;
+            R.kped[pos] = v;
+        }
+        keep_before += __popc(kbm);
+        eq_before += __popc(eqb);
+    }
+}
+
+// Exact selection used when the kept set reaches past the histogram window: the K-th
+// smallest PED is found by bisection over team-wide counts, the kept candidates are
+// compacted stably, and ranked by (PED, enumeration order).
+template <typename MapT, typename Word>
+__device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
+                                          const int32_t *foff, const uint8_t *flist_b,
+                                          int32_t *sel, int32_t *selped, TeamShared &S, int L,
+                                          int stride, int n2, int newL, int lo)
+{
+    Regions<Word> R;
+    R.cand = cand;
+    R.klist = klist;
+    R.kped = kped;
+    R.foff = (int32_t *)foff;
+    R.flist = (uint8_t *)flist_b;
+    R.sel = sel;
+    R.selped = selped;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x, NW = T >> 5;
-    const int N = L * stride;
+    const int s_lo = (warp * L) / NW;
+    const int base = s_lo * stride, n = S.wn[warp];
 
-    // largest valid PED
     int mx = 0;
-    for (int c = tid; c < N; c += T) {
-        const int v = R.cand[c];
-        if (v != INT_MAX && v > mx) mx = v;
-    }
+    for (int k = lane; k < n; k += 32) mx = max(mx, R.cand[base + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -155,7 +208,7 @@ __device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShare
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int c = tid; c < N; c += T) cnt += (R.cand[c] <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (R.cand[base + k] <= mid);
         cnt = warp_sum(cnt);
         __syncthreads();
         if (tid == 0) S.cnt = 0;
@@ -165,60 +218,49 @@ __device__ __forceinline__ void select_exact(const Regions<W, MapT> R, TeamShare
         if (S.cnt >= newL) hi = mid; else lo = mid + 1;
     }
     const int thr = lo;
-
-    // per-warp counts of PED < thr and PED == thr over the warp's contiguous slot range
-    const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
-    const int c_lo = s_lo * stride, c_hi = s_hi * stride;
     int nlt = 0, neq = 0;
-    for (int cb = c_lo; cb < c_hi; cb += 32) {
-        const int cc = cb + lane;
-        const int v = cc < c_hi ? R.cand[cc] : INT_MAX;
-        nlt += __popc(__ballot_sync(0xffffffffu, v < thr));
-        neq += __popc(__ballot_sync(0xffffffffu, v == thr));
+    for (int k = lane; k < n; k += 32) {
+        const int v = R.cand[base + k];
+        nlt += (v < thr);
+        neq += (v == thr);
     }
+    nlt = warp_sum(nlt);
+    neq = warp_sum(neq);
     if (lane == 0) { S.wlt[warp] = nlt; S.weq[warp] = neq; }
     __syncthreads();
     int lt_all = 0;
     for (int w = 0; w < NW; ++w) lt_all += S.wlt[w];
-    const int q = newL - lt_all;   // ties at thr that are kept, first in enumeration order
+    const int q = newL - lt_all;
     int keep_before = 0, eq_before = 0;
     for (int w = 0; w < warp; ++w) {
-        const int take = min(max(q - eq_before, 0), S.weq[w]);
-        keep_before += S.wlt[w] + take;
+        keep_before += S.wlt[w];
         eq_before += S.weq[w];
     }
-    for (int cb = c_lo; cb < c_hi; cb += 32) {
-        const int cc = cb + lane;
-        const int v = cc < c_hi ? R.cand[cc] : INT_MAX;
-        const bool is_eq = (v == thr);
-        const unsigned eqb = __ballot_sync(0xffffffffu, is_eq);
-        const int eq_rank = eq_before + __popc(eqb & lanemask_lt());
-        const bool keep = (v < thr) || (is_eq && eq_rank < q);
-        const unsigned kb = __ballot_sync(0xffffffffu, keep);
-        if (keep) R.tmp[keep_before + __popc(kb & lanemask_lt())] = cc;
-        keep_before += __popc(kb);
-        eq_before += __popc(eqb);
-    }
+    keep_before += min(q, eq_before);
+    compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before);
     __syncthreads();
-    // rank by (PED, enumeration index); tmp is already in enumeration order
+    // rank by (PED, enumeration order); klist is in enumeration order
     for (int a = tid; a < newL; a += T) {
-        const int ca = R.tmp[a];
-        const int pa = R.cand[ca];
+        const int pa = R.kped[a];
         int rank = 0;
         for (int b = 0; b < newL; ++b) {
-            const int pb = R.cand[R.tmp[b]];
+            const int pb = R.kped[b];
             rank += (pb < pa) || (pb == pa && b < a);
         }
-        const int s = ca / stride;
-        R.sel[rank] = (s << kSelShift) | (ca - s * stride);
+        const int c = R.klist[a];
+        const int s = slot_of<Word>(R, L, c);
+        const int r = c - R.foff[s];
+        const int j = (int)((const MapT *)R.flist)[(int64_t)s * stride + r];
+        R.sel[rank] = (s << kSelShift) | j;
         R.selped[rank] = pa;
     }
 }
 
-template <int W, typename MapT>
-__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, MapT> R,
+template <int W, typename MapT, typename Word>
+__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word> R,
                                            TeamShared &S, const int pair)
 {
+    constexpr int WB = 8 * (int)sizeof(Word);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x, NW = T >> 5;
     const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
@@ -229,14 +271,12 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
     const int N2S = p.lay.n2s;
     const int KM = p.lay.kmax;
     const int64_t mrow = p.lay.mrow;
-    const int stride = n2 + 1;
+    const int stride = n2 + 1;   // successors of one node: n2 substitutions + the deletion
     const MapT DEL = (MapT)~(MapT)0;
     const CostModel c = p.cost;
     const int hwin = p.hwin;
     const bool fold_ie = (c.eins == c.edel);
-    // small bitsets keep the target vertex's rows in registers for a whole level
-    constexpr bool HOIST = (W <= 2);
-    constexpr int HW = HOIST ? W : 1;
+    MapT *flist = (MapT *)R.flist;
 #ifdef FASTGED_PHASE_TIMERS
     long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long ph_last = clock64();
@@ -247,19 +287,22 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
         const uint64_t *adj2 = p.adj + m2.adj_off;
         for (int idx = tid; idx < W * n2; idx += T) {
             const int w = idx / n2, u = idx - w * n2;
-            R.a2t[w * N2S + u] = (w < W2) ? adj2[(int64_t)u * W2 + w] : 0ull;
+            const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
+            R.a2t[w * N2S + u] = (w64 < W2) ? (Word)(adj2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
         }
         for (int b = 0; b < B; ++b) {
             const uint64_t *pl2 = p.planes + m2.plane_off + (int64_t)b * n2 * W2;
             for (int idx = tid; idx < W * n2; idx += T) {
                 const int w = idx / n2, u = idx - w * n2;
-                R.l2t[(b * W + w) * N2S + u] = (w < W2) ? pl2[(int64_t)u * W2 + w] : 0ull;
+                const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
+                R.l2t[(b * W + w) * N2S + u] =
+                    (w64 < W2) ? (Word)(pl2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
             }
         }
         for (int u = tid; u < n2; u += T) R.alpha2[u] = p.vlab[m2.lab_off + u];
         for (int x = tid; x < hwin * NW; x += T) R.hist[x] = 0;
         // root node: empty lambda, R_V2 = V2, PED 0
-        for (int w = tid; w < W; w += T) R.img0[w] = 0ull;
+        for (int w = tid; w < W; w += T) R.img0[w] = (Word)0;
         if (tid == 0) {
             R.ped0[0] = 0;
             S.maxb = -1;
@@ -269,27 +312,43 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
     int L = 1;
     // current / next beam buffers, swapped after every level
     uint8_t *mapc = R.map0, *mapn = R.map1;
-    uint64_t *imgc = R.img0, *imgn = R.img1;
+    Word *imgc = R.img0, *imgn = R.img1;
     int32_t *pedc = R.ped0, *pedn = R.ped1;
     __syncthreads();
     PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
-        // ---- S1 cost row + S2 per-node vectors -------------------------------------
         const uint64_t *row1 = p.adj + m1.adj_off + (int64_t)i * W1;
         const uint64_t *pl1 = p.planes + m1.plane_off + (int64_t)i * W1;
         const int64_t pl1_step = (int64_t)n1 * W1;
-        {
-            const int a1 = p.vlab[m1.lab_off + i];
-            for (int j = tid; j < n2; j += T) R.crow[j] = (R.alpha2[j] != a1) ? c.vsub : 0;
-            // clear the buckets the previous level touched
-            for (int x = tid; x < (S.maxb + 1) * NW; x += T) R.hist[x] = 0;
-            for (int s = tid; s < L; s += T) {
-                uint64_t *Ps = R.P + (int64_t)s * W;
+        const int a1 = p.vlab[m1.lab_off + i];
+        int deg = 0;   // neighbours of v_i among v_0..v_{i-1}
+        for (int w = lane; w < W1; w += 32) deg += __popcll(row1[w] & low_mask(i, w));
+        deg = warp_sum(deg);
+        const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes those edges with it
+        const int pbase = pedc[0];                   // the kept list is sorted: slot 0 is least
+        const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
+        const int base = s_lo * stride;              // this warp's candidate storage
+        int32_t *hcol = R.hist + warp;
+        // clear the buckets of this warp's column that the previous level touched
+        for (int b = lane; b <= S.maxb; b += 32) hcol[b * NW] = 0;
+
+        // ---- S1 + S2 per-node vectors, free lists, and S3 evaluation -----------------
+        int kw = 0;      // candidates of this warp so far
+        int wmaxb = -1;
+        for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
+            const int ng = min(32, s_hi - g0);
+            const int s = g0 + lane;
+            const bool act = lane < ng;
+            int cnt = 0;
+            if (act) {
+                // S2: P = images of the substituted g1 neighbours of v_i (and their edge-label
+                // planes moved to the image positions); dcnt = deleted neighbours
+                Word *Ps = R.P + (int64_t)s * W;
 #pragma unroll
-                for (int w = 0; w < W; ++w) Ps[w] = 0ull;
+                for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
                 for (int b = 0; b < B; ++b)
-                    for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = 0ull;
+                    for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
                 const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
                 int dcnt = 0;
                 for (int w = 0; w < W1; ++w) {
@@ -299,8 +358,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
                         bits &= bits - 1ull;
                         const MapT phi = ms[w * 64 + t];
                         if (phi == DEL) { ++dcnt; continue; }
-                        const int pw = (int)phi >> 6;
-                        const uint64_t pb = 1ull << ((int)phi & 63);
+                        const int pw = (int)phi / WB;
+                        const Word pb = (Word)1 << ((int)phi % WB);
                         Ps[pw] |= pb;
                         for (int b = 0; b < B; ++b)
                             if ((pl1[b * pl1_step + w] >> t) & 1ull)
@@ -308,98 +367,97 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
                     }
                 }
                 R.sbase[s] = pedc[s] + c.edel * dcnt;
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int d = 0;
-            for (int w = 0; w < W1; ++w) d += __popcll(row1[w] & low_mask(i, w));
-            S.delcost = c.vdel + c.edel * d;   // v_i -> eps takes its edges to v_0..v_{i-1}
-            S.pbase = pedc[0];                 // kept list is sorted: slot 0 has the least PED
-        }
-        __syncthreads();
-        PHASE_MARK(1);
-
-        // ---- S3 successor evaluation + per-warp PED histogram -----------------------
-        // lane <-> target vertex u_j (j = jb + lane); the warp walks its contiguous slots
-        const int pbase = S.pbase, delcost = S.delcost;
-        const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
-        int32_t *hcol = R.hist + warp;
-        int wmaxb = -1;
-        for (int jb = 0; jb < stride; jb += 32) {
-            const int j = jb + lane;
-            const bool is_sub = j < n2, is_del = (j == n2);
-            uint64_t a[HW], l0[HW], l1[HW];
-            int cj = 0;
+                // free g2 vertices (R_V2) in increasing order, then the deletion
+                MapT *fl = flist + (int64_t)s * stride;
+                const Word *im = imgc + (int64_t)s * W;
 #pragma unroll
-            for (int w = 0; w < HW; ++w) { a[w] = 0ull; l0[w] = 0ull; l1[w] = 0ull; }
-            if (is_sub) {
-                cj = R.crow[j];
-                if (HOIST) {
-#pragma unroll
-                    for (int w = 0; w < HW; ++w) {
-                        a[w] = R.a2t[w * N2S + j];
-                        if (B > 0) l0[w] = R.l2t[(0 * W + w) * N2S + j];
-                        if (B > 1) l1[w] = R.l2t[(1 * W + w) * N2S + j];
+                for (int w = 0; w < W; ++w) {
+                    Word x = ~im[w];
+                    const int lim = n2 - w * WB;
+                    if (lim < WB) x &= lim > 0 ? (((Word)1 << lim) - (Word)1) : (Word)0;
+                    while (x) {
+                        const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
+                        x &= x - (Word)1;
+                        fl[cnt++] = (MapT)(w * WB + t);
                     }
                 }
+                fl[cnt++] = (MapT)n2;   // entry n2 stands for v_i -> eps
             }
-            const uint64_t jbit = 1ull << (j & 63);
-            const int jw = j >> 6;
-            for (int s = s_lo; s < s_hi; ++s) {
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - cnt;
+            const int gtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (act) R.foff[s] = base + kw + excl;
+            __syncwarp();
+
+            // S3: lanes walk the group's successors in enumeration order, 32 at a time
+            int before = 0;
+            for (int kb = 0; kb < gtot; kb += 32) {
+                const int k = kb + lane;
+                const int d = excl - kb;
+                const unsigned bit = (act && d >= 0 && d < 32) ? (1u << d) : 0u;
+                const unsigned M = __reduce_or_sync(0xffffffffu, bit);
+                const int srel = min(before + __popc(M & lanemask_le()) - 1, 31);
+                before += __popc(M);
+                const int st = __shfl_sync(0xffffffffu, excl, max(srel, 0));
                 int ped = INT_MAX;
-                if (is_del) {
-                    ped = pedc[s] + delcost;
-                } else if (is_sub) {
-                    const uint64_t *im = imgc + (int64_t)s * W;
-                    if (!(im[jw] & jbit)) {
-                        const uint64_t *Ps = R.P + (int64_t)s * W;
+                if (k < gtot) {
+                    const int sc = g0 + srel;
+                    const int j = (int)flist[(int64_t)sc * stride + (k - st)];
+                    if (j == n2) {
+                        ped = pedc[sc] + delcost;
+                    } else {
+                        const Word *im = imgc + (int64_t)sc * W;
+                        const Word *Ps = R.P + (int64_t)sc * W;
                         int x = 0, y = 0, z = 0;
 #pragma unroll
                         for (int w = 0; w < W; ++w) {
-                            const uint64_t aw = HOIST ? a[HOIST ? w : 0] : R.a2t[w * N2S + j];
-                            const uint64_t ai = aw & im[w];
-                            const uint64_t pw = Ps[w];
+                            const Word aw = R.a2t[w * N2S + j];
+                            const Word ai = aw & im[w];
+                            const Word pw = Ps[w];
                             if (fold_ie) {
-                                x += __popcll(ai ^ pw);
+                                x += popcw((Word)(ai ^ pw));
                             } else {
-                                x += __popcll(ai & ~pw);
-                                y += __popcll(pw & ~aw);
+                                x += popcw((Word)(ai & ~pw));
+                                y += popcw((Word)(pw & ~aw));
                             }
                             if (B > 0) {
-                                uint64_t ld;
-                                if (HOIST && B <= 2) {
-                                    ld = R.PL[((int64_t)0 * KM + s) * W + w] ^ l0[HOIST ? w : 0];
-                                    if (B > 1)
-                                        ld |= R.PL[((int64_t)1 * KM + s) * W + w] ^ l1[HOIST ? w : 0];
-                                } else {
-                                    ld = 0ull;
-                                    for (int b = 0; b < B; ++b)
-                                        ld |= R.PL[((int64_t)b * KM + s) * W + w] ^
-                                              R.l2t[(b * W + w) * N2S + j];
-                                }
-                                z += __popcll(aw & pw & ld);
+                                Word ld = (Word)0;
+                                for (int b = 0; b < B; ++b)
+                                    ld |= R.PL[((int64_t)b * KM + sc) * W + w] ^
+                                          R.l2t[(b * W + w) * N2S + j];
+                                z += popcw((Word)(aw & pw & ld));
                             }
                         }
-                        ped = R.sbase[s] + cj + c.eins * x + c.edel * y + c.esub * z;
+                        const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
+                        ped = R.sbase[sc] + cv + c.eins * x + c.edel * y + c.esub * z;
                     }
+                    R.cand[base + kw + k] = ped;
                 }
-                if (j < stride) R.cand[s * stride + j] = ped;
                 int bkt = -1;
                 if (ped != INT_MAX) {
-                    const int d = ped - pbase;
-                    bkt = d < hwin - 1 ? d : hwin - 1;
+                    const int dd = ped - pbase;
+                    bkt = dd < hwin - 1 ? dd : hwin - 1;
                     wmaxb = bkt > wmaxb ? bkt : wmaxb;
                 }
                 const unsigned mm = __match_any_sync(0xffffffffu, bkt);
                 if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
             }
+            kw += gtot;
+            __syncwarp();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wmaxb = max(wmaxb, __shfl_xor_sync(0xffffffffu, wmaxb, o));
-        if (lane == 0) S.wmaxb[warp] = wmaxb;
+        if (lane == 0) {
+            S.wmaxb[warp] = wmaxb;
+            S.wn[warp] = kw;
+        }
         __syncthreads();
-        PHASE_MARK(2);
+        PHASE_MARK(1);
 
         // ---- S4 selection: scan of the (bucket, warp) histogram ---------------------
         int maxb = -1;
@@ -450,33 +508,41 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
         const int newL = S.newL;
         const int thr = S.thr;
         if (thr < hwin - 1) {
-            // stable counting sort restricted to buckets <= thr: position = #(smaller PED)
-            // + #(equal PED earlier in (slot, j) order)
-            for (int s = s_lo; s < s_hi; ++s) {
-                for (int jb = 0; jb < stride; jb += 32) {
-                    const int j = jb + lane;
-                    const int ped = j < stride ? R.cand[s * stride + j] : INT_MAX;
-                    int bkt = -1;
-                    if (ped != INT_MAX && ped - pbase <= thr) bkt = ped - pbase;
-                    if (__ballot_sync(0xffffffffu, bkt >= 0) == 0u) continue;
-                    const unsigned mm = __match_any_sync(0xffffffffu, bkt);
-                    if (bkt >= 0) {
-                        const int pos = R.bbase[bkt] + hcol[bkt * NW] + __popc(mm & lanemask_lt());
-                        if (pos < newL) {
-                            R.sel[pos] = (s << kSelShift) | j;
-                            R.selped[pos] = ped;
-                        }
+            // kept = every candidate below the threshold bucket and the first q of it
+            const int q = newL - R.bbase[thr];
+            int lt_before = 0;
+            for (int b = lane; b < thr; b += 32) lt_before += R.hist[b * NW + warp];
+            lt_before = warp_sum(lt_before);
+            const int eq_before = R.hist[thr * NW + warp];
+            compact_kept<Word>(R, base, kw, pbase + thr, q, lt_before + min(q, eq_before),
+                               eq_before);
+            __syncthreads();
+            // stable counting sort of the kept list by PED (single warp; klist is in
+            // enumeration order, so equal PEDs keep (parent slot, j) order)
+            if (warp == 0) {
+                for (int xb = 0; xb < newL; xb += 32) {
+                    const int x = xb + lane;
+                    const int v = x < newL ? R.kped[x] - pbase : -1;
+                    const unsigned mm = __match_any_sync(0xffffffffu, v);
+                    if (v >= 0) {
+                        const int pos = R.bbase[v] + __popc(mm & lanemask_lt());
+                        const int cidx = R.klist[x];
+                        const int sl = slot_of<Word>(R, L, cidx);
+                        const int j = (int)flist[(int64_t)sl * stride + (cidx - R.foff[sl])];
+                        R.sel[pos] = (sl << kSelShift) | j;
+                        R.selped[pos] = v + pbase;
                     }
                     __syncwarp();
-                    if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
+                    if (v >= 0 && lane == __ffs(mm) - 1) R.bbase[v] += __popc(mm);
                     __syncwarp();
                 }
             }
         } else {
-            select_exact<W, MapT>(R, S, L, stride, newL, pbase + hwin - 1);
+            select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.foff, R.flist, R.sel, R.selped,
+                                     S, L, stride, n2, newL, pbase + hwin - 1);
         }
         __syncthreads();
-        PHASE_MARK(3);
+        PHASE_MARK(2);
 
         // ---- kept children, in key order (slot = rank) -----------------------------
         {
@@ -491,8 +557,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
                     ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        uint64_t x = imgc[(int64_t)s * W + w];
-                        if (j < n2 && (j >> 6) == w) x |= 1ull << (j & 63);
+                        Word x = imgc[(int64_t)s * W + w];
+                        if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
                         imgn[(int64_t)r * W + w] = x;
                     }
                     pedn[r] = R.selped[r];
@@ -505,8 +571,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
                     uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
                     for (int t = lane; t < nvec; t += 32) dst[t] = src[t];
                     for (int w = lane; w < W; w += 32) {
-                        uint64_t x = imgc[(int64_t)s * W + w];
-                        if (j < n2 && (j >> 6) == w) x |= 1ull << (j & 63);
+                        Word x = imgc[(int64_t)s * W + w];
+                        if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
                         imgn[(int64_t)r * W + w] = x;
                     }
                     __syncwarp();
@@ -518,9 +584,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
             }
         }
         __syncthreads();
-        PHASE_MARK(4);
+        PHASE_MARK(3);
         { uint8_t *t = mapc; mapc = mapn; mapn = t; }
-        { uint64_t *t = imgc; imgc = imgn; imgn = t; }
+        { Word *t = imgc; imgc = imgn; imgn = t; }
         { int32_t *t = pedc; pedc = pedn; pedn = t; }
         L = newL;
     }
@@ -529,16 +595,16 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
     {
         unsigned long long best = ~0ull;
         for (int s = warp; s < L; s += NW) {
-            const uint64_t *im = imgc + (int64_t)s * W;
+            const Word *im = imgc + (int64_t)s * W;
             int acc = 0;
             for (int u = lane; u < n2; u += 32) {
-                if ((im[u >> 6] >> (u & 63)) & 1ull) {
+                if ((im[u / WB] >> (u % WB)) & (Word)1) {
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc += __popcll(R.a2t[w * N2S + u] & im[w]);
+                    for (int w = 0; w < W; ++w) acc += popcw((Word)(R.a2t[w * N2S + u] & im[w]));
                 }
             }
             int nimg = 0;
-            for (int w = lane; w < W; w += 32) nimg += __popcll(im[w]);
+            for (int w = lane; w < W; w += 32) nimg += popcw(im[w]);
             acc = warp_sum(acc);
             nimg = warp_sum(nimg);
             // g2 edges with both ends used were counted twice in acc
@@ -565,43 +631,47 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<W, Ma
             om[k] = (v == DEL) ? -1 : (int32_t)v;
         }
         __syncthreads();
-        PHASE_MARK(5);
+        PHASE_MARK(4);
     }
 #ifdef FASTGED_PHASE_TIMERS
     if (tid == 0)
-        for (int k = 0; k < 6; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
+        for (int k = 0; k < 5; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
 #endif
 }
 
-template <int W, typename MapT>
+// SM: every region lives in shared memory (addresses then stay in the shared window)
+template <int W, typename MapT, typename Word, bool SM>
 __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ TeamShared S;
     uint8_t *gs = p.gscratch + (int64_t)blockIdx.x * p.lay.slice_bytes;
     auto base = [&](int r) -> uint8_t * {
+        if (SM) return smem + p.lay.off[r];
         return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
     };
-    Regions<W, MapT> R;
+    Regions<Word> R;
     R.hist = (int32_t *)base(RG_HIST);
     R.bbase = (int32_t *)base(RG_BBASE);
-    R.crow = (int32_t *)base(RG_CROW);
     R.alpha2 = (int32_t *)base(RG_ALPHA2);
-    R.a2t = (uint64_t *)base(RG_A2T);
-    R.l2t = (uint64_t *)base(RG_L2T);
+    R.a2t = (Word *)base(RG_A2T);
+    R.l2t = (Word *)base(RG_L2T);
     R.sbase = (int32_t *)base(RG_SBASE);
     R.ped0 = (int32_t *)base(RG_PED0);
     R.ped1 = (int32_t *)base(RG_PED1);
     R.sel = (int32_t *)base(RG_SEL);
     R.selped = (int32_t *)base(RG_SELPED);
-    R.img0 = (uint64_t *)base(RG_IMG0);
-    R.img1 = (uint64_t *)base(RG_IMG1);
-    R.P = (uint64_t *)base(RG_P);
-    R.PL = (uint64_t *)base(RG_PL);
+    R.foff = (int32_t *)base(RG_FOFF);
+    R.klist = (int32_t *)base(RG_KLIST);
+    R.kped = (int32_t *)base(RG_KPED);
+    R.img0 = (Word *)base(RG_IMG0);
+    R.img1 = (Word *)base(RG_IMG1);
+    R.P = (Word *)base(RG_P);
+    R.PL = (Word *)base(RG_PL);
+    R.flist = base(RG_FLIST);
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
     R.map1 = base(RG_MAP1);
-    R.tmp = (int32_t *)base(RG_TMP);
 
     for (;;) {
         if (threadIdx.x == 0) S.pair = atomicAdd(p.queue_head, 1);
@@ -609,7 +679,7 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
         const int qi = S.pair;
         __syncthreads();
         if (qi >= p.n_order) break;
-        solve_pair<W, MapT>(p, R, S, p.order[qi]);
+        solve_pair<W, MapT, Word>(p, R, S, p.order[qi]);
     }
 }
 
@@ -618,7 +688,7 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
 // ------------------------------------------------------------------------------------
 // Opts the kernel into the device's full dynamic shared memory (needed above 48 KB) before
 // it is launched or queried for occupancy.
-template <int W, typename MapT>
+template <int W, typename MapT, typename Word, bool SM>
 static cudaError_t ensure_smem_attr()
 {
     static bool done = false;
@@ -628,56 +698,72 @@ static cudaError_t ensure_smem_attr()
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_kernel<W, MapT>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_kernel<W, MapT, Word, SM>);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kbest_kernel<W, MapT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(kbest_kernel<W, MapT, Word, SM>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-template <int W, typename MapT>
+template <int W, typename MapT, typename Word, bool SM>
 static cudaError_t launch_one(const KParams &p, int grid, int block, size_t smem,
                               cudaStream_t st)
 {
-    cudaError_t e = ensure_smem_attr<W, MapT>();
+    cudaError_t e = ensure_smem_attr<W, MapT, Word, SM>();
     if (e != cudaSuccess) return e;
-    kbest_kernel<W, MapT><<<grid, block, smem, st>>>(p);
+    kbest_kernel<W, MapT, Word, SM><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int W, typename MapT>
+template <int W, typename MapT, typename Word, bool SM>
 static cudaError_t occupancy_one(int block, size_t smem, int *out)
 {
-    cudaError_t e = ensure_smem_attr<W, MapT>();
+    cudaError_t e = ensure_smem_attr<W, MapT, Word, SM>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_kernel<W, MapT>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_kernel<W, MapT, Word, SM>,
+                                                         block, smem);
 }
 
-#define FASTGED_DISPATCH(W_, wide, CALL)                                          \
-    do {                                                                          \
-        switch (W_) {                                                             \
-        case 1: if (wide) return CALL(1, uint16_t); else return CALL(1, uint8_t); \
-        case 2: if (wide) return CALL(2, uint16_t); else return CALL(2, uint8_t); \
-        case 4: if (wide) return CALL(4, uint16_t); else return CALL(4, uint8_t); \
-        case 8: return CALL(8, uint16_t);                                         \
-        case 16: return CALL(16, uint16_t);                                       \
-        default: return cudaErrorInvalidValue;                                    \
-        }                                                                         \
+// size class -> template instance. 16-bit maps only occur with W >= 4 (n2 >= 255), and the
+// all-shared-memory variant is built for bitsets of up to 4 words.
+#define FASTGED_DISPATCH(W_, wide, w32, sm, CALL)                                        \
+    do {                                                                                 \
+        if (sm) {                                                                        \
+            if (w32) return CALL(1, uint8_t, uint32_t, true);                            \
+            if (W_ == 1 && !wide) return CALL(1, uint8_t, uint64_t, true);               \
+            if (W_ == 2 && !wide) return CALL(2, uint8_t, uint64_t, true);               \
+            if (W_ == 4 && !wide) return CALL(4, uint8_t, uint64_t, true);               \
+        }                                                                                \
+        if (w32) return CALL(1, uint8_t, uint32_t, false);                               \
+        switch (W_) {                                                                    \
+        case 1: if (!wide) return CALL(1, uint8_t, uint64_t, false); break;              \
+        case 2: if (!wide) return CALL(2, uint8_t, uint64_t, false); break;              \
+        case 4: if (wide) return CALL(4, uint16_t, uint64_t, false);                     \
+                else return CALL(4, uint8_t, uint64_t, false);                           \
+        case 8: return CALL(8, uint16_t, uint64_t, false);                               \
+        case 16: return CALL(16, uint16_t, uint64_t, false);                             \
+        default: break;                                                                  \
+        }                                                                                \
+        return cudaErrorInvalidValue;                                                    \
     } while (0)
 
-cudaError_t launch_kbest(int W, bool wide_map, const KParams &p, int grid, int block,
-                         size_t smem, cudaStream_t st)
+bool kbest_has_smem_variant(int W, bool wide, bool w32) { return w32 || (W <= 4 && !wide); }
+
+cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
+                         int block, size_t smem, cudaStream_t st)
 {
-#define CALL_LAUNCH(w, M) launch_one<w, M>(p, grid, block, smem, st)
-    FASTGED_DISPATCH(W, wide_map, CALL_LAUNCH);
+#define CALL_LAUNCH(w, M, Wd, S_) launch_one<w, M, Wd, S_>(p, grid, block, smem, st)
+    FASTGED_DISPATCH(W, wide_map, w32, sm, CALL_LAUNCH);
 #undef CALL_LAUNCH
 }
 
-cudaError_t kbest_occupancy(int W, bool wide_map, int block, size_t smem, int *out)
+cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
+                            int *out)
 {
-#define CALL_OCC(w, M) occupancy_one<w, M>(block, smem, out)
-    FASTGED_DISPATCH(W, wide_map, CALL_OCC);
+#define CALL_OCC(w, M, Wd, S_) occupancy_one<w, M, Wd, S_>(block, smem, out)
+    FASTGED_DISPATCH(W, wide_map, w32, sm, CALL_OCC);
 #undef CALL_OCC
 }
 
