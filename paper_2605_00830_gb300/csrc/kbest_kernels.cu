@@ -367,21 +367,27 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     }
                 }
                 R.sbase[s] = pedc[s] + c.edel * dcnt;
-                // free g2 vertices (R_V2) in increasing order, then the deletion
-                MapT *fl = flist + (int64_t)s * stride;
                 const Word *im = imgc + (int64_t)s * W;
+                int used = 0;
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    Word x = ~im[w];
-                    const int lim = n2 - w * WB;
-                    if (lim < WB) x &= lim > 0 ? (((Word)1 << lim) - (Word)1) : (Word)0;
-                    while (x) {
-                        const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
-                        x &= x - (Word)1;
-                        fl[cnt++] = (MapT)(w * WB + t);
-                    }
+                for (int w = 0; w < W; ++w) used += popcw(im[w]);
+                cnt = n2 - used + 1;   // free g2 vertices (R_V2) and the deletion
+            }
+            // free lists: the free g2 vertices of each slot in increasing order, then n2 for
+            // v_i -> eps (lanes over vertices, ballot compaction)
+            for (int t = 0; t < ng; ++t) {
+                const int st_ = g0 + t;
+                const Word *im = imgc + (int64_t)st_ * W;
+                MapT *fl = flist + (int64_t)st_ * stride;
+                int pos = 0;
+                for (int jb = 0; jb < n2; jb += 32) {
+                    const int j = jb + lane;
+                    const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
+                    const unsigned bal = __ballot_sync(0xffffffffu, fr);
+                    if (fr) fl[pos + __popc(bal & lanemask_lt())] = (MapT)j;
+                    pos += __popc(bal);
                 }
-                fl[cnt++] = (MapT)n2;   // entry n2 stands for v_i -> eps
+                if (lane == 0) fl[pos] = (MapT)n2;
             }
             int incl = cnt;
 #pragma unroll
@@ -393,6 +399,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int gtot = __shfl_sync(0xffffffffu, incl, 31);
             if (act) R.foff[s] = base + kw + excl;
             __syncwarp();
+            PHASE_MARK(5);
 
             // S3: lanes walk the group's successors in enumeration order, 32 at a time
             int before = 0;
@@ -463,14 +470,19 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int maxb = -1;
         for (int w = 0; w < NW; ++w) maxb = max(maxb, S.wmaxb[w]);
         const int nb = maxb + 1;   // >= 1: every node has a deletion child
-        for (int b = tid; b < nb; b += T) {
-            int run = 0;
-            for (int w = 0; w < NW; ++w) {
-                const int v = R.hist[b * NW + w];
-                R.hist[b * NW + w] = run;
-                run += v;
+        // per bucket, exclusive prefix over warps (segments of NW lanes) and bucket totals
+        for (int x = tid; x < ((nb * NW + 31) & ~31); x += T) {
+            const int b = x / NW, w = x - b * NW;
+            const int v = b < nb ? R.hist[x] : 0;
+            int incl = v;
+            for (int o = 1; o < NW; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (w >= o) incl += y;
             }
-            R.bbase[b] = run;
+            if (b < nb) {
+                R.hist[x] = incl - v;
+                if (w == NW - 1) R.bbase[b] = incl;
+            }
         }
         __syncthreads();
         if (warp == 0) {
@@ -508,34 +520,34 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         const int newL = S.newL;
         const int thr = S.thr;
         if (thr < hwin - 1) {
-            // kept = every candidate below the threshold bucket and the first q of it
+            // kept = every candidate below the threshold bucket and the first q of it, in
+            // (PED, parent slot, j) order: position = #(smaller PED) + #(equal PED earlier);
+            // hist[b][warp] now holds the bucket-b candidates of the warps before this one
             const int q = newL - R.bbase[thr];
-            int lt_before = 0;
-            for (int b = lane; b < thr; b += 32) lt_before += R.hist[b * NW + warp];
-            lt_before = warp_sum(lt_before);
-            const int eq_before = R.hist[thr * NW + warp];
-            compact_kept<Word>(R, base, kw, pbase + thr, q, lt_before + min(q, eq_before),
-                               eq_before);
-            __syncthreads();
-            // stable counting sort of the kept list by PED (single warp; klist is in
-            // enumeration order, so equal PEDs keep (parent slot, j) order)
-            if (warp == 0) {
-                for (int xb = 0; xb < newL; xb += 32) {
-                    const int x = xb + lane;
-                    const int v = x < newL ? R.kped[x] - pbase : -1;
-                    const unsigned mm = __match_any_sync(0xffffffffu, v);
-                    if (v >= 0) {
-                        const int pos = R.bbase[v] + __popc(mm & lanemask_lt());
-                        const int cidx = R.klist[x];
-                        const int sl = slot_of<Word>(R, L, cidx);
-                        const int j = (int)flist[(int64_t)sl * stride + (cidx - R.foff[sl])];
-                        R.sel[pos] = (sl << kSelShift) | j;
+            for (int kb = 0; kb < kw; kb += 32) {
+                const int k = kb + lane;
+                const int v = k < kw ? R.cand[base + k] - pbase : INT_MAX;
+                if (__ballot_sync(0xffffffffu, v <= thr) == 0u) continue;
+                const int bkt = v <= thr ? v : -1;
+                const unsigned mm = __match_any_sync(0xffffffffu, bkt);
+                if (bkt >= 0) {
+                    const int rank = hcol[bkt * NW] + __popc(mm & lanemask_lt());
+                    if (bkt < thr || rank < q) {
+                        const int pos = R.bbase[bkt] + rank;
+                        // decode the parent slot and target vertex of candidate base + k
+                        int lo = s_lo, hi = s_hi - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (R.foff[mid] <= base + k) lo = mid; else hi = mid - 1;
+                        }
+                        const int j = (int)flist[(int64_t)lo * stride + (base + k - R.foff[lo])];
+                        R.sel[pos] = (lo << kSelShift) | j;
                         R.selped[pos] = v + pbase;
                     }
-                    __syncwarp();
-                    if (v >= 0 && lane == __ffs(mm) - 1) R.bbase[v] += __popc(mm);
-                    __syncwarp();
                 }
+                __syncwarp();
+                if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
+                __syncwarp();
             }
         } else {
             select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.foff, R.flist, R.sel, R.selped,
@@ -635,7 +647,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     }
 #ifdef FASTGED_PHASE_TIMERS
     if (tid == 0)
-        for (int k = 0; k < 5; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
+        for (int k = 0; k < 6; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
 #endif
 }
 
