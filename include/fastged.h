@@ -97,7 +97,7 @@ typedef struct {
                              /* 1: complete every successor of the last level (never worse)   */
     const int32_t *k_per_pair; /* optional host array [n_pairs] of per-pair K (1..K); NULL =  */
                              /* the K argument for every pair                                 */
-    int32_t hist_window;     /* 0 = default. Width (2..256) of the PED histogram window of    */
+    int32_t hist_window;     /* 0 = default. Width (2..32) of the PED histogram window of     */
                              /* the selection step; small values force its exact fallback     */
                              /* path (a testing knob; results do not depend on it)            */
     int32_t block_threads;   /* 0 = autotuned; else 128, 256 or 512 threads per team          */

@@ -18,7 +18,7 @@
 namespace fastged {
 
 constexpr int kMaxWords = 16;       // 1024 vertices
-constexpr int kHistMax = 256;       // PED histogram buckets allocated per team
+constexpr int kHistMax = 32;        // PED histogram buckets (one per lane)
 constexpr int kMaxB = 8;            // edge-label bit-planes (labels 0..255)
 constexpr int kMaxWarps = 16;       // 512 threads per team
 
@@ -35,11 +35,13 @@ struct GraphMeta {
 };
 
 enum Region : int {
-    RG_HIST = 0, RG_BBASE, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1,
-    RG_SEL, RG_SELPED, RG_FOFF, RG_KLIST, RG_KPED, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_FLIST,
+    RG_HIST = 0, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1, RG_SEL, RG_SELPED,
+    RG_KLIST, RG_KPED, RG_NOFF, RG_NBR, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CSLOT, RG_CJ,
     RG_CAND, RG_MAP0, RG_MAP1,
     RG_COUNT
 };
+
+
 
 struct Layout {
     int64_t off[RG_COUNT];     // byte offset inside shared memory or the global slice
@@ -48,7 +50,7 @@ struct Layout {
     int32_t n1max, n2max;      // largest graphs of the class
     int32_t n2s;               // row stride (elements) of the transposed g2 tables
     int32_t mrow;              // bytes per stored vertex map
-    int32_t fs;                // entries per free-vertex list (n2max + 1)
+    int32_t fs;                // successors per node at most (n2max + 1)
     int32_t word_bytes;        // 4 or 8: bytes per bitset word
     int32_t B;                 // edge-label planes
     int64_t smem_bytes;        // dynamic shared memory per team

@@ -205,8 +205,8 @@ static void plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     L.B = B;
     size_t sz[RG_COUNT];
     const size_t km = (size_t)cp.kmax;
+    const size_t ncand = km * ((size_t)cp.n2max + 1);
     sz[RG_HIST] = (size_t)kHistMax * NW * 4;
-    sz[RG_BBASE] = (size_t)kHistMax * 4;
     sz[RG_ALPHA2] = (size_t)L.n2s * 4;
     sz[RG_A2T] = (size_t)W * L.n2s * wb;
     sz[RG_L2T] = (size_t)B * W * L.n2s * wb;
@@ -215,22 +215,24 @@ static void plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_PED1] = km * 4;
     sz[RG_SEL] = km * 4;
     sz[RG_SELPED] = km * 4;
-    sz[RG_FOFF] = km * 4;
     sz[RG_KLIST] = km * 4;
     sz[RG_KPED] = km * 4;
+    sz[RG_NOFF] = ((size_t)cp.n1max + 1) * 4;
+    sz[RG_NBR] = (size_t)std::max(cp.m1max, 1) * 4;
     sz[RG_IMG0] = km * W * wb;
     sz[RG_IMG1] = km * W * wb;
     sz[RG_P] = km * W * wb;
     sz[RG_PL] = (size_t)B * km * W * wb;
-    sz[RG_FLIST] = km * (size_t)L.fs * msz;
-    sz[RG_CAND] = km * ((size_t)cp.n2max + 1) * 4;
+    sz[RG_CSLOT] = ncand * 2;
+    sz[RG_CJ] = ncand * msz;
+    sz[RG_CAND] = ncand * 4;
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
     // shared memory is filled in order of access frequency; the rest goes to global scratch
-    static const int prio[RG_COUNT] = {RG_HIST, RG_BBASE, RG_ALPHA2, RG_SBASE, RG_PED0,
-                                       RG_PED1, RG_SEL, RG_SELPED, RG_FOFF, RG_KLIST, RG_KPED,
+    static const int prio[RG_COUNT] = {RG_HIST, RG_ALPHA2, RG_SBASE, RG_PED0, RG_PED1,
+                                       RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_NOFF,
                                        RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
-                                       RG_FLIST, RG_CAND, RG_MAP0, RG_MAP1};
+                                       RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1};
     size_t s_used = 0, g_used = 0;
     L.smem_mask = 0;
     for (int k = 0; k < RG_COUNT; ++k) {
@@ -391,6 +393,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         }
         ClassPlan &cp = b.classes[cls_of[key]];
         cp.n1max = std::max(cp.n1max, g1.n);
+        cp.m1max = std::max(cp.m1max, g1.m);
         cp.n2max = std::max(cp.n2max, g2.n);
         cp.kmax = std::max(cp.kmax, kp);
         cp.order.push_back(p);

@@ -86,15 +86,10 @@ __global__ void pack_kernel(const PackParams pp)
 // ------------------------------------------------------------------------------------
 struct TeamShared {
     int pair;
-    int newL;
-    int pbase;
-    int delcost;
     int cnt;
     int mx;
-    int maxb;     // largest histogram bucket touched at this level
-    int thr;      // bucket holding the K-th smallest PED
-    int wmaxb[kMaxWarps];
-    int wn[kMaxWarps];    // candidates each warp scored at this level
+    int wmin[kMaxWarps];  // least successor PED each warp scored at this level
+    int wn[kMaxWarps];    // successors each warp scored at this level
     int wlt[kMaxWarps];
     int weq[kMaxWarps];
     unsigned long long wbest[kMaxWarps];
@@ -102,10 +97,11 @@ struct TeamShared {
 
 template <typename Word>
 struct Regions {
-    int32_t *hist, *bbase, *alpha2, *sbase, *sel, *selped, *foff, *klist, *kped, *cand;
+    int32_t *hist, *alpha2, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
     int32_t *ped0, *ped1;
     Word *a2t, *l2t, *img0, *img1, *P, *PL;
-    uint8_t *map0, *map1, *flist;
+    uint16_t *cslot;
+    uint8_t *map0, *map1, *cj;
 };
 
 // A kept child is stored in the selection list as (parent slot << 11) | j, j = 0..n2.
@@ -113,9 +109,6 @@ constexpr int kSelShift = 11;
 
 __device__ __forceinline__ int popcw(uint32_t x) { return __popc(x); }
 __device__ __forceinline__ int popcw(uint64_t x) { return __popcll(x); }
-
-// mask of lanes <= this lane
-__device__ __forceinline__ unsigned lanemask_le() { return 0xffffffffu >> (31 - (threadIdx.x & 31)); }
 
 #ifdef FASTGED_PHASE_TIMERS
 // profiling builds only: cycles thread 0 of every team spends in each phase
@@ -132,17 +125,14 @@ __device__ unsigned long long g_phase_cycles[8];
 #define PHASE_MARK(k) do { } while (0)
 #endif
 
-// Slot owning the candidate stored at index c: the last slot whose first candidate is at
-// or before c (first-candidate offsets increase with the slot).
-template <typename Word>
-__device__ __forceinline__ int slot_of(const Regions<Word> &R, int L, int c)
+// Lanes of the warp whose 5-bit value equals `v`, among the lanes in `valid`, given the
+// ballots b[k] of bit k of every lane's value.
+__device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsigned b[5], int v)
 {
-    int lo = 0, hi = L - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (R.foff[mid] <= c) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+    unsigned m = valid;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m &= ((v >> k) & 1) ? b[k] : ~b[k];
+    return m;
 }
 
 // Stable compaction of the kept successors of this warp, in enumeration order: every
@@ -177,25 +167,21 @@ __device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, i
 // compacted stably, and ranked by (PED, enumeration order).
 template <typename MapT, typename Word>
 __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
-                                          const int32_t *foff, const uint8_t *flist_b,
+                                          const uint16_t *cslot, const uint8_t *cj_b,
                                           int32_t *sel, int32_t *selped, TeamShared &S, int L,
-                                          int stride, int n2, int newL, int lo)
+                                          int stride, int newL, int lo)
 {
-    Regions<Word> R;
-    R.cand = cand;
-    R.klist = klist;
-    R.kped = kped;
-    R.foff = (int32_t *)foff;
-    R.flist = (uint8_t *)flist_b;
-    R.sel = sel;
-    R.selped = selped;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x, NW = T >> 5;
     const int s_lo = (warp * L) / NW;
     const int base = s_lo * stride, n = S.wn[warp];
+    Regions<Word> R;
+    R.cand = cand;
+    R.klist = klist;
+    R.kped = kped;
 
     int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, R.cand[base + k]);
+    for (int k = lane; k < n; k += 32) mx = max(mx, cand[base + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -208,7 +194,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (R.cand[base + k] <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (cand[base + k] <= mid);
         cnt = warp_sum(cnt);
         __syncthreads();
         if (tid == 0) S.cnt = 0;
@@ -220,7 +206,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     const int thr = lo;
     int nlt = 0, neq = 0;
     for (int k = lane; k < n; k += 32) {
-        const int v = R.cand[base + k];
+        const int v = cand[base + k];
         nlt += (v < thr);
         neq += (v == thr);
     }
@@ -240,19 +226,17 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before);
     __syncthreads();
     // rank by (PED, enumeration order); klist is in enumeration order
+    const MapT *cj = (const MapT *)cj_b;
     for (int a = tid; a < newL; a += T) {
-        const int pa = R.kped[a];
+        const int pa = kped[a];
         int rank = 0;
         for (int b = 0; b < newL; ++b) {
-            const int pb = R.kped[b];
+            const int pb = kped[b];
             rank += (pb < pa) || (pb == pa && b < a);
         }
-        const int c = R.klist[a];
-        const int s = slot_of<Word>(R, L, c);
-        const int r = c - R.foff[s];
-        const int j = (int)((const MapT *)R.flist)[(int64_t)s * stride + r];
-        R.sel[rank] = (s << kSelShift) | j;
-        R.selped[rank] = pa;
+        const int c = klist[a];
+        sel[rank] = ((int)cslot[c] << kSelShift) | (int)cj[c];
+        selped[rank] = pa;
     }
 }
 
@@ -271,18 +255,22 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const int N2S = p.lay.n2s;
     const int KM = p.lay.kmax;
     const int64_t mrow = p.lay.mrow;
-    const int stride = n2 + 1;   // successors of one node: n2 substitutions + the deletion
+    const int stride = n2 + 1;   // successors of one node at most: n2 substitutions + deletion
     const MapT DEL = (MapT)~(MapT)0;
     const CostModel c = p.cost;
-    const int hwin = p.hwin;
+    const int hwin = p.hwin;     // buckets 0..hwin-2 hold one PED each, hwin-1 the rest
     const bool fold_ie = (c.eins == c.edel);
-    MapT *flist = (MapT *)R.flist;
+    MapT *cjv = (MapT *)R.cj;
+    // lane-constant masks: lane b answers for histogram bucket b
+    unsigned lanebit[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lanebit[k] = ((lane >> k) & 1) ? 0xffffffffu : 0u;
 #ifdef FASTGED_PHASE_TIMERS
     long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long ph_last = clock64();
 #endif
 
-    // stage g2: transposed adjacency and label planes, vertex labels; clear the histogram
+    // stage g2: transposed adjacency and label planes, vertex labels; g1 degrees
     {
         const uint64_t *adj2 = p.adj + m2.adj_off;
         for (int idx = tid; idx < W * n2; idx += T) {
@@ -300,12 +288,52 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             }
         }
         for (int u = tid; u < n2; u += T) R.alpha2[u] = p.vlab[m2.lab_off + u];
-        for (int x = tid; x < hwin * NW; x += T) R.hist[x] = 0;
+        // number of neighbours v_k of v_i with k < i
+        for (int v = tid; v < n1; v += T) {
+            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+            int d = 0;
+            for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
+            R.noff[v + 1] = d;
+        }
         // root node: empty lambda, R_V2 = V2, PED 0
         for (int w = tid; w < W; w += T) R.img0[w] = (Word)0;
         if (tid == 0) {
             R.ped0[0] = 0;
-            S.maxb = -1;
+            R.noff[0] = 0;
+        }
+    }
+    __syncthreads();
+    // prior-neighbour lists of g1: nbr[noff[i] .. noff[i+1]) = k | (edge label << 16)
+    if (warp == 0) {
+        int carry = 0;
+        for (int v0 = 0; v0 < n1; v0 += 32) {
+            const int v = v0 + lane;
+            const int d = v < n1 ? R.noff[v + 1] : 0;
+            int incl = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (v < n1) R.noff[v + 1] = carry + incl;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    for (int v = tid; v < n1; v += T) {
+        const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+        const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
+        const int64_t pstep = (int64_t)n1 * W1;
+        int o = R.noff[v];
+        for (int w = 0; w < W1; ++w) {
+            uint64_t bits = row[w] & low_mask(v, w);
+            while (bits) {
+                const int t = __ffsll((long long)bits) - 1;
+                bits &= bits - 1ull;
+                int lab = 0;
+                for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
+                R.nbr[o++] = (w * 64 + t) | (lab << 16);
+            }
         }
     }
     long long nevals = 0;
@@ -318,32 +346,23 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
-        const uint64_t *row1 = p.adj + m1.adj_off + (int64_t)i * W1;
-        const uint64_t *pl1 = p.planes + m1.plane_off + (int64_t)i * W1;
-        const int64_t pl1_step = (int64_t)n1 * W1;
         const int a1 = p.vlab[m1.lab_off + i];
-        int deg = 0;   // neighbours of v_i among v_0..v_{i-1}
-        for (int w = lane; w < W1; w += 32) deg += __popcll(row1[w] & low_mask(i, w));
-        deg = warp_sum(deg);
-        const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes those edges with it
-        const int pbase = pedc[0];                   // the kept list is sorted: slot 0 is least
+        const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
+        const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes its edges to v_0..v_{i-1}
         const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
-        const int base = s_lo * stride;              // this warp's candidate storage
-        int32_t *hcol = R.hist + warp;
-        // clear the buckets of this warp's column that the previous level touched
-        for (int b = lane; b <= S.maxb; b += 32) hcol[b * NW] = 0;
+        const int base = s_lo * stride;              // this warp's successor storage
 
-        // ---- S1 + S2 per-node vectors, free lists, and S3 evaluation -----------------
-        int kw = 0;      // candidates of this warp so far
-        int wmaxb = -1;
+        // ---- S1 + S2 per-node vectors, successor lists, S3 evaluation ----------------
+        int kw = 0;          // successors of this warp so far
+        int wmin = INT_MAX;
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
             const bool act = lane < ng;
             int cnt = 0;
             if (act) {
-                // S2: P = images of the substituted g1 neighbours of v_i (and their edge-label
-                // planes moved to the image positions); dcnt = deleted neighbours
+                // S2: P = images of the substituted g1 neighbours of v_i (their edge labels in
+                // bit-planes PL at the image positions); dcnt = deleted neighbours
                 Word *Ps = R.P + (int64_t)s * W;
 #pragma unroll
                 for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
@@ -351,20 +370,15 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
                 const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
                 int dcnt = 0;
-                for (int w = 0; w < W1; ++w) {
-                    uint64_t bits = row1[w] & low_mask(i, w);
-                    while (bits) {
-                        const int t = __ffsll((long long)bits) - 1;
-                        bits &= bits - 1ull;
-                        const MapT phi = ms[w * 64 + t];
-                        if (phi == DEL) { ++dcnt; continue; }
-                        const int pw = (int)phi / WB;
-                        const Word pb = (Word)1 << ((int)phi % WB);
-                        Ps[pw] |= pb;
-                        for (int b = 0; b < B; ++b)
-                            if ((pl1[b * pl1_step + w] >> t) & 1ull)
-                                R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
-                    }
+                for (int t = 0; t < deg; ++t) {
+                    const int e = R.nbr[n0 + t];
+                    const MapT phi = ms[e & 0xffff];
+                    if (phi == DEL) { ++dcnt; continue; }
+                    const int pw = (int)phi / WB;
+                    const Word pb = (Word)1 << ((int)phi % WB);
+                    Ps[pw] |= pb;
+                    for (int b = 0; b < B; ++b)
+                        if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
                 }
                 R.sbase[s] = pedc[s] + c.edel * dcnt;
                 const Word *im = imgc + (int64_t)s * W;
@@ -372,22 +386,6 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #pragma unroll
                 for (int w = 0; w < W; ++w) used += popcw(im[w]);
                 cnt = n2 - used + 1;   // free g2 vertices (R_V2) and the deletion
-            }
-            // free lists: the free g2 vertices of each slot in increasing order, then n2 for
-            // v_i -> eps (lanes over vertices, ballot compaction)
-            for (int t = 0; t < ng; ++t) {
-                const int st_ = g0 + t;
-                const Word *im = imgc + (int64_t)st_ * W;
-                MapT *fl = flist + (int64_t)st_ * stride;
-                int pos = 0;
-                for (int jb = 0; jb < n2; jb += 32) {
-                    const int j = jb + lane;
-                    const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
-                    const unsigned bal = __ballot_sync(0xffffffffu, fr);
-                    if (fr) fl[pos + __popc(bal & lanemask_lt())] = (MapT)j;
-                    pos += __popc(bal);
-                }
-                if (lane == 0) fl[pos] = (MapT)n2;
             }
             int incl = cnt;
 #pragma unroll
@@ -397,24 +395,40 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             }
             const int excl = incl - cnt;
             const int gtot = __shfl_sync(0xffffffffu, incl, 31);
-            if (act) R.foff[s] = base + kw + excl;
+            // successor ids in enumeration order: for each node the free g2 vertices in
+            // increasing order, then n2 for v_i -> eps (lanes over vertices, ballot compaction)
+            for (int t = 0; t < ng; ++t) {
+                const int st_ = g0 + t;
+                const Word *im = imgc + (int64_t)st_ * W;
+                const int o0 = base + kw + __shfl_sync(0xffffffffu, excl, t);
+                int pos = 0;
+                for (int jb = 0; jb < n2; jb += 32) {
+                    const int j = jb + lane;
+                    const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
+                    const unsigned bal = __ballot_sync(0xffffffffu, fr);
+                    if (fr) {
+                        const int idx = o0 + pos + __popc(bal & lanemask_lt());
+                        R.cslot[idx] = (uint16_t)st_;
+                        cjv[idx] = (MapT)j;
+                    }
+                    pos += __popc(bal);
+                }
+                if (lane == 0) {
+                    R.cslot[o0 + pos] = (uint16_t)st_;
+                    cjv[o0 + pos] = (MapT)n2;
+                }
+            }
             __syncwarp();
             PHASE_MARK(5);
 
-            // S3: lanes walk the group's successors in enumeration order, 32 at a time
-            int before = 0;
+            // S3: 32 successors at a time, in enumeration order
             for (int kb = 0; kb < gtot; kb += 32) {
                 const int k = kb + lane;
-                const int d = excl - kb;
-                const unsigned bit = (act && d >= 0 && d < 32) ? (1u << d) : 0u;
-                const unsigned M = __reduce_or_sync(0xffffffffu, bit);
-                const int srel = min(before + __popc(M & lanemask_le()) - 1, 31);
-                before += __popc(M);
-                const int st = __shfl_sync(0xffffffffu, excl, max(srel, 0));
-                int ped = INT_MAX;
                 if (k < gtot) {
-                    const int sc = g0 + srel;
-                    const int j = (int)flist[(int64_t)sc * stride + (k - st)];
+                    const int idx = base + kw + k;
+                    const int sc = R.cslot[idx];
+                    const int j = (int)cjv[idx];
+                    int ped;
                     if (j == n2) {
                         ped = pedc[sc] + delcost;
                     } else {
@@ -443,115 +457,96 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
                         ped = R.sbase[sc] + cv + c.eins * x + c.edel * y + c.esub * z;
                     }
-                    R.cand[base + kw + k] = ped;
+                    R.cand[idx] = ped;
+                    wmin = ped < wmin ? ped : wmin;
                 }
-                int bkt = -1;
-                if (ped != INT_MAX) {
-                    const int dd = ped - pbase;
-                    bkt = dd < hwin - 1 ? dd : hwin - 1;
-                    wmaxb = bkt > wmaxb ? bkt : wmaxb;
-                }
-                const unsigned mm = __match_any_sync(0xffffffffu, bkt);
-                if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
             }
             kw += gtot;
             __syncwarp();
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wmaxb = max(wmaxb, __shfl_xor_sync(0xffffffffu, wmaxb, o));
+        for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
         if (lane == 0) {
-            S.wmaxb[warp] = wmaxb;
+            S.wmin[warp] = wmin;
             S.wn[warp] = kw;
         }
         __syncthreads();
         PHASE_MARK(1);
 
-        // ---- S4 selection: scan of the (bucket, warp) histogram ---------------------
-        int maxb = -1;
-        for (int w = 0; w < NW; ++w) maxb = max(maxb, S.wmaxb[w]);
-        const int nb = maxb + 1;   // >= 1: every node has a deletion child
-        // per bucket, exclusive prefix over warps (segments of NW lanes) and bucket totals
-        for (int x = tid; x < ((nb * NW + 31) & ~31); x += T) {
-            const int b = x / NW, w = x - b * NW;
-            const int v = b < nb ? R.hist[x] : 0;
-            int incl = v;
-            for (int o = 1; o < NW; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (w >= o) incl += y;
-            }
-            if (b < nb) {
-                R.hist[x] = incl - v;
-                if (w == NW - 1) R.bbase[b] = incl;
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const int per = (nb + 31) >> 5;
-            int loc = 0;
-            for (int k = 0; k < per; ++k) {
-                const int b = lane * per + k;
-                if (b < nb) loc += R.bbase[b];
-            }
-            int incl = loc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int nl = min(K, total);
-            int run = incl - loc;
-            for (int k = 0; k < per; ++k) {
-                const int b = lane * per + k;
-                if (b < nb) {
-                    const int v = R.bbase[b];
-                    R.bbase[b] = run;
-                    if (run < nl && run + v >= nl) S.thr = b;   // exactly one bucket crosses
-                    run += v;
-                }
-            }
-            if (lane == 0) {
-                S.newL = nl;
-                S.maxb = maxb;
-                nevals += total;
-            }
-        }
-        __syncthreads();
-        const int newL = S.newL;
-        const int thr = S.thr;
-        if (thr < hwin - 1) {
-            // kept = every candidate below the threshold bucket and the first q of it, in
-            // (PED, parent slot, j) order: position = #(smaller PED) + #(equal PED earlier);
-            // hist[b][warp] now holds the bucket-b candidates of the warps before this one
-            const int q = newL - R.bbase[thr];
+        // ---- S4 selection ---------------------------------------------------------
+        // histogram of PED - pmin over this warp's successors (ballot counting: lane b
+        // keeps the count of bucket b; the last bucket collects every PED past the window)
+        int pmin = INT_MAX;
+        for (int w = 0; w < NW; ++w) pmin = min(pmin, S.wmin[w]);
+        {
+            int hreg = 0;
             for (int kb = 0; kb < kw; kb += 32) {
                 const int k = kb + lane;
-                const int v = k < kw ? R.cand[base + k] - pbase : INT_MAX;
-                if (__ballot_sync(0xffffffffu, v <= thr) == 0u) continue;
-                const int bkt = v <= thr ? v : -1;
-                const unsigned mm = __match_any_sync(0xffffffffu, bkt);
-                if (bkt >= 0) {
-                    const int rank = hcol[bkt * NW] + __popc(mm & lanemask_lt());
-                    if (bkt < thr || rank < q) {
-                        const int pos = R.bbase[bkt] + rank;
-                        // decode the parent slot and target vertex of candidate base + k
-                        int lo = s_lo, hi = s_hi - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (R.foff[mid] <= base + k) lo = mid; else hi = mid - 1;
-                        }
-                        const int j = (int)flist[(int64_t)lo * stride + (base + k - R.foff[lo])];
-                        R.sel[pos] = (lo << kSelShift) | j;
-                        R.selped[pos] = v + pbase;
-                    }
+                const bool valid = k < kw;
+                const int d = valid ? min(R.cand[base + k] - pmin, hwin - 1) : 0;
+                const unsigned V = __ballot_sync(0xffffffffu, valid);
+                unsigned bb[5];
+#pragma unroll
+                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1);
+                unsigned m = V;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
+                hreg += __popc(m);
+            }
+            R.hist[lane * NW + warp] = hreg;
+        }
+        __syncthreads();
+        // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
+        // and the bucket-b successors of the warps before this one
+        int tot = 0, mine = 0;
+        for (int w = 0; w < NW; ++w) {
+            const int v = R.hist[lane * NW + w];
+            tot += v;
+            mine += (w < warp) ? v : 0;
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int bexcl = incl - tot;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int newL = min(K, total);
+        // the bucket where the cumulative count reaches newL
+        const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
+        if (tid == 0) nevals += total;
+        if (thr < hwin - 1) {
+            // kept = every successor below the threshold bucket and the first q in it, placed
+            // in (PED, parent slot, j) order: position = #(smaller PED) + #(equal PED earlier)
+            const int q = newL - __shfl_sync(0xffffffffu, bexcl, thr);
+            int run = mine;   // lane b: bucket-b successors before the current chunk
+            for (int kb = 0; kb < kw; kb += 32) {
+                const int k = kb + lane;
+                const int d = k < kw ? R.cand[base + k] - pmin : INT_MAX;
+                const bool elig = d <= thr;
+                const unsigned V = __ballot_sync(0xffffffffu, elig);
+                if (V == 0u) continue;
+                const int dd = elig ? d : 0;
+                unsigned bb[5];
+#pragma unroll
+                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (dd >> b) & 1);
+                const int rank = __shfl_sync(0xffffffffu, run, dd) +
+                                 __popc(same_value_lanes(V, bb, dd) & lanemask_lt());
+                const int pos = __shfl_sync(0xffffffffu, bexcl, dd) + rank;
+                if (elig && (dd < thr || rank < q)) {
+                    const int idx = base + k;
+                    R.sel[pos] = ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
+                    R.selped[pos] = dd + pmin;
                 }
-                __syncwarp();
-                if (bkt >= 0 && lane == __ffs(mm) - 1) hcol[bkt * NW] += __popc(mm);
-                __syncwarp();
+                unsigned m = V;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
+                run += __popc(m);
             }
         } else {
-            select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.foff, R.flist, R.sel, R.selped,
-                                     S, L, stride, n2, newL, pbase + hwin - 1);
+            select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.cslot, R.cj, R.sel, R.selped, S,
+                                     L, stride, newL, pmin + hwin - 1);
         }
         __syncthreads();
         PHASE_MARK(2);
@@ -664,7 +659,6 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
     };
     Regions<Word> R;
     R.hist = (int32_t *)base(RG_HIST);
-    R.bbase = (int32_t *)base(RG_BBASE);
     R.alpha2 = (int32_t *)base(RG_ALPHA2);
     R.a2t = (Word *)base(RG_A2T);
     R.l2t = (Word *)base(RG_L2T);
@@ -673,14 +667,16 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
     R.ped1 = (int32_t *)base(RG_PED1);
     R.sel = (int32_t *)base(RG_SEL);
     R.selped = (int32_t *)base(RG_SELPED);
-    R.foff = (int32_t *)base(RG_FOFF);
     R.klist = (int32_t *)base(RG_KLIST);
     R.kped = (int32_t *)base(RG_KPED);
+    R.noff = (int32_t *)base(RG_NOFF);
+    R.nbr = (int32_t *)base(RG_NBR);
     R.img0 = (Word *)base(RG_IMG0);
     R.img1 = (Word *)base(RG_IMG1);
     R.P = (Word *)base(RG_P);
     R.PL = (Word *)base(RG_PL);
-    R.flist = base(RG_FLIST);
+    R.cslot = (uint16_t *)base(RG_CSLOT);
+    R.cj = base(RG_CJ);
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
     R.map1 = base(RG_MAP1);
