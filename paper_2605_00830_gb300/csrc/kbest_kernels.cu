@@ -364,21 +364,41 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 // S2: P = images of the substituted g1 neighbours of v_i (their edge labels in
                 // bit-planes PL at the image positions); dcnt = deleted neighbours
                 Word *Ps = R.P + (int64_t)s * W;
-#pragma unroll
-                for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
-                for (int b = 0; b < B; ++b)
-                    for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
                 const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
                 int dcnt = 0;
-                for (int t = 0; t < deg; ++t) {
-                    const int e = R.nbr[n0 + t];
-                    const MapT phi = ms[e & 0xffff];
-                    if (phi == DEL) { ++dcnt; continue; }
-                    const int pw = (int)phi / WB;
-                    const Word pb = (Word)1 << ((int)phi % WB);
-                    Ps[pw] |= pb;
+                if (W == 1) {
+                    Word pr = (Word)0, plr[kMaxB];
+#pragma unroll
+                    for (int b = 0; b < kMaxB; ++b) plr[b] = (Word)0;
+                    for (int t = 0; t < deg; ++t) {
+                        const int e = R.nbr[n0 + t];
+                        const MapT phi = ms[e & 0xffff];
+                        if (phi == DEL) { ++dcnt; continue; }
+                        const Word pb = (Word)1 << ((int)phi % WB);
+                        pr |= pb;
+#pragma unroll
+                        for (int b = 0; b < kMaxB; ++b)
+                            if (b < B && ((e >> (16 + b)) & 1)) plr[b] |= pb;
+                    }
+                    Ps[0] = pr;
+#pragma unroll
+                    for (int b = 0; b < kMaxB; ++b)
+                        if (b < B) R.PL[(int64_t)b * KM + s] = plr[b];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
                     for (int b = 0; b < B; ++b)
-                        if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
+                        for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
+                    for (int t = 0; t < deg; ++t) {
+                        const int e = R.nbr[n0 + t];
+                        const MapT phi = ms[e & 0xffff];
+                        if (phi == DEL) { ++dcnt; continue; }
+                        const int pw = (int)phi / WB;
+                        const Word pb = (Word)1 << ((int)phi % WB);
+                        Ps[pw] |= pb;
+                        for (int b = 0; b < B; ++b)
+                            if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
+                    }
                 }
                 R.sbase[s] = pedc[s] + c.edel * dcnt;
                 const Word *im = imgc + (int64_t)s * W;
@@ -396,27 +416,25 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int excl = incl - cnt;
             const int gtot = __shfl_sync(0xffffffffu, incl, 31);
             // successor ids in enumeration order: for each node the free g2 vertices in
-            // increasing order, then n2 for v_i -> eps (lanes over vertices, ballot compaction)
-            for (int t = 0; t < ng; ++t) {
-                const int st_ = g0 + t;
-                const Word *im = imgc + (int64_t)st_ * W;
-                const int o0 = base + kw + __shfl_sync(0xffffffffu, excl, t);
-                int pos = 0;
-                for (int jb = 0; jb < n2; jb += 32) {
-                    const int j = jb + lane;
-                    const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
-                    const unsigned bal = __ballot_sync(0xffffffffu, fr);
-                    if (fr) {
-                        const int idx = o0 + pos + __popc(bal & lanemask_lt());
-                        R.cslot[idx] = (uint16_t)st_;
-                        cjv[idx] = (MapT)j;
+            // increasing order, then n2 for v_i -> eps (each lane walks its own node's bits)
+            if (act) {
+                const Word *im = imgc + (int64_t)s * W;
+                int idx = base + kw + excl;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    Word x = ~im[w];
+                    const int lim = n2 - w * WB;
+                    if (lim < WB) x &= lim > 0 ? (((Word)1 << lim) - (Word)1) : (Word)0;
+                    while (x) {
+                        const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
+                        x &= x - (Word)1;
+                        R.cslot[idx] = (uint16_t)s;
+                        cjv[idx] = (MapT)(w * WB + t);
+                        ++idx;
                     }
-                    pos += __popc(bal);
                 }
-                if (lane == 0) {
-                    R.cslot[o0 + pos] = (uint16_t)st_;
-                    cjv[o0 + pos] = (MapT)n2;
-                }
+                R.cslot[idx] = (uint16_t)s;
+                cjv[idx] = (MapT)n2;
             }
             __syncwarp();
             PHASE_MARK(5);
