@@ -186,6 +186,66 @@ void fastged_plan_destroy(fastged_plan *p);
  * pointer may be NULL. Allocates and frees a 16 KB device buffer. */
 int fastged_measure_int_peak(double *lop3_per_s, double *iadd_per_s, double *popc_per_s);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free batch (the paper has no counterpart; this is a deployment aid).
+ *
+ * For callers that cannot allocate device memory themselves or let a library do it: code
+ * embedded in an application that owns every device allocation through its own pool, a
+ * plugin handed a fixed device budget, or a runtime where cudaMalloc at an arbitrary point
+ * is forbidden. The caller passes device inputs and device outputs; all scratch the path
+ * needs (graph table, work queue, status word, adjacency bit-set pools, per-team working
+ * sets) comes from one file-scope device array of FASTGED_NOALLOC_SCRATCH_BYTES that the
+ * library module carries, so every GPU that loads the library holds that memory until the
+ * process exits. The call performs no cudaMalloc / cudaFree and no other allocation.
+ *
+ * All graph arrays are DEVICE pointers in the flattened form below; max_n, max_m,
+ * max_elabel and total_vertices are host values that bound the device data (they size the
+ * kernels' working sets). The results are identical to fastged_batch_ex with the same
+ * graphs, pairs, cost model and K.
+ * --------------------------------------------------------------------------------------- */
+#define FASTGED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+typedef struct {
+    int32_t n_graphs;
+    int32_t n_pairs;
+    int32_t max_n;            /* host: >= every graph's vertex count; 1..FASTGED_MAX_N     */
+    int32_t max_m;            /* host: >= every graph's edge count                          */
+    int32_t max_elabel;       /* host: >= every edge label (0 for unlabelled graphs)        */
+    int32_t pad;
+    int64_t total_vertices;   /* host: sum of graph_n                                       */
+    const int32_t *graph_n;   /* device [n_graphs] vertices per graph                       */
+    const int32_t *graph_m;   /* device [n_graphs] edges per graph                          */
+    const int64_t *vlabel_off;/* device [n_graphs] first label of graph g in vlabel         */
+    const int64_t *edge_off;  /* device [n_graphs] first edge of graph g in edges / elabel  */
+    const int32_t *vlabel;    /* device [total_vertices] vertex labels                      */
+    const int32_t *edges;     /* device [2 * total edges] endpoint pairs, as fastged_graph  */
+    const int32_t *elabel;    /* device [total edges] edge labels, or NULL                  */
+    const int32_t *pairs;     /* device [2 * n_pairs] (source g1, target g2) graph indices  */
+    const int64_t *map_off;   /* device [n_pairs] first entry of pair p's map in out_mapping*/
+} fastged_device_batch;
+
+/* K-Best GED of every pair of a device-resident batch without allocating memory.
+ *   cost         host cost model (all entries >= 0)
+ *   batch        host struct of device arrays and host bounds (above)
+ *   K            beam width, 1..FASTGED_MAX_K
+ *   out_cost     device [n_pairs]; out_mapping device [sum of n1], laid out by map_off;
+ *   out_nevals   device [n_pairs] or NULL
+ *   stream       cudaStream_t the work is enqueued on (NULL = the legacy default stream)
+ * Blocks until the results are on the device (it reads back a status word twice).
+ * Errors: FASTGED_ERR_INVALID_ARG for out-of-range host bounds, for device data that breaks
+ * them (vertex / edge counts, endpoints, self-loops, duplicate edges, labels, pair indices;
+ * the outputs are then unspecified), and for a batch whose tables, bit-set pools and one
+ * team's working set do not fit FASTGED_NOALLOC_SCRATCH_BYTES; FASTGED_ERR_CUDA otherwise.
+ * The scratch array is shared by every call in the process: calls whose device work
+ * overlaps (on different streams, or from several host threads) race and corrupt each
+ * other's results, so issue them one after another. It keeps the last call's contents;
+ * each call clears what must start at zero itself. The first call on a device resolves the
+ * array's device address (with that device current) and should be made before any stream
+ * capture begins. */
+int fastged_batch_noalloc(const fastged_cost_model *cost, const fastged_device_batch *batch,
+                          int32_t K, int32_t *out_cost, int32_t *out_mapping,
+                          int64_t *out_nevals, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

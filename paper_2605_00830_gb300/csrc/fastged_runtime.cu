@@ -39,15 +39,18 @@ using namespace fastged;
 // ------------------------------------------------------------------------------------
 // errors
 // ------------------------------------------------------------------------------------
-static thread_local std::string g_err;
+// per-thread message of the last failed call (a fixed buffer: storing it never allocates)
+static thread_local char g_err[512];
 
-int fastged::set_error(int code, const std::string &msg)
+int fastged::set_error(int code, const char *msg)
 {
-    g_err = msg;
+    snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
     return code;
 }
 
-void fastged::clear_error() { g_err.clear(); }
+int fastged::set_error(int code, const std::string &msg) { return set_error(code, msg.c_str()); }
+
+void fastged::clear_error() { g_err[0] = '\0'; }
 
 static int cuda_fail(cudaError_t e, const char *what)
 {
@@ -129,7 +132,7 @@ static int words_class(int n)
 // ------------------------------------------------------------------------------------
 extern "C" int fastged_version(void) { return FASTGED_VERSION; }
 
-extern "C" const char *fastged_last_error(const fastged_handle *) { return g_err.c_str(); }
+extern "C" const char *fastged_last_error(const fastged_handle *) { return g_err; }
 
 extern "C" int fastged_create(const fastged_cost_model *cost, fastged_handle **out)
 {
@@ -188,7 +191,7 @@ static fastged_options default_options()
     return o;
 }
 
-static void plan_layout(ClassPlan &cp, int B, int block, size_t budget)
+void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
 {
     Layout &L = cp.lay;
     const int NW = block / 32;

@@ -63,6 +63,10 @@ struct Batch {
 };
 
 int set_error(int code, const std::string &msg);
+int set_error(int code, const char *msg);
+// splits a team's working set into shared-memory and global-scratch regions (budget bytes of
+// shared memory, filled in order of access frequency)
+void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 void clear_error();
 int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const fastged_options &opt, Batch &b);

@@ -31,7 +31,7 @@ FASTGED_FORM_PLAIN = 1
 EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
             "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
             "fastged_plan_read", "fastged_plan_info", "fastged_plan_kernel_ms",
-            "fastged_plan_destroy", "fastged_measure_int_peak"]
+            "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc"]
 
 
 class FastGEDError(RuntimeError):
@@ -68,6 +68,19 @@ class PlanStats(ctypes.Structure):
                 ("output_bytes", ctypes.c_int64), ("block_threads", ctypes.c_int32 * 8),
                 ("grid", ctypes.c_int32 * 8), ("words", ctypes.c_int32 * 8),
                 ("smem_bytes", ctypes.c_int32 * 8)]
+
+
+class DeviceBatch(ctypes.Structure):
+    """fastged_device_batch: device arrays of a flattened batch plus host bounds."""
+    _fields_ = [("n_graphs", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
+                ("max_n", ctypes.c_int32), ("max_m", ctypes.c_int32),
+                ("max_elabel", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("total_vertices", ctypes.c_int64),
+                ("graph_n", ctypes.c_void_p), ("graph_m", ctypes.c_void_p),
+                ("vlabel_off", ctypes.c_void_p), ("edge_off", ctypes.c_void_p),
+                ("vlabel", ctypes.c_void_p), ("edges", ctypes.c_void_p),
+                ("elabel", ctypes.c_void_p), ("pairs", ctypes.c_void_p),
+                ("map_off", ctypes.c_void_p)]
 
 
 _GRAPH_DTYPE = np.dtype({"names": ["n", "vlabel", "m", "edges", "elabel"],
@@ -109,6 +122,8 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_plan_destroy.restype = None
     dp = ctypes.POINTER(ctypes.c_double)
     lib.fastged_measure_int_peak.argtypes = [dp, dp, dp]
+    lib.fastged_batch_noalloc.argtypes = [ctypes.POINTER(CostModel), ctypes.POINTER(DeviceBatch),
+                                          i32, vp, vp, vp, vp]
     for name in EXPORTED:
         if name in ("fastged_destroy", "fastged_plan_destroy", "fastged_last_error",
                     "fastged_version"):
@@ -286,6 +301,15 @@ def fastged_measure_int_peak() -> dict:
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib, lib.fastged_measure_int_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"lop3": a.value, "iadd": b.value, "popc": c.value}
+
+
+def fastged_batch_noalloc(cost: Sequence[int], batch: DeviceBatch, K: int, d_out_cost: int,
+                          d_out_mapping: int, d_out_nevals: int = 0, stream: int = 0) -> None:
+    """Allocation-free batch on device inputs and outputs (device addresses as ints)."""
+    lib = load()
+    _check(lib, lib.fastged_batch_noalloc(ctypes.byref(CostModel(*[int(x) for x in cost])),
+                                          ctypes.byref(batch), int(K), d_out_cost,
+                                          d_out_mapping, d_out_nevals or None, stream or None))
 
 
 def split_maps(mm: Marshalled, flat: np.ndarray):
