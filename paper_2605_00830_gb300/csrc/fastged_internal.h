@@ -82,6 +82,8 @@ struct KParams {
     // scratch
     uint8_t *gscratch;
     Layout lay;
+    // per-phase cycle counters; profiling builds only (nullptr otherwise)
+    unsigned long long *phase_cycles;
 };
 
 struct PackParams {

@@ -25,10 +25,10 @@
 #include "fastged_runtime.h"
 
 namespace fastged {
-cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
-                         int block, size_t smem, cudaStream_t st);
-cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
-                            int *out);
+cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, int bk, const KParams &p,
+                         int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int block,
+                            size_t smem, int *out);
 bool kbest_has_smem_variant(int W, bool wide, bool w32);
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
@@ -116,6 +116,9 @@ void PinBuf::release()
 }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// kernel instance for B edge-label planes: 0, exactly 2, or up to 8
+int fastged::label_instance(int B) { return B == 0 ? 0 : (B == 2 ? 2 : 8); }
 
 static int words_class(int n)
 {
@@ -279,7 +282,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     plan_layout(cp, B, block, budget);
     cp.all_smem = cp.lay.slice_bytes == 0 && kbest_has_smem_variant(cp.W, cp.wide, cp.w32);
     int occ = 0;
-    cudaError_t e = kbest_occupancy(cp.W, cp.wide, cp.w32, cp.all_smem, block,
+    cudaError_t e = kbest_occupancy(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(B), block,
                                     (size_t)cp.lay.smem_bytes, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (occ < 1) return set_error(FASTGED_ERR_CUDA, "team does not fit on an SM");
@@ -349,6 +352,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     }
     int B = 0;
     while ((1 << B) <= maxlab) ++B;   // planes needed for labels 0..maxlab
+    if (B == 1) B = 2;                // served by the two-plane kernel (second plane all zero)
     b.B = B;
     b.labelled = labelled && B > 0;
     for (int g = 0; g < ng; ++g) b.meta[g].plane_off = b.meta[g].adj_off * B;
@@ -488,6 +492,19 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     return FASTGED_OK;
 }
 
+#ifdef FASTGED_PHASE_TIMERS
+// profiling builds only: per-phase cycle counters summed over every team
+static unsigned long long *g_phase_dev = nullptr;
+
+extern "C" int fastged_debug_phase_cycles(unsigned long long *out, int reset)
+{
+    if (!g_phase_dev) return -3;
+    if (cudaMemcpy(out, g_phase_dev, 64, cudaMemcpyDeviceToHost) != cudaSuccess) return -3;
+    if (reset) cudaMemset(g_phase_dev, 0, 64);
+    return 0;
+}
+#endif
+
 // Fills the kernel parameters of class k for a batch whose inputs sit at `in` and whose
 // work region sits at `wk` on the device.
 static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8_t *in,
@@ -521,6 +538,10 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     p.out_nevals = (int64_t *)(wk + b.woff_nev);
     p.gscratch = wk + b.woff_scratch + cp.scratch_off;
     p.lay = cp.lay;
+#ifdef FASTGED_PHASE_TIMERS
+    if (!g_phase_dev && cudaMalloc(&g_phase_dev, 64) == cudaSuccess) cudaMemset(g_phase_dev, 0, 64);
+    p.phase_cycles = g_phase_dev;
+#endif
     return p;
 }
 
@@ -565,13 +586,13 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             p.order += pos[pr];
             p.n_order = 1;
             p.queue_head = qbase + pr;
-            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, 1, cp.block, cp.smem, st));
+            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, 1, cp.block, cp.smem, st));
             ++nl;
         }
     } else if (nc == 1) {
         const ClassPlan &cp = b.classes[0];
         KParams p = make_params(h, b, 0, in, wk);
-        CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, cp.grid, cp.block, cp.smem, st));
+        CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid, cp.block, cp.smem, st));
         ++nl;
     } else if (nc > 1) {
         CK(cudaEventRecord(h->ev[kMaxClasses], st));
@@ -579,7 +600,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             const ClassPlan &cp = b.classes[k];
             CK(cudaStreamWaitEvent(h->class_stream[k], h->ev[kMaxClasses], 0));
             KParams p = make_params(h, b, k, in, wk);
-            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
+            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
             ++nl;
             CK(cudaEventRecord(h->ev[k], h->class_stream[k]));
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));

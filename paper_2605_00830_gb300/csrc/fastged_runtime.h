@@ -67,6 +67,8 @@ int set_error(int code, const char *msg);
 // splits a team's working set into shared-memory and global-scratch regions (budget bytes of
 // shared memory, filled in order of access frequency)
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
+// kernel instance serving B edge-label planes (0, 2 or 8)
+int label_instance(int B);
 void clear_error();
 int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const fastged_options &opt, Batch &b);

@@ -1,0 +1,8 @@
+// kbest_b8.cu -- K-Best kernel instances for up to eight edge-label bit-planes.
+#include "kbest_impl.cuh"
+
+namespace fastged {
+template cudaError_t launch_kbest_bk<8>(int, bool, bool, bool, const KParams &, int, int,
+                                          size_t, cudaStream_t);
+template cudaError_t kbest_occupancy_bk<8>(int, bool, bool, bool, int, size_t, int *);
+}  // namespace fastged

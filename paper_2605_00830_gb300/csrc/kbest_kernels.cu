@@ -1,7 +1,7 @@
 // kbest_kernels.cu -- sm_103a kernels of the K-Best GED path.
 //
 //   pack_kernel   S0: edge lists -> adjacency bitsets and edge-label bit-planes
-//   kbest_kernel  S1-S5 for every pair of a size class: persistent teams pull pairs from a
+//   kbest_kernel  S1-S5 (templates in kbest_impl.cuh) for every pair of a size class: persistent teams pull pairs from a
 //                 device work queue; per level they stage the vertex-cost row, build per-node
 //                 neighbour bitsets, score every successor with AND/XOR + popcount, select the
 //                 best K with a deterministic stable counting sort, write the kept children in
@@ -19,35 +19,9 @@
 //   relabelled edges = popc(A2[u] & P & OR_b(PL_b ^ L2_b[u]))
 // and when insertion and deletion cost the same, the first two fold into one
 // popc((A2[u] & Img) ^ P) since P is a subset of Img.
-#include <climits>
-#include <cstdint>
-
-#include "fastged_internal.h"
+#include "kbest_impl.cuh"
 
 namespace fastged {
-
-__device__ __forceinline__ unsigned lanemask_lt()
-{
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-__device__ __forceinline__ int warp_sum(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// bits k of word w with k < i
-__device__ __forceinline__ uint64_t low_mask(int i, int w)
-{
-    const int lo = w * 64;
-    if (i >= lo + 64) return ~0ull;
-    if (i <= lo) return 0ull;
-    return (1ull << (i - lo)) - 1ull;
-}
 
 // ------------------------------------------------------------------------------------
 // S0: pack edge lists into bitsets (one warp per graph, lanes over its edges).
@@ -81,716 +55,31 @@ __global__ void pack_kernel(const PackParams pp)
     }
 }
 
-// ------------------------------------------------------------------------------------
-// K-Best teams
-// ------------------------------------------------------------------------------------
-struct TeamShared {
-    int pair;
-    int cnt;
-    int mx;
-    int wmin[kMaxWarps];  // least successor PED each warp scored at this level
-    int wn[kMaxWarps];    // successors each warp scored at this level
-    int wlt[kMaxWarps];
-    int weq[kMaxWarps];
-    unsigned long long wbest[kMaxWarps];
-};
-
-template <typename Word>
-struct Regions {
-    int32_t *hist, *alpha2, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
-    int32_t *ped0, *ped1;
-    Word *a2t, *l2t, *img0, *img1, *P, *PL;
-    uint16_t *cslot;
-    uint8_t *map0, *map1, *cj;
-};
-
-// A kept child is stored in the selection list as (parent slot << 11) | j, j = 0..n2.
-constexpr int kSelShift = 11;
-
-__device__ __forceinline__ int popcw(uint32_t x) { return __popc(x); }
-__device__ __forceinline__ int popcw(uint64_t x) { return __popcll(x); }
-
-#ifdef FASTGED_PHASE_TIMERS
-// profiling builds only: cycles thread 0 of every team spends in each phase
-__device__ unsigned long long g_phase_cycles[8];
-#define PHASE_MARK(k)                                        \
-    do {                                                     \
-        if (threadIdx.x == 0) {                              \
-            const long long t_ = clock64();                  \
-            ph[k] += t_ - ph_last;                           \
-            ph_last = t_;                                    \
-        }                                                    \
-    } while (0)
-#else
-#define PHASE_MARK(k) do { } while (0)
-#endif
-
-// Lanes of the warp whose 5-bit value equals `v`, among the lanes in `valid`, given the
-// ballots b[k] of bit k of every lane's value.
-__device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsigned b[5], int v)
-{
-    unsigned m = valid;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) m &= ((v >> k) & 1) ? b[k] : ~b[k];
-    return m;
-}
-
-// Stable compaction of the kept successors of this warp, in enumeration order: every
-// candidate with PED < T, and the first q with PED == T counted over the whole team.
-// keep_before / eq_before: kept / tied candidates of the warps before this one.
-template <typename Word>
-__device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, int n, int T,
-                                            int q, int keep_before, int eq_before)
-{
-    const int lane = threadIdx.x & 31;
-    for (int kb = 0; kb < n; kb += 32) {
-        const int k = kb + lane;
-        const int v = k < n ? R.cand[base + k] : INT_MAX;
-        if (__ballot_sync(0xffffffffu, v <= T) == 0u) continue;
-        const bool is_eq = (v == T);
-        const unsigned eqb = __ballot_sync(0xffffffffu, is_eq);
-        const int eq_rank = eq_before + __popc(eqb & lanemask_lt());
-        const bool keep = (v < T) || (is_eq && eq_rank < q);
-        const unsigned kbm = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int pos = keep_before + __popc(kbm & lanemask_lt());
-            R.klist[pos] = base + k;
-            R.kped[pos] = v;
-        }
-        keep_before += __popc(kbm);
-        eq_before += __popc(eqb);
-    }
-}
-
-// Exact selection used when the kept set reaches past the histogram window: the K-th
-// smallest PED is found by bisection over team-wide counts, the kept candidates are
-// compacted stably, and ranked by (PED, enumeration order).
-template <typename MapT, typename Word>
-__device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
-                                          const uint16_t *cslot, const uint8_t *cj_b,
-                                          int32_t *sel, int32_t *selped, TeamShared &S, int L,
-                                          int stride, int newL, int lo)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = blockDim.x, NW = T >> 5;
-    const int s_lo = (warp * L) / NW;
-    const int base = s_lo * stride, n = S.wn[warp];
-    Regions<Word> R;
-    R.cand = cand;
-    R.klist = klist;
-    R.kped = kped;
-
-    int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, cand[base + k]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (tid == 0) S.mx = 0;
-    __syncthreads();
-    if (lane == 0) atomicMax(&S.mx, mx);
-    __syncthreads();
-    int hi = S.mx;
-    if (lo > hi) lo = hi;
-    // invariant: count(PED < lo) < newL <= count(PED <= hi)
-    while (lo < hi) {
-        const int mid = lo + (hi - lo) / 2;
-        int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (cand[base + k] <= mid);
-        cnt = warp_sum(cnt);
-        __syncthreads();
-        if (tid == 0) S.cnt = 0;
-        __syncthreads();
-        if (lane == 0) atomicAdd(&S.cnt, cnt);
-        __syncthreads();
-        if (S.cnt >= newL) hi = mid; else lo = mid + 1;
-    }
-    const int thr = lo;
-    int nlt = 0, neq = 0;
-    for (int k = lane; k < n; k += 32) {
-        const int v = cand[base + k];
-        nlt += (v < thr);
-        neq += (v == thr);
-    }
-    nlt = warp_sum(nlt);
-    neq = warp_sum(neq);
-    if (lane == 0) { S.wlt[warp] = nlt; S.weq[warp] = neq; }
-    __syncthreads();
-    int lt_all = 0;
-    for (int w = 0; w < NW; ++w) lt_all += S.wlt[w];
-    const int q = newL - lt_all;
-    int keep_before = 0, eq_before = 0;
-    for (int w = 0; w < warp; ++w) {
-        keep_before += S.wlt[w];
-        eq_before += S.weq[w];
-    }
-    keep_before += min(q, eq_before);
-    compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before);
-    __syncthreads();
-    // rank by (PED, enumeration order); klist is in enumeration order
-    const MapT *cj = (const MapT *)cj_b;
-    for (int a = tid; a < newL; a += T) {
-        const int pa = kped[a];
-        int rank = 0;
-        for (int b = 0; b < newL; ++b) {
-            const int pb = kped[b];
-            rank += (pb < pa) || (pb == pa && b < a);
-        }
-        const int c = klist[a];
-        sel[rank] = ((int)cslot[c] << kSelShift) | (int)cj[c];
-        selped[rank] = pa;
-    }
-}
-
-template <int W, typename MapT, typename Word>
-__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word> R,
-                                           TeamShared &S, const int pair)
-{
-    constexpr int WB = 8 * (int)sizeof(Word);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = blockDim.x, NW = T >> 5;
-    const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
-    const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
-    const int n1 = m1.n, n2 = m2.n, W1 = m1.W, W2 = m2.W;
-    const int K = p.kpp ? p.kpp[pair] : p.K;
-    const int B = p.lay.B;
-    const int N2S = p.lay.n2s;
-    const int KM = p.lay.kmax;
-    const int64_t mrow = p.lay.mrow;
-    const int stride = n2 + 1;   // successors of one node at most: n2 substitutions + deletion
-    const MapT DEL = (MapT)~(MapT)0;
-    const CostModel c = p.cost;
-    const int hwin = p.hwin;     // buckets 0..hwin-2 hold one PED each, hwin-1 the rest
-    const bool fold_ie = (c.eins == c.edel);
-    MapT *cjv = (MapT *)R.cj;
-    // lane-constant masks: lane b answers for histogram bucket b
-    unsigned lanebit[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) lanebit[k] = ((lane >> k) & 1) ? 0xffffffffu : 0u;
-#ifdef FASTGED_PHASE_TIMERS
-    long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long ph_last = clock64();
-#endif
-
-    // stage g2: transposed adjacency and label planes, vertex labels; g1 degrees
-    {
-        const uint64_t *adj2 = p.adj + m2.adj_off;
-        for (int idx = tid; idx < W * n2; idx += T) {
-            const int w = idx / n2, u = idx - w * n2;
-            const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
-            R.a2t[w * N2S + u] = (w64 < W2) ? (Word)(adj2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
-        }
-        for (int b = 0; b < B; ++b) {
-            const uint64_t *pl2 = p.planes + m2.plane_off + (int64_t)b * n2 * W2;
-            for (int idx = tid; idx < W * n2; idx += T) {
-                const int w = idx / n2, u = idx - w * n2;
-                const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
-                R.l2t[(b * W + w) * N2S + u] =
-                    (w64 < W2) ? (Word)(pl2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
-            }
-        }
-        for (int u = tid; u < n2; u += T) R.alpha2[u] = p.vlab[m2.lab_off + u];
-        // number of neighbours v_k of v_i with k < i
-        for (int v = tid; v < n1; v += T) {
-            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
-            int d = 0;
-            for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
-            R.noff[v + 1] = d;
-        }
-        // root node: empty lambda, R_V2 = V2, PED 0
-        for (int w = tid; w < W; w += T) R.img0[w] = (Word)0;
-        if (tid == 0) {
-            R.ped0[0] = 0;
-            R.noff[0] = 0;
-        }
-    }
-    __syncthreads();
-    // prior-neighbour lists of g1: nbr[noff[i] .. noff[i+1]) = k | (edge label << 16)
-    if (warp == 0) {
-        int carry = 0;
-        for (int v0 = 0; v0 < n1; v0 += 32) {
-            const int v = v0 + lane;
-            const int d = v < n1 ? R.noff[v + 1] : 0;
-            int incl = d;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (v < n1) R.noff[v + 1] = carry + incl;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-    }
-    __syncthreads();
-    for (int v = tid; v < n1; v += T) {
-        const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
-        const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
-        const int64_t pstep = (int64_t)n1 * W1;
-        int o = R.noff[v];
-        for (int w = 0; w < W1; ++w) {
-            uint64_t bits = row[w] & low_mask(v, w);
-            while (bits) {
-                const int t = __ffsll((long long)bits) - 1;
-                bits &= bits - 1ull;
-                int lab = 0;
-                for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
-                R.nbr[o++] = (w * 64 + t) | (lab << 16);
-            }
-        }
-    }
-    long long nevals = 0;
-    int L = 1;
-    // current / next beam buffers, swapped after every level
-    uint8_t *mapc = R.map0, *mapn = R.map1;
-    Word *imgc = R.img0, *imgn = R.img1;
-    int32_t *pedc = R.ped0, *pedn = R.ped1;
-    __syncthreads();
-    PHASE_MARK(0);
-
-    for (int i = 0; i < n1; ++i) {
-        const int a1 = p.vlab[m1.lab_off + i];
-        const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
-        const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes its edges to v_0..v_{i-1}
-        const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
-        const int base = s_lo * stride;              // this warp's successor storage
-
-        // ---- S1 + S2 per-node vectors, successor lists, S3 evaluation ----------------
-        int kw = 0;          // successors of this warp so far
-        int wmin = INT_MAX;
-        for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
-            const int ng = min(32, s_hi - g0);
-            const int s = g0 + lane;
-            const bool act = lane < ng;
-            int cnt = 0;
-            if (act) {
-                // S2: P = images of the substituted g1 neighbours of v_i (their edge labels in
-                // bit-planes PL at the image positions); dcnt = deleted neighbours
-                Word *Ps = R.P + (int64_t)s * W;
-                const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
-                int dcnt = 0;
-                if (W == 1) {
-                    Word pr = (Word)0, plr[kMaxB];
-#pragma unroll
-                    for (int b = 0; b < kMaxB; ++b) plr[b] = (Word)0;
-                    for (int t = 0; t < deg; ++t) {
-                        const int e = R.nbr[n0 + t];
-                        const MapT phi = ms[e & 0xffff];
-                        if (phi == DEL) { ++dcnt; continue; }
-                        const Word pb = (Word)1 << ((int)phi % WB);
-                        pr |= pb;
-#pragma unroll
-                        for (int b = 0; b < kMaxB; ++b)
-                            if (b < B && ((e >> (16 + b)) & 1)) plr[b] |= pb;
-                    }
-                    Ps[0] = pr;
-#pragma unroll
-                    for (int b = 0; b < kMaxB; ++b)
-                        if (b < B) R.PL[(int64_t)b * KM + s] = plr[b];
-                } else {
-#pragma unroll
-                    for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
-                    for (int b = 0; b < B; ++b)
-                        for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
-                    for (int t = 0; t < deg; ++t) {
-                        const int e = R.nbr[n0 + t];
-                        const MapT phi = ms[e & 0xffff];
-                        if (phi == DEL) { ++dcnt; continue; }
-                        const int pw = (int)phi / WB;
-                        const Word pb = (Word)1 << ((int)phi % WB);
-                        Ps[pw] |= pb;
-                        for (int b = 0; b < B; ++b)
-                            if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
-                    }
-                }
-                R.sbase[s] = pedc[s] + c.edel * dcnt;
-                const Word *im = imgc + (int64_t)s * W;
-                int used = 0;
-#pragma unroll
-                for (int w = 0; w < W; ++w) used += popcw(im[w]);
-                cnt = n2 - used + 1;   // free g2 vertices (R_V2) and the deletion
-            }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int excl = incl - cnt;
-            const int gtot = __shfl_sync(0xffffffffu, incl, 31);
-            // successor ids in enumeration order: for each node the free g2 vertices in
-            // increasing order, then n2 for v_i -> eps (each lane walks its own node's bits)
-            if (act) {
-                const Word *im = imgc + (int64_t)s * W;
-                int idx = base + kw + excl;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    Word x = ~im[w];
-                    const int lim = n2 - w * WB;
-                    if (lim < WB) x &= lim > 0 ? (((Word)1 << lim) - (Word)1) : (Word)0;
-                    while (x) {
-                        const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
-                        x &= x - (Word)1;
-                        R.cslot[idx] = (uint16_t)s;
-                        cjv[idx] = (MapT)(w * WB + t);
-                        ++idx;
-                    }
-                }
-                R.cslot[idx] = (uint16_t)s;
-                cjv[idx] = (MapT)n2;
-            }
-            __syncwarp();
-            PHASE_MARK(5);
-
-            // S3: 32 successors at a time, in enumeration order
-            for (int kb = 0; kb < gtot; kb += 32) {
-                const int k = kb + lane;
-                if (k < gtot) {
-                    const int idx = base + kw + k;
-                    const int sc = R.cslot[idx];
-                    const int j = (int)cjv[idx];
-                    int ped;
-                    if (j == n2) {
-                        ped = pedc[sc] + delcost;
-                    } else {
-                        const Word *im = imgc + (int64_t)sc * W;
-                        const Word *Ps = R.P + (int64_t)sc * W;
-                        int x = 0, y = 0, z = 0;
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const Word aw = R.a2t[w * N2S + j];
-                            const Word ai = aw & im[w];
-                            const Word pw = Ps[w];
-                            if (fold_ie) {
-                                x += popcw((Word)(ai ^ pw));
-                            } else {
-                                x += popcw((Word)(ai & ~pw));
-                                y += popcw((Word)(pw & ~aw));
-                            }
-                            if (B > 0) {
-                                Word ld = (Word)0;
-                                for (int b = 0; b < B; ++b)
-                                    ld |= R.PL[((int64_t)b * KM + sc) * W + w] ^
-                                          R.l2t[(b * W + w) * N2S + j];
-                                z += popcw((Word)(aw & pw & ld));
-                            }
-                        }
-                        const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
-                        ped = R.sbase[sc] + cv + c.eins * x + c.edel * y + c.esub * z;
-                    }
-                    R.cand[idx] = ped;
-                    wmin = ped < wmin ? ped : wmin;
-                }
-            }
-            kw += gtot;
-            __syncwarp();
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
-        if (lane == 0) {
-            S.wmin[warp] = wmin;
-            S.wn[warp] = kw;
-        }
-        __syncthreads();
-        PHASE_MARK(1);
-
-        // ---- S4 selection ---------------------------------------------------------
-        // histogram of PED - pmin over this warp's successors (ballot counting: lane b
-        // keeps the count of bucket b; the last bucket collects every PED past the window)
-        int pmin = INT_MAX;
-        for (int w = 0; w < NW; ++w) pmin = min(pmin, S.wmin[w]);
-        {
-            int hreg = 0;
-            for (int kb = 0; kb < kw; kb += 32) {
-                const int k = kb + lane;
-                const bool valid = k < kw;
-                const int d = valid ? min(R.cand[base + k] - pmin, hwin - 1) : 0;
-                const unsigned V = __ballot_sync(0xffffffffu, valid);
-                unsigned bb[5];
-#pragma unroll
-                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1);
-                unsigned m = V;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
-                hreg += __popc(m);
-            }
-            R.hist[lane * NW + warp] = hreg;
-        }
-        __syncthreads();
-        // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
-        // and the bucket-b successors of the warps before this one
-        int tot = 0, mine = 0;
-        for (int w = 0; w < NW; ++w) {
-            const int v = R.hist[lane * NW + w];
-            tot += v;
-            mine += (w < warp) ? v : 0;
-        }
-        int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int bexcl = incl - tot;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int newL = min(K, total);
-        // the bucket where the cumulative count reaches newL
-        const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
-        if (tid == 0) nevals += total;
-        if (thr < hwin - 1) {
-            // kept = every successor below the threshold bucket and the first q in it, placed
-            // in (PED, parent slot, j) order: position = #(smaller PED) + #(equal PED earlier)
-            const int q = newL - __shfl_sync(0xffffffffu, bexcl, thr);
-            int run = mine;   // lane b: bucket-b successors before the current chunk
-            for (int kb = 0; kb < kw; kb += 32) {
-                const int k = kb + lane;
-                const int d = k < kw ? R.cand[base + k] - pmin : INT_MAX;
-                const bool elig = d <= thr;
-                const unsigned V = __ballot_sync(0xffffffffu, elig);
-                if (V == 0u) continue;
-                const int dd = elig ? d : 0;
-                unsigned bb[5];
-#pragma unroll
-                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (dd >> b) & 1);
-                const int rank = __shfl_sync(0xffffffffu, run, dd) +
-                                 __popc(same_value_lanes(V, bb, dd) & lanemask_lt());
-                const int pos = __shfl_sync(0xffffffffu, bexcl, dd) + rank;
-                if (elig && (dd < thr || rank < q)) {
-                    const int idx = base + k;
-                    R.sel[pos] = ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
-                    R.selped[pos] = dd + pmin;
-                }
-                unsigned m = V;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
-                run += __popc(m);
-            }
-        } else {
-            select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.cslot, R.cj, R.sel, R.selped, S,
-                                     L, stride, newL, pmin + hwin - 1);
-        }
-        __syncthreads();
-        PHASE_MARK(2);
-
-        // ---- kept children, in key order (slot = rank) -----------------------------
-        {
-            const int nvec = (int)((i * (int)sizeof(MapT) + 15) >> 4);
-            if (mrow <= 128) {
-                for (int r = tid; r < newL; r += T) {
-                    const int v = R.sel[r];
-                    const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
-                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
-                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
-                    for (int t = 0; t < nvec; ++t) dst[t] = src[t];
-                    ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        Word x = imgc[(int64_t)s * W + w];
-                        if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
-                        imgn[(int64_t)r * W + w] = x;
-                    }
-                    pedn[r] = R.selped[r];
-                }
-            } else {
-                for (int r = warp; r < newL; r += NW) {
-                    const int v = R.sel[r];
-                    const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
-                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
-                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
-                    for (int t = lane; t < nvec; t += 32) dst[t] = src[t];
-                    for (int w = lane; w < W; w += 32) {
-                        Word x = imgc[(int64_t)s * W + w];
-                        if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
-                        imgn[(int64_t)r * W + w] = x;
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
-                        pedn[r] = R.selped[r];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        PHASE_MARK(3);
-        { uint8_t *t = mapc; mapc = mapn; mapn = t; }
-        { Word *t = imgc; imgc = imgn; imgn = t; }
-        { int32_t *t = pedc; pedc = pedn; pedn = t; }
-        L = newL;
-    }
-
-    // ---- S5 leaf completion (insert the free g2 vertices and their edges) + argmin ------
-    {
-        unsigned long long best = ~0ull;
-        for (int s = warp; s < L; s += NW) {
-            const Word *im = imgc + (int64_t)s * W;
-            int acc = 0;
-            for (int u = lane; u < n2; u += 32) {
-                if ((im[u / WB] >> (u % WB)) & (Word)1) {
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc += popcw((Word)(R.a2t[w * N2S + u] & im[w]));
-                }
-            }
-            int nimg = 0;
-            for (int w = lane; w < W; w += 32) nimg += popcw(im[w]);
-            acc = warp_sum(acc);
-            nimg = warp_sum(nimg);
-            // g2 edges with both ends used were counted twice in acc
-            const long long total = (long long)pedc[s] + (long long)c.vins * (n2 - nimg) +
-                                    (long long)c.eins * (m2.m - acc / 2);
-            const unsigned long long key = ((unsigned long long)total << 32) | (unsigned)s;
-            best = key < best ? key : best;
-        }
-        if (lane == 0) S.wbest[warp] = best;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long b = S.wbest[0];
-            for (int w = 1; w < NW; ++w) b = S.wbest[w] < b ? S.wbest[w] : b;
-            S.wbest[0] = b;
-            p.out_cost[pair] = (int32_t)(b >> 32);
-            if (p.out_nevals) p.out_nevals[pair] = nevals + L;
-        }
-        __syncthreads();
-        const int bs = (int)(S.wbest[0] & 0xffffffffull);
-        const MapT *mb = (const MapT *)(mapc + (int64_t)bs * mrow);
-        int32_t *om = p.out_map + p.map_off[pair];
-        for (int k = tid; k < n1; k += T) {
-            const MapT v = mb[k];
-            om[k] = (v == DEL) ? -1 : (int32_t)v;
-        }
-        __syncthreads();
-        PHASE_MARK(4);
-    }
-#ifdef FASTGED_PHASE_TIMERS
-    if (tid == 0)
-        for (int k = 0; k < 6; ++k) atomicAdd(&g_phase_cycles[k], (unsigned long long)ph[k]);
-#endif
-}
-
-// SM: every region lives in shared memory (addresses then stay in the shared window)
-template <int W, typename MapT, typename Word, bool SM>
-__global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ TeamShared S;
-    uint8_t *gs = p.gscratch + (int64_t)blockIdx.x * p.lay.slice_bytes;
-    auto base = [&](int r) -> uint8_t * {
-        if (SM) return smem + p.lay.off[r];
-        return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
-    };
-    Regions<Word> R;
-    R.hist = (int32_t *)base(RG_HIST);
-    R.alpha2 = (int32_t *)base(RG_ALPHA2);
-    R.a2t = (Word *)base(RG_A2T);
-    R.l2t = (Word *)base(RG_L2T);
-    R.sbase = (int32_t *)base(RG_SBASE);
-    R.ped0 = (int32_t *)base(RG_PED0);
-    R.ped1 = (int32_t *)base(RG_PED1);
-    R.sel = (int32_t *)base(RG_SEL);
-    R.selped = (int32_t *)base(RG_SELPED);
-    R.klist = (int32_t *)base(RG_KLIST);
-    R.kped = (int32_t *)base(RG_KPED);
-    R.noff = (int32_t *)base(RG_NOFF);
-    R.nbr = (int32_t *)base(RG_NBR);
-    R.img0 = (Word *)base(RG_IMG0);
-    R.img1 = (Word *)base(RG_IMG1);
-    R.P = (Word *)base(RG_P);
-    R.PL = (Word *)base(RG_PL);
-    R.cslot = (uint16_t *)base(RG_CSLOT);
-    R.cj = base(RG_CJ);
-    R.cand = (int32_t *)base(RG_CAND);
-    R.map0 = base(RG_MAP0);
-    R.map1 = base(RG_MAP1);
-
-    for (;;) {
-        if (threadIdx.x == 0) S.pair = atomicAdd(p.queue_head, 1);
-        __syncthreads();
-        const int qi = S.pair;
-        __syncthreads();
-        if (qi >= p.n_order) break;
-        solve_pair<W, MapT, Word>(p, R, S, p.order[qi]);
-    }
-}
-
-// ------------------------------------------------------------------------------------
-// launch wrappers (host side of this translation unit)
-// ------------------------------------------------------------------------------------
-// Opts the kernel into the device's full dynamic shared memory (needed above 48 KB) before
-// it is launched or queried for occupancy.
-template <int W, typename MapT, typename Word, bool SM>
-static cudaError_t ensure_smem_attr()
-{
-    static bool done = false;
-    if (done) return cudaSuccess;
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_kernel<W, MapT, Word, SM>);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kbest_kernel<W, MapT, Word, SM>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)fa.sharedSizeBytes);
-    if (e == cudaSuccess) done = true;
-    return e;
-}
-
-template <int W, typename MapT, typename Word, bool SM>
-static cudaError_t launch_one(const KParams &p, int grid, int block, size_t smem,
-                              cudaStream_t st)
-{
-    cudaError_t e = ensure_smem_attr<W, MapT, Word, SM>();
-    if (e != cudaSuccess) return e;
-    kbest_kernel<W, MapT, Word, SM><<<grid, block, smem, st>>>(p);
-    return cudaGetLastError();
-}
-
-template <int W, typename MapT, typename Word, bool SM>
-static cudaError_t occupancy_one(int block, size_t smem, int *out)
-{
-    cudaError_t e = ensure_smem_attr<W, MapT, Word, SM>();
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_kernel<W, MapT, Word, SM>,
-                                                         block, smem);
-}
-
-// size class -> template instance. 16-bit maps only occur with W >= 4 (n2 >= 255), and the
-// all-shared-memory variant is built for bitsets of up to 4 words.
-#define FASTGED_DISPATCH(W_, wide, w32, sm, CALL)                                        \
-    do {                                                                                 \
-        if (sm) {                                                                        \
-            if (w32) return CALL(1, uint8_t, uint32_t, true);                            \
-            if (W_ == 1 && !wide) return CALL(1, uint8_t, uint64_t, true);               \
-            if (W_ == 2 && !wide) return CALL(2, uint8_t, uint64_t, true);               \
-            if (W_ == 4 && !wide) return CALL(4, uint8_t, uint64_t, true);               \
-        }                                                                                \
-        if (w32) return CALL(1, uint8_t, uint32_t, false);                               \
-        switch (W_) {                                                                    \
-        case 1: if (!wide) return CALL(1, uint8_t, uint64_t, false); break;              \
-        case 2: if (!wide) return CALL(2, uint8_t, uint64_t, false); break;              \
-        case 4: if (wide) return CALL(4, uint16_t, uint64_t, false);                     \
-                else return CALL(4, uint8_t, uint64_t, false);                           \
-        case 8: return CALL(8, uint16_t, uint64_t, false);                               \
-        case 16: return CALL(16, uint16_t, uint64_t, false);                             \
-        default: break;                                                                  \
-        }                                                                                \
-        return cudaErrorInvalidValue;                                                    \
-    } while (0)
 
 bool kbest_has_smem_variant(int W, bool wide, bool w32) { return w32 || (W <= 4 && !wide); }
 
-cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
-                         int block, size_t smem, cudaStream_t st)
+template <int BK>
+cudaError_t launch_kbest_bk(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
+                            int block, size_t smem, cudaStream_t st);
+template <int BK>
+cudaError_t kbest_occupancy_bk(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
+                               int *out);
+
+// bk: edge-label planes of the instance (0, 2 or 8; see solve_pair)
+cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, int bk, const KParams &p,
+                         int grid, int block, size_t smem, cudaStream_t st)
 {
-#define CALL_LAUNCH(w, M, Wd, S_) launch_one<w, M, Wd, S_>(p, grid, block, smem, st)
-    FASTGED_DISPATCH(W, wide_map, w32, sm, CALL_LAUNCH);
-#undef CALL_LAUNCH
+    if (bk == 0) return launch_kbest_bk<0>(W, wide_map, w32, sm, p, grid, block, smem, st);
+    if (bk == 2) return launch_kbest_bk<2>(W, wide_map, w32, sm, p, grid, block, smem, st);
+    return launch_kbest_bk<8>(W, wide_map, w32, sm, p, grid, block, smem, st);
 }
 
-cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
-                            int *out)
+cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int block,
+                            size_t smem, int *out)
 {
-#define CALL_OCC(w, M, Wd, S_) occupancy_one<w, M, Wd, S_>(block, smem, out)
-    FASTGED_DISPATCH(W, wide_map, w32, sm, CALL_OCC);
-#undef CALL_OCC
+    if (bk == 0) return kbest_occupancy_bk<0>(W, wide_map, w32, sm, block, smem, out);
+    if (bk == 2) return kbest_occupancy_bk<2>(W, wide_map, w32, sm, block, smem, out);
+    return kbest_occupancy_bk<8>(W, wide_map, w32, sm, block, smem, out);
 }
 
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
@@ -807,18 +96,3 @@ cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
 size_t team_shared_static_bytes() { return sizeof(TeamShared) + 256; }
 
 }  // namespace fastged
-
-#ifdef FASTGED_PHASE_TIMERS
-// profiling builds only: reads (and optionally clears) the per-phase cycle counters
-extern "C" int fastged_debug_phase_cycles(unsigned long long *out, int reset)
-{
-    if (cudaMemcpyFromSymbol(out, fastged::g_phase_cycles, sizeof(unsigned long long) * 8) !=
-        cudaSuccess)
-        return -3;
-    if (reset) {
-        unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        cudaMemcpyToSymbol(fastged::g_phase_cycles, z, sizeof(z));
-    }
-    return 0;
-}
-#endif

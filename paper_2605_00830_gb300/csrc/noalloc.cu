@@ -24,10 +24,10 @@
 #include "fastged_runtime.h"
 
 namespace fastged {
-cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
-                         int block, size_t smem, cudaStream_t st);
-cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
-                            int *out);
+cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, int bk, const KParams &p,
+                         int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int block,
+                            size_t smem, int *out);
 bool kbest_has_smem_variant(int W, bool wide, bool w32);
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
@@ -135,6 +135,7 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     // one size class covering every graph of the batch
     int B = 0;
     while ((1 << B) <= b->max_elabel) ++B;
+    if (B == 1) B = 2;   // served by the two-plane kernel (second plane all zero)
     const int Wg = (b->max_n + 63) / 64;
     ClassPlan cp;
     cp.W = Wg <= 1 ? 1 : Wg <= 2 ? 2 : Wg <= 4 ? 4 : Wg <= 8 ? 8 : 16;
@@ -159,7 +160,7 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     plan_layout(cp, B, block, budget);
     cp.all_smem = cp.lay.slice_bytes == 0 && kbest_has_smem_variant(cp.W, cp.wide, cp.w32);
     int occ = 0;
-    cudaError_t e = kbest_occupancy(cp.W, cp.wide, cp.w32, cp.all_smem, block,
+    cudaError_t e = kbest_occupancy(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(B), block,
                                     (size_t)cp.lay.smem_bytes, &occ);
     if (e != cudaSuccess || occ < 1)
         return set_error(FASTGED_ERR_CUDA, "team does not fit on an SM");
@@ -254,7 +255,7 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     p.out_nevals = out_nevals;
     p.gscratch = base + off_teams;
     p.lay = cp.lay;
-    NA_CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, p, (int)grid, block,
+    NA_CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(B), p, (int)grid, block,
                        (size_t)cp.lay.smem_bytes, st));
     NA_CK(cudaMemcpyAsync(&host_err, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
