@@ -304,7 +304,6 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         return set_error(FASTGED_ERR_INVALID_ARG, "null graphs or pairs");
     if (opt.variant != 0 && opt.variant != 1)
         return set_error(FASTGED_ERR_INVALID_ARG, "variant must be 0 or 1");
-    if (opt.variant == 1) return set_error(FASTGED_ERR_INVALID_ARG, "variant 1 not built yet");
     if (opt.hist_window != 0 && (opt.hist_window < 2 || opt.hist_window > kHistMax))
         return set_error(FASTGED_ERR_INVALID_ARG, "hist_window out of range");
     if (opt.block_threads != 0 && opt.block_threads != 128 && opt.block_threads != 256 &&

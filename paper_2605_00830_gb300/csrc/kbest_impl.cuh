@@ -465,6 +465,88 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         __syncthreads();
         PHASE_MARK(1);
 
+        if (p.variant == 1 && i == n1 - 1) {
+            // variant B: every successor of the last level is completed (insertions of the
+            // free g2 vertices and their edges) and the least (total, PED, enumeration order)
+            // wins. Per node: nimg = |Img|, e2 = g2 edges inside Img (kept in klist / kped,
+            // which the selection does not use at this level).
+            for (int t = lane; t < s_hi - s_lo; t += 32) {
+                const int sl = s_lo + t;
+                const Word *im = imgc + (int64_t)sl * W;
+                int nimg = 0, acc = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    nimg += popcw(im[w]);
+                    Word x = im[w];
+                    while (x) {
+                        const int bt = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
+                        x &= x - (Word)1;
+                        const int u = w * WB + bt;
+#pragma unroll
+                        for (int w2 = 0; w2 < W; ++w2) acc += popcw((Word)(R.a2t[w2 * N2S + u] & im[w2]));
+                    }
+                }
+                R.kped[sl] = nimg;
+                R.klist[sl] = acc / 2;
+            }
+            __syncwarp();
+            auto leaf_total = [&](int k) -> long long {
+                const int idx = base + k;
+                const int sc = R.cslot[idx];
+                const int j = (int)cjv[idx];
+                const Word *im = imgc + (int64_t)sc * W;
+                int nimg = R.kped[sc], e2 = R.klist[sc];
+                if (j < n2) {
+                    ++nimg;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) e2 += popcw((Word)(R.a2t[w * N2S + j] & im[w]));
+                }
+                return (long long)R.cand[idx] + (long long)c.vins * (n2 - nimg) +
+                       (long long)c.eins * (m2.m - e2);
+            };
+            long long tmin = LLONG_MAX;
+            for (int k = lane; k < kw; k += 32) tmin = min(tmin, leaf_total(k));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, (long long)__shfl_xor_sync(0xffffffffu, tmin, o));
+            if (lane == 0) S.wbest[warp] = (unsigned long long)tmin;
+            __syncthreads();
+            long long best_total = LLONG_MAX;
+            for (int w = 0; w < NW; ++w) best_total = min(best_total, (long long)S.wbest[w]);
+            __syncthreads();
+            unsigned long long key = ~0ull;
+            for (int k = lane; k < kw; k += 32)
+                if (leaf_total(k) == best_total) {
+                    const unsigned long long kk =
+                        ((unsigned long long)R.cand[base + k] << 32) | (unsigned)(base + k);
+                    key = kk < key ? kk : key;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+                key = y < key ? y : key;
+            }
+            if (lane == 0) S.wbest[warp] = key;
+            __syncthreads();
+            unsigned long long bk = S.wbest[0];
+            for (int w = 1; w < NW; ++w) bk = S.wbest[w] < bk ? S.wbest[w] : bk;
+            const int widx = (int)(bk & 0xffffffffull);
+            const int ws = R.cslot[widx], wj = (int)cjv[widx];
+            int all = 0;
+            for (int w = 0; w < NW; ++w) all += S.wn[w];
+            if (tid == 0) {
+                p.out_cost[pair] = (int32_t)best_total;
+                if (p.out_nevals) p.out_nevals[pair] = nevals + 2LL * all;
+            }
+            const MapT *mb = (const MapT *)(mapc + (int64_t)ws * mrow);
+            int32_t *om = p.out_map + p.map_off[pair];
+            for (int k = tid; k < n1; k += T) {
+                const MapT v = (k == i) ? ((wj < n2) ? (MapT)wj : DEL) : mb[k];
+                om[k] = (v == DEL) ? -1 : (int32_t)v;
+            }
+            __syncthreads();
+            return;
+        }
+
         // ---- S4 selection ---------------------------------------------------------
         // histogram of PED - pmin over this warp's successors (ballot counting: lane b
         // keeps the count of bucket b; the last bucket collects every PED past the window)

@@ -213,3 +213,33 @@ def test_invalid_inputs():
         big_cost = (1 << 29,) * 6
         with F.FastGED(big_cost) as fg:
             fg.run(single([(g, h)], big_cost, 4))
+
+
+@pytest.mark.parametrize("cfg", ["config1", "config2", "config3"])
+def test_variant_b_complete_every_last_level_successor(cfg):
+    n = {"config1": 200, "config2": 150, "config3": 6}[cfg]
+    w = getattr(W, cfg)(n)
+    b = gpu_run(w, variant=1)
+    assert_parity(w, b, variant=1)
+    a = gpu_run(w)
+    assert np.all(b[0] <= a[0])   # completing a superset of leaves is never worse
+
+
+def test_golden_hand_traces_on_gpu():
+    """The hand-traced cases of Algorithm 1 (tests/golden) through the GPU path."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_traces.json")
+    for case in json.load(open(path))["cases"]:
+        def gr(d):
+            e = np.array(d["edges"], dtype=np.int32).reshape(-1, 2)
+            el = None if d.get("elabel") is None else np.array(d["elabel"], dtype=np.int32)
+            return W.Graph(d["n"], np.array(d["vlabel"], dtype=np.int32), e, el)
+        g1, g2 = gr(case["g1"]), gr(case["g2"])
+        for variant, key in ((0, "kbest"), (1, "kbest_variant1")):
+            for exp in case.get(key, []):
+                w = single([(g1, g2)], case["cost"], exp["K"])
+                cost, maps, nev = gpu_run(w, variant=variant)
+                assert int(cost[0]) == exp["cost"], (case["name"], exp)
+                assert maps.tolist() == exp["map"], (case["name"], exp)
+                assert int(nev[0]) == exp["n_evals"], (case["name"], exp)
