@@ -49,7 +49,9 @@ def parse_args():
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the plain-form, e2e and CPU-baseline legs")
+                    help="skip the plain-form, e2e, serving and CPU-baseline legs")
+    ap.add_argument("--serve-window", type=float, default=2.0,
+                    help="seconds of Poisson arrivals in the serving leg")
     return ap.parse_args()
 
 
@@ -134,6 +136,52 @@ def int_ops_per_eval(W: int, B: int, fold: bool) -> int:
     word = 7 if fold else 11
     lab = (4 * B + 5) if B > 0 else 0
     return (word + lab) * W + 6
+
+
+def serving_leg(window_s: float, rate: float = 5000.0):
+    """Continuous-batching server under a Poisson stream (the serving mix, setting-1 costs):
+    requests are submitted at their arrival times from one host thread while another
+    polls; returns latency percentiles and throughput."""
+    import threading
+    from paper_2605_00830_gb300 import fastged as F
+    from paper_2605_00830_gb300 import workloads as W
+    w = W.config5(duration_s=window_s, rate=rate, seed=5)
+    mm = F.marshal(w)
+    srv = F.Server(w.cost, F.serve_config())
+    lat, done, rejected = [], [0], [0]
+    stop = [False]
+
+    def poller():
+        while not stop[0] or done[0] < w.n_pairs - rejected[0]:
+            for r in srv.poll(timeout_ms=20):
+                lat.append(r[5])
+                done[0] += 1
+            if stop[0] and done[0] >= w.n_pairs - rejected[0]:
+                break
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for p in range(w.n_pairs):
+        delay = t0 + float(w.arrival[p]) - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        rc = srv.submit(mm, w.pairs[p][0], w.pairs[p][1], int(w.k_per_pair[p]), p)
+        if rc != 0:
+            rejected[0] += 1
+    stop[0] = True
+    th.join(timeout=600)
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"workload": "Poisson stream, serving mix (70/25/5 % molecule-like / dense ER / BA), "
+                        "K in {32,128,512}, setting-1 costs",
+            "offered_rps": rate, "window_s": window_s, "requests": int(w.n_pairs),
+            "completed": int(done[0]), "rejected": int(rejected[0]),
+            "pairs_per_s": done[0] / (t_end - t0), "wall_s": t_end - t0,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "batches": int(st["batches"]), "mean_batch": st["batched_pairs"] / max(1, st["batches"])}
 
 
 def run_cpu_oracle(w, idx, threads):
@@ -298,6 +346,8 @@ def ours(args):
         plain = mms.n_pairs / (pms / 1e3)
         line["plain_form"] = {"value": plain, "unit": UNIT, "sample_pairs": mms.n_pairs,
                               "batched_over_plain": value / ws / plain}
+        # serving: continuous batching under a Poisson stream
+        line["serve"] = serving_leg(args.serve_window)
         # CPU oracle on a bounded sample, all host cores
         threads = os.cpu_count() or 1
         idx = list(range(min(args.cpu_sample, w.n_pairs)))

@@ -179,6 +179,74 @@ int fastged_plan_kernel_ms(fastged_plan *p, float *ms);
 /* Releases the plan (waits for its last run). NULL is ignored. */
 void fastged_plan_destroy(fastged_plan *p);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: continuous batching of GED queries on one GPU.
+ *
+ * fastged_serve_submit copies a query (g1, g2, K) into the server and returns. A dispatcher
+ * thread keeps up to `lanes` batches in flight, each lane owning its own streams and
+ * grow-only device buffers (graph bit-sets, beams and outputs stay resident between
+ * batches). While batches run, newly arrived queries are grouped by size bucket (bit-set
+ * words of g2, K range) and launched as the next batch as soon as a lane is free and one of
+ * these holds: min_batch_pairs of the oldest query's bucket are pending, the oldest query
+ * has waited max_wait_us, or nothing else is running. Before launching, free device memory
+ * must exceed the batch's footprint plus hbm_reserve_bytes (otherwise the batch waits for a
+ * running one to finish). Results are identical to fastged_batch_ex on the same query.
+ * --------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t lanes;             /* batches in flight at most, 1..16 (default 4)             */
+    int32_t max_batch_pairs;   /* queries per batch at most (default 4096)                 */
+    int32_t min_batch_pairs;   /* launch once this many queries of a bucket wait (64)      */
+    int32_t max_pending;       /* queued queries at most; beyond: FASTGED_ERR_BUSY (2^20)  */
+    int32_t max_wait_us;       /* longest wait of the oldest query before launch (200)     */
+    int32_t pad;
+    int64_t hbm_reserve_bytes; /* device memory kept free by admission (1 GiB)             */
+} fastged_serve_config;
+
+typedef struct {
+    uint64_t tag;              /* the caller's tag from fastged_serve_submit                */
+    int32_t status;            /* FASTGED_OK or the error of the batch the query was in     */
+    int32_t cost;              /* GED upper bound                                           */
+    int32_t n1;                /* entries of the vertex map                                 */
+    int32_t pad;
+    int64_t map_offset;        /* first entry of the map in the poll's map buffer           */
+    int64_t n_evals;           /* successors scored plus leaves completed                   */
+    double latency_ms;         /* submit -> result ready                                    */
+    double queue_ms;           /* submit -> batch launch                                    */
+} fastged_serve_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, batches, batched_pairs, rejected_busy,
+        admission_waits, pending, lanes_busy;
+} fastged_serve_stats;
+
+/* Starts a server on the current device (cfg NULL = the defaults above). */
+int fastged_serve_start(const fastged_cost_model *cost, const fastged_serve_config *cfg,
+                        fastged_server **out);
+
+/* Queues one query; the graphs are copied, so the caller may reuse them at once. Returns
+ * FASTGED_ERR_INVALID_ARG for invalid graphs or K (same rules as fastged_batch, duplicate
+ * edges included), FASTGED_ERR_BUSY when max_pending queries are queued, and
+ * FASTGED_ERR_STOPPED after fastged_serve_stop. Thread-safe. */
+int fastged_serve_submit(fastged_server *s, const fastged_graph *g1, const fastged_graph *g2,
+                         int32_t K, uint64_t tag);
+
+/* Moves up to max_results finished queries into out[], their vertex maps into map_buf
+ * (capacity map_cap entries; each result's map_offset points into it), waiting up to
+ * timeout_ms for the first one. Returns the number of results (0 on timeout) or a negative
+ * status (FASTGED_ERR_INVALID_ARG if even the first map does not fit). */
+int fastged_serve_poll(fastged_server *s, fastged_serve_result *out, int32_t max_results,
+                       int32_t *map_buf, int64_t map_cap, int32_t timeout_ms);
+
+/* Counters of the server so far. */
+int fastged_serve_get_stats(fastged_server *s, fastged_serve_stats *out);
+
+/* Stops accepting queries, runs every queued one and waits for all batches; results stay
+ * available to fastged_serve_poll. */
+void fastged_serve_stop(fastged_server *s);
+
+/* Stops the server if needed and releases it (unpolled results are discarded). */
+void fastged_serve_destroy(fastged_server *s);
+
 /* Integer-pipe throughput of the current device (no counterpart in the paper; it is the
  * measured peak the benchmark compares the successor evaluation against). Runs three
  * short probe kernels issuing independent 32-bit LOP3, IADD and POPC chains on every SM

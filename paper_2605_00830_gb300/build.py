@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["kbest_kernels.cu", "kbest_b0.cu", "kbest_b2.cu", "kbest_b8.cu", "fastged_runtime.cu",
-           "probe_kernels.cu", "noalloc.cu"]
+           "probe_kernels.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         res = list(ex.map(one, SOURCES))
     objs = [o for o, _ in res]
     tmp = out + f".tmp{os.getpid()}"
-    cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

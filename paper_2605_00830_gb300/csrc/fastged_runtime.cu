@@ -186,7 +186,7 @@ extern "C" void fastged_destroy(fastged_handle *h)
 // ------------------------------------------------------------------------------------
 // flattening + validation
 // ------------------------------------------------------------------------------------
-static fastged_options default_options()
+fastged_options fastged::default_options()
 {
     fastged_options o;
     memset(&o, 0, sizeof(o));
@@ -435,7 +435,24 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     b.off_mapoff = o; o = align_up(o + 8 * (size_t)np, 256);
     b.off_kpp = o;    o = align_up(o + (kpp ? 4 * (size_t)np : 0), 256);
     b.in_bytes = o;
-    int rc = h->pin.ensure(std::max<size_t>(b.in_bytes, 256));
+    // device work region: [status | cost | nevals | map] then pools, queues, scratch
+    size_t w = 0;
+    b.woff_err = w;    w = align_up(w + 16, 256);
+    b.woff_cost = w;   w = align_up(w + 4 * (size_t)np, 256);
+    b.woff_nev = w;    w = align_up(w + 8 * (size_t)np, 256);
+    b.woff_map = w;    w = align_up(w + 4 * (size_t)mtot, 256);
+    b.out_bytes = w;   // one device-to-host copy covers [0, out_bytes)
+    b.woff_queue = w;  w = align_up(w + 4 * ((size_t)np + kMaxClasses), 256);
+    b.woff_pool = w;   w = align_up(w + 8 * (size_t)(b.adj_words + b.plane_words), 256);
+    size_t scratch = 0;
+    for (auto &cp : b.classes) {
+        cp.scratch_off = scratch;
+        scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)cp.grid, 256);
+    }
+    b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
+    b.work_bytes = w;
+    // the pinned staging buffer carries the inputs up and the results back
+    int rc = h->pin.ensure(std::max<size_t>(std::max(b.in_bytes, b.out_bytes), 256));
     if (rc) return rc;
     uint8_t *S = (uint8_t *)h->pin.p;
     memcpy(S + b.off_meta, b.meta.data(), sizeof(GraphMeta) * (size_t)ng);
@@ -472,22 +489,6 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     memcpy(S + b.off_mapoff, b.map_off.data(), 8 * (size_t)np);
     if (kpp) memcpy(S + b.off_kpp, kpp, 4 * (size_t)np);
 
-    // device work region: [status | cost | nevals | map] then pools, queues, scratch
-    size_t w = 0;
-    b.woff_err = w;    w = align_up(w + 16, 256);
-    b.woff_cost = w;   w = align_up(w + 4 * (size_t)np, 256);
-    b.woff_nev = w;    w = align_up(w + 8 * (size_t)np, 256);
-    b.woff_map = w;    w = align_up(w + 4 * (size_t)mtot, 256);
-    b.out_bytes = w;   // one device-to-host copy covers [0, out_bytes)
-    b.woff_queue = w;  w = align_up(w + 4 * ((size_t)np + kMaxClasses), 256);
-    b.woff_pool = w;   w = align_up(w + 8 * (size_t)(b.adj_words + b.plane_words), 256);
-    size_t scratch = 0;
-    for (auto &cp : b.classes) {
-        cp.scratch_off = scratch;
-        scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)cp.grid, 256);
-    }
-    b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
-    b.work_bytes = w;
     return FASTGED_OK;
 }
 
@@ -625,13 +626,9 @@ int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *ou
 // ------------------------------------------------------------------------------------
 // one-shot batch
 // ------------------------------------------------------------------------------------
-extern "C" int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
-                                const fastged_options *opt, int32_t *out_cost,
-                                int32_t *out_mapping, int64_t *out_nevals)
+int fastged::batch_enqueue(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                           const fastged_options &o)
 {
-    clear_error();
-    if (!h) return set_error(FASTGED_ERR_INVALID_ARG, "null handle");
-    const fastged_options o = opt ? *opt : default_options();
     Batch &b = h->batch;
     int rc = flatten(h, pairs, K, o, b);
     if (rc) return rc;
@@ -643,10 +640,28 @@ extern "C" int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pair
     rc = enqueue(h, b, (uint8_t *)h->dev_in.p, (uint8_t *)h->dev_work.p, st, nullptr);
     if (rc) return rc;
     // results come back through the (already consumed) staging buffer
-    if ((rc = h->pin.ensure(std::max(b.in_bytes, b.out_bytes)))) return rc;
     CK(cudaMemcpyAsync(h->pin.p, h->dev_work.p, b.out_bytes, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return finish_outputs(b, (const uint8_t *)h->pin.p, out_cost, out_mapping, out_nevals);
+    return FASTGED_OK;
+}
+
+int fastged::batch_results(fastged_handle *h, int32_t *out_cost, int32_t *out_mapping,
+                           int64_t *out_nevals)
+{
+    if (h->batch.n_pairs == 0) return FASTGED_OK;
+    return finish_outputs(h->batch, (const uint8_t *)h->pin.p, out_cost, out_mapping, out_nevals);
+}
+
+extern "C" int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                                const fastged_options *opt, int32_t *out_cost,
+                                int32_t *out_mapping, int64_t *out_nevals)
+{
+    clear_error();
+    if (!h) return set_error(FASTGED_ERR_INVALID_ARG, "null handle");
+    const fastged_options o = opt ? *opt : default_options();
+    int rc = batch_enqueue(h, pairs, K, o);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return batch_results(h, out_cost, out_mapping, out_nevals);
 }
 
 extern "C" int fastged_batch(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,

@@ -77,6 +77,14 @@ int enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk, cudaStr
             bool capturing = false);
 int finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *out_cost,
                    int32_t *out_mapping, int64_t *out_nevals);
+// asynchronous halves of fastged_batch_ex: enqueue everything (flatten, upload, kernels,
+// download into the handle's staging buffer) on h->stream; after the stream has finished,
+// copy the results out of the staging buffer
+int batch_enqueue(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
+                  const fastged_options &o);
+int batch_results(fastged_handle *h, int32_t *out_cost, int32_t *out_mapping,
+                  int64_t *out_nevals);
+fastged_options default_options();
 
 }  // namespace fastged
 

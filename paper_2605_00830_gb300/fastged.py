@@ -31,7 +31,9 @@ FASTGED_FORM_PLAIN = 1
 EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
             "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
             "fastged_plan_read", "fastged_plan_info", "fastged_plan_kernel_ms",
-            "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc"]
+            "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc",
+            "fastged_serve_start", "fastged_serve_submit", "fastged_serve_poll",
+            "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy"]
 
 
 class FastGEDError(RuntimeError):
@@ -83,6 +85,26 @@ class DeviceBatch(ctypes.Structure):
                 ("map_off", ctypes.c_void_p)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
+                ("min_batch_pairs", ctypes.c_int32), ("max_pending", ctypes.c_int32),
+                ("max_wait_us", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("hbm_reserve_bytes", ctypes.c_int64)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("cost", ctypes.c_int32),
+                ("n1", ctypes.c_int32), ("pad", ctypes.c_int32), ("map_offset", ctypes.c_int64),
+                ("n_evals", ctypes.c_int64), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "batches",
+                                              "batched_pairs", "rejected_busy",
+                                              "admission_waits", "pending", "lanes_busy")]
+
+
 _GRAPH_DTYPE = np.dtype({"names": ["n", "vlabel", "m", "edges", "elabel"],
                          "formats": ["<i4", "<u8", "<i4", "<u8", "<u8"],
                          "offsets": [0, 8, 16, 24, 32], "itemsize": 40})
@@ -124,9 +146,18 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_measure_int_peak.argtypes = [dp, dp, dp]
     lib.fastged_batch_noalloc.argtypes = [ctypes.POINTER(CostModel), ctypes.POINTER(DeviceBatch),
                                           i32, vp, vp, vp, vp]
+    lib.fastged_serve_start.argtypes = [ctypes.POINTER(CostModel), ctypes.POINTER(ServeConfig),
+                                        ctypes.POINTER(vp)]
+    lib.fastged_serve_submit.argtypes = [vp, vp, vp, i32, ctypes.c_uint64]
+    lib.fastged_serve_poll.argtypes = [vp, ctypes.POINTER(ServeResult), i32, vp, i64, i32]
+    lib.fastged_serve_get_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    lib.fastged_serve_stop.argtypes = [vp]
+    lib.fastged_serve_stop.restype = None
+    lib.fastged_serve_destroy.argtypes = [vp]
+    lib.fastged_serve_destroy.restype = None
     for name in EXPORTED:
         if name in ("fastged_destroy", "fastged_plan_destroy", "fastged_last_error",
-                    "fastged_version"):
+                    "fastged_version", "fastged_serve_stop", "fastged_serve_destroy"):
             continue
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
@@ -351,3 +382,63 @@ class FastGED:
         cost, maps, nev = _outputs(mm)
         fastged_batch_ex(self.h, mm, K, make_options(**opts), cost, maps, nev)
         return cost, maps, nev
+
+
+def serve_config(lanes=4, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
+                 max_wait_us=200, hbm_reserve_bytes=1 << 30) -> ServeConfig:
+    return ServeConfig(lanes, max_batch_pairs, min_batch_pairs, max_pending, max_wait_us, 0,
+                       hbm_reserve_bytes)
+
+
+class Server:
+    """Continuous-batching server (fastged_serve_*). Queries reference graphs of a marshalled
+    workload; results come back through poll()."""
+
+    def __init__(self, cost: Sequence[int], cfg: Optional[ServeConfig] = None):
+        self.lib = load()
+        s = ctypes.c_void_p()
+        _check(self.lib, self.lib.fastged_serve_start(
+            ctypes.byref(CostModel(*[int(x) for x in cost])),
+            ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(s)))
+        self.s = s.value
+
+    def submit(self, mm: "Marshalled", g1: int, g2: int, K: int, tag: int) -> int:
+        """Queue (graph g1, graph g2) of a marshalled workload; returns the status code."""
+        base = mm.gs.ctypes.data
+        return self.lib.fastged_serve_submit(self.s, base + 40 * int(g1), base + 40 * int(g2),
+                                             int(K), int(tag))
+
+    def poll(self, max_results: int = 4096, map_cap: int = 1 << 20, timeout_ms: int = 10):
+        """[(tag, status, cost, map, n_evals, latency_ms, queue_ms)] of finished queries."""
+        out = (ServeResult * max_results)()
+        buf = np.zeros(map_cap, np.int32)
+        n = self.lib.fastged_serve_poll(self.s, out, max_results, buf.ctypes.data, map_cap,
+                                        timeout_ms)
+        if n < 0:
+            _check(self.lib, n)
+        res = []
+        for r in out[:n]:
+            mp = buf[r.map_offset:r.map_offset + r.n1].copy()
+            res.append((r.tag, r.status, r.cost, mp, r.n_evals, r.latency_ms, r.queue_ms))
+        return res
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(self.lib, self.lib.fastged_serve_get_stats(self.s, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def stop(self):
+        if self.s:
+            self.lib.fastged_serve_stop(self.s)
+
+    def close(self):
+        if self.s:
+            self.lib.fastged_serve_destroy(self.s)
+            self.s = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
