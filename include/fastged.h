@@ -193,7 +193,8 @@ void fastged_plan_destroy(fastged_plan *p);
  * running one to finish). Results are identical to fastged_batch_ex on the same query.
  * --------------------------------------------------------------------------------------- */
 typedef struct {
-    int32_t lanes;             /* batches in flight at most, 1..16 (default 4)             */
+    int32_t lanes;             /* batches in flight at most, 1..16 (default 6); batches of */
+                               /* pairs with > 256 target vertices hold at most half      */
     int32_t max_batch_pairs;   /* queries per batch at most (default 4096)                 */
     int32_t min_batch_pairs;   /* launch once this many queries of a bucket wait (64)      */
     int32_t max_pending;       /* queued queries at most; beyond: FASTGED_ERR_BUSY (2^20)  */

@@ -50,6 +50,7 @@ struct Result {
 struct Lane {
     fastged_handle *h = nullptr;
     bool busy = false;
+    bool large = false;   // running a batch of large pairs
     bool done = false;
     std::vector<Request *> reqs;
     std::vector<fastged_graph> graphs;
@@ -70,6 +71,10 @@ int bucket_of(int n2, int K)
     const int k = K <= 32 ? 0 : K <= 128 ? 1 : K <= 512 ? 2 : 3;
     return w * 4 + k;
 }
+
+// Buckets of pairs with more than 256 target vertices: such batches run for long, so they
+// may hold at most half of the lanes and never starve the small queries.
+bool bucket_is_large(int bucket) { return bucket / 4 >= 4; }
 
 // The checks fastged_batch applies to one graph, plus duplicate edges (found by sorting).
 int validate_graph(const fastged_graph *g, bool *labelled)
@@ -251,14 +256,23 @@ static void dispatcher_main(fastged_server *s)
         if (s->stopping && s->pending.empty() && busy == 0) break;
         bool launched = false;
         if (free_lane && !s->pending.empty()) {
-            const Request *oldest = s->pending.front();
-            const int bkt = oldest->bucket;
+            int large_busy = 0;
+            for (const Lane &l : s->lanes) large_busy += (l.busy && l.large) ? 1 : 0;
+            const bool large_ok = large_busy < std::max(1, (int)s->lanes.size() / 2);
+            // the oldest query whose bucket may run now
+            const Request *oldest = nullptr;
+            for (const Request *q : s->pending)
+                if (large_ok || !bucket_is_large(q->bucket)) {
+                    oldest = q;
+                    break;
+                }
+            const int bkt = oldest ? oldest->bucket : -1;
             int avail = 0;
-            for (const Request *q : s->pending) avail += (q->bucket == bkt);
-            const double waited_us =
-                1e3 * ms_between(oldest->t_submit, Clock::now());
-            if (avail >= s->cfg.min_batch_pairs || waited_us >= s->cfg.max_wait_us ||
-                busy == 0 || s->stopping) {
+            if (oldest)
+                for (const Request *q : s->pending) avail += (q->bucket == bkt);
+            const double waited_us = oldest ? 1e3 * ms_between(oldest->t_submit, Clock::now()) : 0.0;
+            if (oldest && (avail >= s->cfg.min_batch_pairs || waited_us >= s->cfg.max_wait_us ||
+                           busy == 0 || s->stopping)) {
                 std::vector<Request *> take;
                 for (auto it = s->pending.begin();
                      it != s->pending.end() && (int)take.size() < s->cfg.max_batch_pairs;) {
@@ -279,6 +293,7 @@ static void dispatcher_main(fastged_server *s)
                     s->st.admission_waits++;
                 } else {
                     free_lane->reqs = std::move(take);
+                    free_lane->large = bucket_is_large(bkt);
                     launch_batch(s, *free_lane, lk);
                     launched = true;
                 }
@@ -293,7 +308,7 @@ static fastged_serve_config serve_defaults()
 {
     fastged_serve_config c;
     memset(&c, 0, sizeof(c));
-    c.lanes = 4;
+    c.lanes = 6;
     c.max_batch_pairs = 4096;
     c.min_batch_pairs = 64;
     c.max_pending = 1 << 20;

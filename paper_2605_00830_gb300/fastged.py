@@ -384,7 +384,7 @@ class FastGED:
         return cost, maps, nev
 
 
-def serve_config(lanes=4, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
+def serve_config(lanes=6, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
                  max_wait_us=200, hbm_reserve_bytes=1 << 30) -> ServeConfig:
     return ServeConfig(lanes, max_batch_pairs, min_batch_pairs, max_pending, max_wait_us, 0,
                        hbm_reserve_bytes)
