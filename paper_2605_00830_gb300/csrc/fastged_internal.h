@@ -20,7 +20,8 @@ namespace fastged {
 constexpr int kMaxWords = 16;       // 1024 vertices
 constexpr int kHistMax = 32;        // PED histogram buckets (one per lane)
 constexpr int kMaxB = 8;            // edge-label bit-planes (labels 0..255)
-constexpr int kMaxWarps = 16;       // 512 threads per team
+constexpr int kMaxWarps = 16;       // 512 threads per CTA
+constexpr int kMaxClusterWarps = 256; // 16 CTAs of 512 threads
 
 struct CostModel {
     int32_t vsub, vdel, vins, esub, edel, eins;
@@ -53,8 +54,9 @@ struct Layout {
     int32_t fs;                // successors per node at most (n2max + 1)
     int32_t word_bytes;        // 4 or 8: bytes per bitset word
     int32_t B;                 // edge-label planes
-    int64_t smem_bytes;        // dynamic shared memory per team
-    int64_t slice_bytes;       // global scratch bytes per team
+    int64_t smem_bytes;        // dynamic shared memory per CTA
+    int64_t slice_bytes;       // global scratch bytes per team (CTA or cluster)
+    int64_t team_off;          // cluster teams: offset of the team scalars in the slice
 };
 
 struct KParams {

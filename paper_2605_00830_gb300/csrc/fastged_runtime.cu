@@ -30,6 +30,11 @@ cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, int bk, const 
 cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int block,
                             size_t smem, int *out);
 bool kbest_has_smem_variant(int W, bool wide, bool w32);
+bool kbest_has_cluster_variant(int W, bool wide, bool w32);
+cudaError_t launch_kbest_cluster(int W, int bk, const KParams &p, int grid, int block,
+                                 size_t smem, int cluster, cudaStream_t st);
+cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int cluster, int *out);
+size_t team_shared_cluster_bytes();
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
 }  // namespace fastged
@@ -197,7 +202,7 @@ fastged_options fastged::default_options()
 void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
 {
     Layout &L = cp.lay;
-    const int NW = block / 32;
+    const int NW = (block / 32) * cp.cluster;   // warps of the whole team
     const int W = cp.W;
     const size_t msz = cp.wide ? 2 : 1;
     const size_t wb = cp.w32 ? 4 : 8;
@@ -239,12 +244,17 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
                                        RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_NOFF,
                                        RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
                                        RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1};
+    // a cluster team shares only global memory: its CTAs keep private shared-memory copies
+    // of the read-only target-graph tables and neighbour lists, everything else is global
+    auto cta_local = [](int r) {
+        return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR;
+    };
     size_t s_used = 0, g_used = 0;
     L.smem_mask = 0;
     for (int k = 0; k < RG_COUNT; ++k) {
         const int r = prio[k];
         const size_t a = align_up(sz[r], 16);
-        if (s_used + a <= budget) {
+        if (s_used + a <= budget && (cp.cluster == 1 || cta_local(r))) {
             L.off[r] = (int64_t)s_used;
             L.smem_mask |= 1u << r;
             s_used += a;
@@ -253,6 +263,8 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
             g_used += a;
         }
     }
+    L.team_off = (int64_t)align_up(g_used, 256);
+    if (cp.cluster > 1) g_used = (size_t)L.team_off + team_shared_cluster_bytes();
     L.smem_bytes = (int64_t)s_used;
     L.slice_bytes = (int64_t)align_up(g_used, 256);
 }
@@ -264,14 +276,38 @@ static size_t layout_total(const ClassPlan &cp, int B, int block)
     return (size_t)t.lay.smem_bytes;
 }
 
-// Chooses threads per team and the shared-memory budget of a class.
+// Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
+// Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
+// CTAs per pair.
 static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
 {
-    int block = forced_block;
-    if (block == 0) block = cp.kmax <= 32 ? 128 : 256;
     const size_t stat = team_shared_static_bytes() + 1024;   // + per-block reservation
     const size_t per_sm = (size_t)h->smem_per_sm;
     const size_t max_dyn = (size_t)h->smem_optin - team_shared_static_bytes();
+    const int npairs = (int)std::max<size_t>(cp.order.size(), 1);
+    if (kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) && npairs < h->sm_count) {
+        const char *env = getenv("FASTGED_CLUSTER");
+        int cl = env ? atoi(env) : 8;
+        if (cl == 1 || cl == 2 || cl == 4 || cl == 8 || cl == 16) {
+            cp.cluster = cl;
+        }
+    }
+    if (cp.cluster > 1) {
+        const int block = forced_block ? forced_block : 512;
+        plan_layout(cp, B, block, max_dyn);
+        int nclu = 0;
+        cudaError_t e = kbest_cluster_occupancy(cp.W, label_instance(B), block,
+                                                (size_t)cp.lay.smem_bytes, cp.cluster, &nclu);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+        if (nclu < 1) return set_error(FASTGED_ERR_CUDA, "a cluster team does not fit the GPU");
+        cp.block = block;
+        cp.smem = (size_t)cp.lay.smem_bytes;
+        cp.all_smem = false;
+        cp.grid = std::min(nclu, npairs) * cp.cluster;
+        return FASTGED_OK;
+    }
+    int block = forced_block;
+    if (block == 0) block = cp.kmax <= 32 ? 128 : 256;
     const size_t total = layout_total(cp, B, block);
     size_t budget;
     if (total + stat <= per_sm / 2 && total <= max_dyn) {
@@ -447,7 +483,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     size_t scratch = 0;
     for (auto &cp : b.classes) {
         cp.scratch_off = scratch;
-        scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)cp.grid, 256);
+        scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)(cp.grid / cp.cluster), 256);
     }
     b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
     b.work_bytes = w;
@@ -586,13 +622,23 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             p.order += pos[pr];
             p.n_order = 1;
             p.queue_head = qbase + pr;
-            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, 1, cp.block, cp.smem, st));
+            if (cp.cluster > 1)
+                CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.cluster, cp.block, cp.smem,
+                                        cp.cluster, st));
+            else
+                CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, 1,
+                                cp.block, cp.smem, st));
             ++nl;
         }
     } else if (nc == 1) {
         const ClassPlan &cp = b.classes[0];
         KParams p = make_params(h, b, 0, in, wk);
-        CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid, cp.block, cp.smem, st));
+        if (cp.cluster > 1)
+            CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
+                                    cp.cluster, st));
+        else
+            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid,
+                            cp.block, cp.smem, st));
         ++nl;
     } else if (nc > 1) {
         CK(cudaEventRecord(h->ev[kMaxClasses], st));
@@ -600,7 +646,12 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             const ClassPlan &cp = b.classes[k];
             CK(cudaStreamWaitEvent(h->class_stream[k], h->ev[kMaxClasses], 0));
             KParams p = make_params(h, b, k, in, wk);
-            CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid, cp.block, cp.smem, h->class_stream[k]));
+            if (cp.cluster > 1)
+                CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
+                                        cp.cluster, h->class_stream[k]));
+            else
+                CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p,
+                                cp.grid, cp.block, cp.smem, h->class_stream[k]));
             ++nl;
             CK(cudaEventRecord(h->ev[k], h->class_stream[k]));
             CK(cudaStreamWaitEvent(st, h->ev[k], 0));

@@ -34,6 +34,7 @@ struct ClassPlan {
     bool wide = false;
     bool w32 = false;             // one 32-bit word per bitset (every g2 has <= 32 vertices)
     bool all_smem = false;        // every region of a team fits in shared memory
+    int cluster = 1;              // CTAs per team (> 1: a thread-block cluster per pair)
     int n1max = 0, n2max = 0, m1max = 0, kmax = 1;
     std::vector<int32_t> order;   // pair indices, heaviest first
     int64_t order_off = 0;        // offset of this class's order in the device order array

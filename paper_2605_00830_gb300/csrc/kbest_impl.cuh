@@ -56,15 +56,65 @@ __device__ __forceinline__ uint64_t low_mask(int i, int w)
 // ------------------------------------------------------------------------------------
 // K-Best teams
 // ------------------------------------------------------------------------------------
-struct TeamShared {
+// Team scalars: in shared memory for a one-CTA team, in the cluster's global scratch for a
+// cluster team (MW = warps the team may have).
+template <int MW>
+struct TeamSharedT {
     int pair;
     int cnt;
     int mx;
-    int wmin[kMaxWarps];  // least successor PED each warp scored at this level
-    int wn[kMaxWarps];    // successors each warp scored at this level
-    int wlt[kMaxWarps];
-    int weq[kMaxWarps];
-    unsigned long long wbest[kMaxWarps];
+    int wmin[MW];  // least successor PED each warp scored at this level
+    int wn[MW];    // successors each warp scored at this level
+    int wlt[MW];
+    int weq[MW];
+    unsigned long long wbest[MW];
+};
+using TeamShared = TeamSharedT<kMaxWarps>;
+using TeamSharedCl = TeamSharedT<kMaxClusterWarps>;
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier over every thread of the cluster; writes before it (shared or global) are visible
+// to every thread of the cluster after it (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+}
+
+// The threads solving one pair: one CTA, or every CTA of a cluster (CL).
+template <bool CL>
+struct Team {
+    int tid, T, warp, NW;
+    __device__ __forceinline__ Team()
+    {
+        if (CL) {
+            tid = (int)cluster_rank() * (int)blockDim.x + (int)threadIdx.x;
+            T = (int)cluster_size() * (int)blockDim.x;
+        } else {
+            tid = (int)threadIdx.x;
+            T = (int)blockDim.x;
+        }
+        warp = tid >> 5;
+        NW = T >> 5;
+    }
+    __device__ __forceinline__ void sync() const
+    {
+        if (CL) cluster_barrier();
+        else __syncthreads();
+    }
 };
 
 template <typename Word>
@@ -136,14 +186,15 @@ __device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, i
 // Exact selection used when the kept set reaches past the histogram window: the K-th
 // smallest PED is found by bisection over team-wide counts, the kept candidates are
 // compacted stably, and ranked by (PED, enumeration order).
-template <typename MapT, typename Word>
+template <typename MapT, typename Word, bool CL, typename TS>
 __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
                                           const uint16_t *cslot, const uint8_t *cj_b,
-                                          int32_t *sel, int32_t *selped, TeamShared &S, int L,
+                                          int32_t *sel, int32_t *selped, TS &S, int L,
                                           int stride, int newL, int lo)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = blockDim.x, NW = T >> 5;
+    const Team<CL> tm;
+    const int tid = tm.tid, lane = threadIdx.x & 31, warp = tm.warp;
+    const int T = tm.T, NW = tm.NW;
     const int s_lo = (warp * L) / NW;
     const int base = s_lo * stride, n = S.wn[warp];
     Regions<Word> R;
@@ -156,9 +207,9 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
-    __syncthreads();
+    tm.sync();
     if (lane == 0) atomicMax(&S.mx, mx);
-    __syncthreads();
+    tm.sync();
     int hi = S.mx;
     if (lo > hi) lo = hi;
     // invariant: count(PED < lo) < newL <= count(PED <= hi)
@@ -167,11 +218,11 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
         int cnt = 0;
         for (int k = lane; k < n; k += 32) cnt += (cand[base + k] <= mid);
         cnt = warp_sum(cnt);
-        __syncthreads();
+        tm.sync();
         if (tid == 0) S.cnt = 0;
-        __syncthreads();
+        tm.sync();
         if (lane == 0) atomicAdd(&S.cnt, cnt);
-        __syncthreads();
+        tm.sync();
         if (S.cnt >= newL) hi = mid; else lo = mid + 1;
     }
     const int thr = lo;
@@ -184,7 +235,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     nlt = warp_sum(nlt);
     neq = warp_sum(neq);
     if (lane == 0) { S.wlt[warp] = nlt; S.weq[warp] = neq; }
-    __syncthreads();
+    tm.sync();
     int lt_all = 0;
     for (int w = 0; w < NW; ++w) lt_all += S.wlt[w];
     const int q = newL - lt_all;
@@ -195,7 +246,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     }
     keep_before += min(q, eq_before);
     compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before);
-    __syncthreads();
+    tm.sync();
     // rank by (PED, enumeration order); klist is in enumeration order
     const MapT *cj = (const MapT *)cj_b;
     for (int a = tid; a < newL; a += T) {
@@ -213,13 +264,18 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
 
 // BK: edge-label planes known at compile time: 0 (unlabelled), 2 (exactly two planes), or
 // 8 (any count up to 8, read from the layout)
-template <int W, typename MapT, typename Word, int BK>
-__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word> R,
-                                           TeamShared &S, const int pair)
+// CL: the team is a whole cluster (S then lives in global scratch); regions the team
+// writes are global, the read-only target-graph tables are per CTA in shared memory.
+template <int W, typename MapT, typename Word, int BK, bool CL, typename TS>
+__device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word> R, TS &S,
+                                           const int pair)
 {
     constexpr int WB = 8 * (int)sizeof(Word);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = blockDim.x, NW = T >> 5;
+    const Team<CL> tm;
+    const int tid = tm.tid, lane = threadIdx.x & 31, warp = tm.warp;
+    const int T = tm.T, NW = tm.NW;
+    // CTA-local threads (staging of the per-CTA read-only tables)
+    const int ltid = threadIdx.x, LT = blockDim.x;
     const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
     const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
     const int n1 = m1.n, n2 = m2.n, W1 = m1.W, W2 = m2.W;
@@ -243,41 +299,40 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     long long ph_last = clock64();
 #endif
 
-    // stage g2: transposed adjacency and label planes, vertex labels; g1 degrees
+    // stage g2: transposed adjacency and label planes, vertex labels; g1 degrees (these
+    // tables are per CTA)
     {
         const uint64_t *adj2 = p.adj + m2.adj_off;
-        for (int idx = tid; idx < W * n2; idx += T) {
+        for (int idx = ltid; idx < W * n2; idx += LT) {
             const int w = idx / n2, u = idx - w * n2;
             const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
             R.a2t[w * N2S + u] = (w64 < W2) ? (Word)(adj2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
         }
         for (int b = 0; b < B; ++b) {
             const uint64_t *pl2 = p.planes + m2.plane_off + (int64_t)b * n2 * W2;
-            for (int idx = tid; idx < W * n2; idx += T) {
+            for (int idx = ltid; idx < W * n2; idx += LT) {
                 const int w = idx / n2, u = idx - w * n2;
                 const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
                 R.l2t[(b * W + w) * N2S + u] =
                     (w64 < W2) ? (Word)(pl2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
             }
         }
-        for (int u = tid; u < n2; u += T) R.alpha2[u] = p.vlab[m2.lab_off + u];
+        for (int u = ltid; u < n2; u += LT) R.alpha2[u] = p.vlab[m2.lab_off + u];
         // number of neighbours v_k of v_i with k < i
-        for (int v = tid; v < n1; v += T) {
+        for (int v = ltid; v < n1; v += LT) {
             const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
             int d = 0;
             for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
             R.noff[v + 1] = d;
         }
+        if (ltid == 0) R.noff[0] = 0;
         // root node: empty lambda, R_V2 = V2, PED 0
         for (int w = tid; w < W; w += T) R.img0[w] = (Word)0;
-        if (tid == 0) {
-            R.ped0[0] = 0;
-            R.noff[0] = 0;
-        }
+        if (tid == 0) R.ped0[0] = 0;
     }
     __syncthreads();
     // prior-neighbour lists of g1: nbr[noff[i] .. noff[i+1]) = k | (edge label << 16)
-    if (warp == 0) {
+    if (ltid < 32) {
         int carry = 0;
         for (int v0 = 0; v0 < n1; v0 += 32) {
             const int v = v0 + lane;
@@ -293,7 +348,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
     }
     __syncthreads();
-    for (int v = tid; v < n1; v += T) {
+    for (int v = ltid; v < n1; v += LT) {
         const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
         const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
         const int64_t pstep = (int64_t)n1 * W1;
@@ -315,7 +370,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     uint8_t *mapc = R.map0, *mapn = R.map1;
     Word *imgc = R.img0, *imgn = R.img1;
     int32_t *pedc = R.ped0, *pedn = R.ped1;
-    __syncthreads();
+    tm.sync();
     PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
@@ -462,7 +517,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             S.wmin[warp] = wmin;
             S.wn[warp] = kw;
         }
-        __syncthreads();
+        tm.sync();
         PHASE_MARK(1);
 
         if (p.variant == 1 && i == n1 - 1) {
@@ -509,10 +564,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, (long long)__shfl_xor_sync(0xffffffffu, tmin, o));
             if (lane == 0) S.wbest[warp] = (unsigned long long)tmin;
-            __syncthreads();
+            tm.sync();
             long long best_total = LLONG_MAX;
             for (int w = 0; w < NW; ++w) best_total = min(best_total, (long long)S.wbest[w]);
-            __syncthreads();
+            tm.sync();
             unsigned long long key = ~0ull;
             for (int k = lane; k < kw; k += 32)
                 if (leaf_total(k) == best_total) {
@@ -526,7 +581,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 key = y < key ? y : key;
             }
             if (lane == 0) S.wbest[warp] = key;
-            __syncthreads();
+            tm.sync();
             unsigned long long bk = S.wbest[0];
             for (int w = 1; w < NW; ++w) bk = S.wbest[w] < bk ? S.wbest[w] : bk;
             const int widx = (int)(bk & 0xffffffffull);
@@ -543,7 +598,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 const MapT v = (k == i) ? ((wj < n2) ? (MapT)wj : DEL) : mb[k];
                 om[k] = (v == DEL) ? -1 : (int32_t)v;
             }
-            __syncthreads();
+            tm.sync();
             return;
         }
 
@@ -569,7 +624,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             }
             R.hist[lane * NW + warp] = hreg;
         }
-        __syncthreads();
+        tm.sync();
         // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
         // and the bucket-b successors of the warps before this one
         int tot = 0, mine = 0;
@@ -619,10 +674,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 run += __popc(m);
             }
         } else {
-            select_exact<MapT, Word>(R.cand, R.klist, R.kped, R.cslot, R.cj, R.sel, R.selped, S,
-                                     L, stride, newL, pmin + hwin - 1);
+            select_exact<MapT, Word, CL, TS>(R.cand, R.klist, R.kped, R.cslot, R.cj, R.sel,
+                                             R.selped, S, L, stride, newL, pmin + hwin - 1);
         }
-        __syncthreads();
+        tm.sync();
         PHASE_MARK(2);
 
         // ---- kept children, in key order (slot = rank) -----------------------------
@@ -664,7 +719,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 }
             }
         }
-        __syncthreads();
+        tm.sync();
         PHASE_MARK(3);
         { uint8_t *t = mapc; mapc = mapn; mapn = t; }
         { Word *t = imgc; imgc = imgn; imgn = t; }
@@ -695,7 +750,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             best = key < best ? key : best;
         }
         if (lane == 0) S.wbest[warp] = best;
-        __syncthreads();
+        tm.sync();
         if (tid == 0) {
             unsigned long long b = S.wbest[0];
             for (int w = 1; w < NW; ++w) b = S.wbest[w] < b ? S.wbest[w] : b;
@@ -703,7 +758,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             p.out_cost[pair] = (int32_t)(b >> 32);
             if (p.out_nevals) p.out_nevals[pair] = nevals + L;
         }
-        __syncthreads();
+        tm.sync();
         const int bs = (int)(S.wbest[0] & 0xffffffffull);
         const MapT *mb = (const MapT *)(mapc + (int64_t)bs * mrow);
         int32_t *om = p.out_map + p.map_off[pair];
@@ -711,7 +766,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const MapT v = mb[k];
             om[k] = (v == DEL) ? -1 : (int32_t)v;
         }
-        __syncthreads();
+        tm.sync();
         PHASE_MARK(4);
     }
 #ifdef FASTGED_PHASE_TIMERS
@@ -720,17 +775,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #endif
 }
 
-// SM: every region lives in shared memory (addresses then stay in the shared window)
-template <int W, typename MapT, typename Word, bool SM, int BK>
-__global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
+// Region pointers of a team from a region -> base address function.
+template <typename Word, typename F>
+__device__ __forceinline__ Regions<Word> make_regions(F base)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ TeamShared S;
-    uint8_t *gs = p.gscratch + (int64_t)blockIdx.x * p.lay.slice_bytes;
-    auto base = [&](int r) -> uint8_t * {
-        if (SM) return smem + p.lay.off[r];
-        return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
-    };
     Regions<Word> R;
     R.hist = (int32_t *)base(RG_HIST);
     R.alpha2 = (int32_t *)base(RG_ALPHA2);
@@ -754,14 +802,52 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
     R.map1 = base(RG_MAP1);
+    return R;
+}
 
+// SM: every region lives in shared memory (addresses then stay in the shared window)
+template <int W, typename MapT, typename Word, bool SM, int BK>
+__global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ TeamShared S;
+    uint8_t *gs = p.gscratch + (int64_t)blockIdx.x * p.lay.slice_bytes;
+    auto base = [&](int r) -> uint8_t * {
+        if (SM) return smem + p.lay.off[r];
+        return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
+    };
+    const Regions<Word> R = make_regions<Word>(base);
     for (;;) {
         if (threadIdx.x == 0) S.pair = atomicAdd(p.queue_head, 1);
         __syncthreads();
         const int qi = S.pair;
         __syncthreads();
         if (qi >= p.n_order) break;
-        solve_pair<W, MapT, Word, BK>(p, R, S, p.order[qi]);
+        solve_pair<W, MapT, Word, BK, false, TeamShared>(p, R, S, p.order[qi]);
+    }
+}
+
+// One pair per thread-block cluster: every CTA of the cluster belongs to the team. Each
+// CTA keeps its own copy of the read-only target-graph tables; what the team writes lives in
+// the cluster's slice of global scratch, together with the team scalars.
+template <int W, typename MapT, typename Word, int BK>
+__global__ void __launch_bounds__(512, 1) kbest_cluster_kernel(const KParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const unsigned crank = cluster_rank(), csize = cluster_size();
+    uint8_t *gs = p.gscratch + (int64_t)(blockIdx.x / csize) * p.lay.slice_bytes;
+    auto base = [&](int r) -> uint8_t * {
+        return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
+    };
+    const Regions<Word> R = make_regions<Word>(base);
+    TeamSharedCl &S = *(TeamSharedCl *)(gs + p.lay.team_off);
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) S.pair = atomicAdd(p.queue_head, 1);
+        cluster_barrier();
+        const int qi = *(volatile int *)&S.pair;
+        cluster_barrier();
+        if (qi >= p.n_order) break;
+        solve_pair<W, MapT, Word, BK, true, TeamSharedCl>(p, R, S, p.order[qi]);
     }
 }
 
@@ -830,6 +916,96 @@ static cudaError_t occupancy_one(int block, size_t smem, int *out)
         }                                                                                \
         return cudaErrorInvalidValue;                                                    \
     } while (0)
+
+template <int W, typename MapT, typename Word, int BK>
+static cudaError_t ensure_cluster_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_cluster_kernel<W, MapT, Word, BK>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kbest_cluster_kernel<W, MapT, Word, BK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kbest_cluster_kernel<W, MapT, Word, BK>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int W, typename MapT, typename Word, int BK>
+static cudaError_t cluster_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, int grid,
+                                  int block, size_t smem, int cluster, cudaStream_t st)
+{
+    cudaError_t e = ensure_cluster_attr<W, MapT, Word, BK>();
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return e;
+}
+
+template <int W, typename MapT, typename Word, int BK>
+static cudaError_t launch_cluster_one(const KParams &p, int grid, int block, size_t smem,
+                                      int cluster, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    cudaError_t e = cluster_config<W, MapT, Word, BK>(cfg, attr, grid, block, smem, cluster, st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, kbest_cluster_kernel<W, MapT, Word, BK>, p);
+}
+
+template <int W, typename MapT, typename Word, int BK>
+static cudaError_t cluster_occupancy_one(int block, size_t smem, int cluster, int *out)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    cudaError_t e = cluster_config<W, MapT, Word, BK>(cfg, attr, cluster, block, smem, cluster,
+                                                      nullptr);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(out, kbest_cluster_kernel<W, MapT, Word, BK>, &cfg);
+}
+
+// cluster teams are built for the 16-bit-map classes of 4, 8 and 16 words
+#define FASTGED_CLUSTER_DISPATCH(W_, CALL)                                               \
+    do {                                                                                 \
+        switch (W_) {                                                                    \
+        case 4: return CALL(4, uint16_t, uint64_t);                                      \
+        case 8: return CALL(8, uint16_t, uint64_t);                                      \
+        case 16: return CALL(16, uint16_t, uint64_t);                                    \
+        default: return cudaErrorInvalidValue;                                           \
+        }                                                                                \
+    } while (0)
+
+template <int BK>
+cudaError_t launch_kbest_cluster_bk(int W, const KParams &p, int grid, int block, size_t smem,
+                                    int cluster, cudaStream_t st)
+{
+#define CALL_CL(w, M, Wd) launch_cluster_one<w, M, Wd, BK>(p, grid, block, smem, cluster, st)
+    FASTGED_CLUSTER_DISPATCH(W, CALL_CL);
+#undef CALL_CL
+}
+
+template <int BK>
+cudaError_t kbest_cluster_occupancy_bk(int W, int block, size_t smem, int cluster, int *out)
+{
+#define CALL_CO(w, M, Wd) cluster_occupancy_one<w, M, Wd, BK>(block, smem, cluster, out)
+    FASTGED_CLUSTER_DISPATCH(W, CALL_CO);
+#undef CALL_CO
+}
 
 template <int BK>
 cudaError_t launch_kbest_bk(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,

@@ -82,6 +82,29 @@ cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int
     return kbest_occupancy_bk<8>(W, wide_map, w32, sm, block, smem, out);
 }
 
+template <int BK>
+cudaError_t launch_kbest_cluster_bk(int W, const KParams &p, int grid, int block, size_t smem,
+                                    int cluster, cudaStream_t st);
+template <int BK>
+cudaError_t kbest_cluster_occupancy_bk(int W, int block, size_t smem, int cluster, int *out);
+
+bool kbest_has_cluster_variant(int W, bool wide, bool w32) { return !w32 && wide && W >= 4; }
+
+cudaError_t launch_kbest_cluster(int W, int bk, const KParams &p, int grid, int block,
+                                 size_t smem, int cluster, cudaStream_t st)
+{
+    if (bk == 0) return launch_kbest_cluster_bk<0>(W, p, grid, block, smem, cluster, st);
+    if (bk == 2) return launch_kbest_cluster_bk<2>(W, p, grid, block, smem, cluster, st);
+    return launch_kbest_cluster_bk<8>(W, p, grid, block, smem, cluster, st);
+}
+
+cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int cluster, int *out)
+{
+    if (bk == 0) return kbest_cluster_occupancy_bk<0>(W, block, smem, cluster, out);
+    if (bk == 2) return kbest_cluster_occupancy_bk<2>(W, block, smem, cluster, out);
+    return kbest_cluster_occupancy_bk<8>(W, block, smem, cluster, out);
+}
+
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
 {
     const int block = 256;
@@ -94,5 +117,6 @@ cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)
 
 // upper bound of the kernels' static shared memory (the team's scalars)
 size_t team_shared_static_bytes() { return sizeof(TeamShared) + 256; }
+size_t team_shared_cluster_bytes() { return sizeof(TeamSharedCl); }
 
 }  // namespace fastged

@@ -243,3 +243,16 @@ def test_golden_hand_traces_on_gpu():
                 assert int(cost[0]) == exp["cost"], (case["name"], exp)
                 assert maps.tolist() == exp["map"], (case["name"], exp)
                 assert int(nev[0]) == exp["n_evals"], (case["name"], exp)
+
+
+@pytest.mark.parametrize("cl", ["1", "2", "4", "8", "16"])
+def test_cluster_teams_match_oracle(cl, monkeypatch):
+    """Large pairs (16-bit maps, 4 to 16 words) solved by one CTA or by clusters of 2 to 16
+    CTAs sharing the beam through global memory: identical results."""
+    monkeypatch.setenv("FASTGED_CLUSTER", cl)
+    w = W.config4(3, seed=43, n_range=(260, 700))
+    w.K = 40
+    assert_parity(w, gpu_run(w))
+    w2 = W.config4(2, seed=44, n_range=(255, 300))
+    w2.K = 300
+    assert_parity(w2, gpu_run(w2, variant=1), variant=1)
