@@ -38,7 +38,7 @@ struct GraphMeta {
 enum Region : int {
     RG_HIST = 0, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1, RG_SEL, RG_SELPED,
     RG_KLIST, RG_KPED, RG_NOFF, RG_NBR, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CSLOT, RG_CJ,
-    RG_CAND, RG_MAP0, RG_MAP1,
+    RG_CAND, RG_MAP0, RG_MAP1, RG_IMGL,
     RG_COUNT
 };
 
@@ -48,6 +48,7 @@ struct Layout {
     int64_t off[RG_COUNT];     // byte offset inside shared memory or the global slice
     uint32_t smem_mask;        // bit r set: region r lives in shared memory
     int32_t kmax;              // slots per beam buffer
+    int32_t kloc;              // node slots a CTA prepares (kmax, or its share of a cluster)
     int32_t n1max, n2max;      // largest graphs of the class
     int32_t n2s;               // row stride (elements) of the transposed g2 tables
     int32_t mrow;              // bytes per stored vertex map

@@ -217,11 +217,14 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     size_t sz[RG_COUNT];
     const size_t km = (size_t)cp.kmax;
     const size_t ncand = km * ((size_t)cp.n2max + 1);
+    // node slots a CTA prepares: all of them, or its share of a cluster team
+    const size_t kl = cp.cluster > 1 ? (km + cp.cluster - 1) / cp.cluster + 1 : km;
+    L.kloc = (int32_t)kl;
     sz[RG_HIST] = (size_t)kHistMax * NW * 4;
     sz[RG_ALPHA2] = (size_t)L.n2s * 4;
     sz[RG_A2T] = (size_t)W * L.n2s * wb;
     sz[RG_L2T] = (size_t)B * W * L.n2s * wb;
-    sz[RG_SBASE] = km * 4;
+    sz[RG_SBASE] = kl * 4;
     sz[RG_PED0] = km * 4;
     sz[RG_PED1] = km * 4;
     sz[RG_SEL] = km * 4;
@@ -232,8 +235,9 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_NBR] = (size_t)std::max(cp.m1max, 1) * 4;
     sz[RG_IMG0] = km * W * wb;
     sz[RG_IMG1] = km * W * wb;
-    sz[RG_P] = km * W * wb;
-    sz[RG_PL] = (size_t)B * km * W * wb;
+    sz[RG_P] = kl * W * wb;
+    sz[RG_PL] = (size_t)B * kl * W * wb;
+    sz[RG_IMGL] = cp.cluster > 1 ? kl * W * wb : 0;
     sz[RG_CSLOT] = ncand * 2;
     sz[RG_CJ] = ncand * msz;
     sz[RG_CAND] = ncand * 4;
@@ -243,16 +247,24 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     static const int prio[RG_COUNT] = {RG_HIST, RG_ALPHA2, RG_SBASE, RG_PED0, RG_PED1,
                                        RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_NOFF,
                                        RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
-                                       RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1};
+                                       RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1,
+                                       RG_IMGL};
+    // cluster teams: the per-CTA tables the CTA writes (P, PL, sbase, staged Img) must be in
+    // shared memory, so they come first
+    static const int prio_cl[RG_COUNT] = {RG_SBASE, RG_P, RG_PL, RG_IMGL, RG_ALPHA2, RG_NOFF,
+                                          RG_A2T, RG_L2T, RG_NBR, RG_HIST, RG_PED0, RG_PED1,
+                                          RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_IMG0,
+                                          RG_IMG1, RG_CSLOT, RG_CJ, RG_CAND, RG_MAP0, RG_MAP1};
     // a cluster team shares only global memory: its CTAs keep private shared-memory copies
     // of the read-only target-graph tables and neighbour lists, everything else is global
     auto cta_local = [](int r) {
-        return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR;
+        return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR ||
+               r == RG_P || r == RG_PL || r == RG_SBASE || r == RG_IMGL;
     };
     size_t s_used = 0, g_used = 0;
     L.smem_mask = 0;
     for (int k = 0; k < RG_COUNT; ++k) {
-        const int r = prio[k];
+        const int r = cp.cluster > 1 ? prio_cl[k] : prio[k];
         const size_t a = align_up(sz[r], 16);
         if (s_used + a <= budget && (cp.cluster == 1 || cta_local(r))) {
             L.off[r] = (int64_t)s_used;
@@ -295,6 +307,11 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     if (cp.cluster > 1) {
         const int block = forced_block ? forced_block : 512;
         plan_layout(cp, B, block, max_dyn);
+        const uint32_t need = (1u << RG_SBASE) | (1u << RG_P) | (1u << RG_PL) | (1u << RG_IMGL);
+        if ((cp.lay.smem_mask & need) != need) cp.cluster = 1;   // too large: one CTA per pair
+    }
+    if (cp.cluster > 1) {
+        const int block = cp.block = forced_block ? forced_block : 512;
         int nclu = 0;
         cudaError_t e = kbest_cluster_occupancy(cp.W, label_instance(B), block,
                                                 (size_t)cp.lay.smem_bytes, cp.cluster, &nclu);

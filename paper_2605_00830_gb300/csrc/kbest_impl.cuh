@@ -121,7 +121,7 @@ template <typename Word>
 struct Regions {
     int32_t *hist, *alpha2, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
     int32_t *ped0, *ped1;
-    Word *a2t, *l2t, *img0, *img1, *P, *PL;
+    Word *a2t, *l2t, *img0, *img1, *P, *PL, *imgl;
     uint16_t *cslot;
     uint8_t *map0, *map1, *cj;
 };
@@ -282,7 +282,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const int K = p.kpp ? p.kpp[pair] : p.K;
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
     const int N2S = p.lay.n2s;
-    const int KM = p.lay.kmax;
+    const int KM = p.lay.kloc;   // node slots of the P / PL / sbase tables this CTA indexes
     const int64_t mrow = p.lay.mrow;
     const int stride = n2 + 1;   // successors of one node at most: n2 substitutions + deletion
     const MapT DEL = (MapT)~(MapT)0;
@@ -379,7 +379,21 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes its edges to v_0..v_{i-1}
         const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
         const int base = s_lo * stride;              // this warp's successor storage
-
+        // node tables the warp prepares and evaluates are indexed from cs0: 0 for a one-CTA
+        // team; for a cluster, the first node of this CTA (its P, PL and sbase are CTA-local
+        // and its nodes' Img rows are staged into shared memory)
+        int cs0 = 0, ioff = 0;
+        const Word *imgw = imgc;
+        if (CL) {
+            const int nwl = (int)blockDim.x >> 5;
+            const int r0 = (int)cluster_rank() * nwl;
+            cs0 = (r0 * L) / NW;
+            const int cs1 = ((r0 + nwl) * L) / NW;
+            for (int x = ltid; x < (cs1 - cs0) * W; x += LT) R.imgl[x] = imgc[(int64_t)cs0 * W + x];
+            __syncthreads();
+            imgw = R.imgl;
+            ioff = cs0;
+        }
         // ---- S1 + S2 per-node vectors, successor lists, S3 evaluation ----------------
         int kw = 0;          // successors of this warp so far
         int wmin = INT_MAX;
@@ -391,7 +405,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             if (act) {
                 // S2: P = images of the substituted g1 neighbours of v_i (their edge labels in
                 // bit-planes PL at the image positions); dcnt = deleted neighbours
-                Word *Ps = R.P + (int64_t)s * W;
+                Word *Ps = R.P + (int64_t)(s - cs0) * W;
                 const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
                 int dcnt = 0;
                 if (W == 1) {
@@ -412,12 +426,12 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     Ps[0] = pr;
 #pragma unroll
                     for (int b = 0; b < NPL; ++b)
-                        if (b < B) R.PL[(int64_t)b * KM + s] = plr[b];
+                        if (b < B) R.PL[(int64_t)b * KM + (s - cs0)] = plr[b];
                 } else {
 #pragma unroll
                     for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
                     for (int b = 0; b < B; ++b)
-                        for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + s) * W + w] = (Word)0;
+                        for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + (s - cs0)) * W + w] = (Word)0;
                     for (int t = 0; t < deg; ++t) {
                         const int e = R.nbr[n0 + t];
                         const MapT phi = ms[e & 0xffff];
@@ -426,11 +440,11 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         const Word pb = (Word)1 << ((int)phi % WB);
                         Ps[pw] |= pb;
                         for (int b = 0; b < B; ++b)
-                            if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + s) * W + pw] |= pb;
+                            if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + (s - cs0)) * W + pw] |= pb;
                     }
                 }
-                R.sbase[s] = pedc[s] + c.edel * dcnt;
-                const Word *im = imgc + (int64_t)s * W;
+                R.sbase[s - cs0] = pedc[s] + c.edel * dcnt;
+                const Word *im = imgw + (int64_t)(s - ioff) * W;
                 int used = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) used += popcw(im[w]);
@@ -447,7 +461,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // successor ids in enumeration order: for each node the free g2 vertices in
             // increasing order, then n2 for v_i -> eps (each lane walks its own node's bits)
             if (act) {
-                const Word *im = imgc + (int64_t)s * W;
+                const Word *im = imgw + (int64_t)(s - ioff) * W;
                 int idx = base + kw + excl;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -479,8 +493,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     if (j == n2) {
                         ped = pedc[sc] + delcost;
                     } else {
-                        const Word *im = imgc + (int64_t)sc * W;
-                        const Word *Ps = R.P + (int64_t)sc * W;
+                        const Word *im = imgw + (int64_t)(sc - ioff) * W;
+                        const Word *Ps = R.P + (int64_t)(sc - cs0) * W;
                         int x = 0, y = 0, z = 0;
 #pragma unroll
                         for (int w = 0; w < W; ++w) {
@@ -496,13 +510,13 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                             if (B > 0) {
                                 Word ld = (Word)0;
                                 for (int b = 0; b < B; ++b)
-                                    ld |= R.PL[((int64_t)b * KM + sc) * W + w] ^
+                                    ld |= R.PL[((int64_t)b * KM + (sc - cs0)) * W + w] ^
                                           R.l2t[(b * W + w) * N2S + j];
                                 z += popcw((Word)(aw & pw & ld));
                             }
                         }
                         const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
-                        ped = R.sbase[sc] + cv + c.eins * x + c.edel * y + c.esub * z;
+                        ped = R.sbase[sc - cs0] + cv + c.eins * x + c.edel * y + c.esub * z;
                     }
                     R.cand[idx] = ped;
                     wmin = ped < wmin ? ped : wmin;
@@ -802,6 +816,7 @@ __device__ __forceinline__ Regions<Word> make_regions(F base)
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
     R.map1 = base(RG_MAP1);
+    R.imgl = (Word *)base(RG_IMGL);
     return R;
 }
 
