@@ -160,10 +160,11 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsig
 // candidate with PED < T, and the first q with PED == T counted over the whole team.
 // keep_before / eq_before: kept / tied candidates of the warps before this one.
 template <typename Word>
-__device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, int n, int T,
-                                            int q, int keep_before, int eq_before)
+__device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, int n, int T,
+                                           int q, int keep_before, int eq_before)
 {
     const int lane = threadIdx.x & 31;
+    const int keep0 = keep_before;
     for (int kb = 0; kb < n; kb += 32) {
         const int k = kb + lane;
         const int v = k < n ? R.cand[base + k] : INT_MAX;
@@ -181,6 +182,7 @@ __device__ __forceinline__ void compact_kept(const Regions<Word> &R, int base, i
         keep_before += __popc(kbm);
         eq_before += __popc(eqb);
     }
+    return keep_before - keep0;
 }
 
 // Exact selection used when the kept set reaches past the histogram window: the K-th
@@ -660,27 +662,32 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
         if (tid == 0) nevals += total;
         if (thr < hwin - 1) {
-            // kept = every successor below the threshold bucket and the first q in it, placed
-            // in (PED, parent slot, j) order: position = #(smaller PED) + #(equal PED earlier)
+            // kept = every successor below the threshold bucket and the first q in it. Each
+            // warp compacts its kept successors in enumeration order, then places them at
+            // their rank in (PED, parent slot, j) order: position = #(smaller PED) +
+            // #(equal PED earlier); lane b holds the bucket-b counts of earlier warps.
             const int q = newL - __shfl_sync(0xffffffffu, bexcl, thr);
-            int run = mine;   // lane b: bucket-b successors before the current chunk
-            for (int kb = 0; kb < kw; kb += 32) {
-                const int k = kb + lane;
-                const int d = k < kw ? R.cand[base + k] - pmin : INT_MAX;
-                const bool elig = d <= thr;
-                const unsigned V = __ballot_sync(0xffffffffu, elig);
-                if (V == 0u) continue;
-                const int dd = elig ? d : 0;
+            const int eq_before = __shfl_sync(0xffffffffu, mine, thr);
+            const int lt_before = warp_sum(lane < thr ? mine : 0);
+            const int kbeg = lt_before + min(q, eq_before);
+            const int kcnt = compact_kept<Word>(R, base, kw, pmin + thr, q, kbeg, eq_before);
+            __syncwarp();
+            int run = lane < thr ? mine : min(q, eq_before);   // kept of bucket `lane` before
+            for (int xb = 0; xb < kcnt; xb += 32) {
+                const int x = kbeg + xb + lane;
+                const bool v = xb + lane < kcnt;
+                const int d = v ? R.kped[x] - pmin : 0;
+                const unsigned V = __ballot_sync(0xffffffffu, v);
                 unsigned bb[5];
 #pragma unroll
-                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (dd >> b) & 1);
-                const int rank = __shfl_sync(0xffffffffu, run, dd) +
-                                 __popc(same_value_lanes(V, bb, dd) & lanemask_lt());
-                const int pos = __shfl_sync(0xffffffffu, bexcl, dd) + rank;
-                if (elig && (dd < thr || rank < q)) {
-                    const int idx = base + k;
+                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1);
+                const int pos = __shfl_sync(0xffffffffu, bexcl, d) +
+                                __shfl_sync(0xffffffffu, run, d) +
+                                __popc(same_value_lanes(V, bb, d) & lanemask_lt());
+                if (v) {
+                    const int idx = R.klist[x];
                     R.sel[pos] = ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
-                    R.selped[pos] = dd + pmin;
+                    R.selped[pos] = d + pmin;
                 }
                 unsigned m = V;
 #pragma unroll
