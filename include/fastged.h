@@ -103,6 +103,12 @@ typedef struct {
     int32_t block_threads;   /* 0 = autotuned; else 128, 256 or 512 threads per team          */
     int32_t use_cuda_graph;  /* plans only: 1 = capture the run once and replay it as a CUDA  */
                              /* graph, 0 = launch directly (a NULL options pointer means 1)   */
+    int32_t autotune;        /* plans only: 1 = before the plan is built, time every size     */
+                             /* class that the tuning table does not know yet with each team  */
+                             /* shape (threads per CTA, or CTAs per cluster for large pairs)  */
+                             /* on a sample of its pairs, and record the fastest; 0 = use the */
+                             /* table's entries where present, built-in rules elsewhere       */
+    int32_t pad;
 } fastged_options;
 
 typedef struct fastged_handle fastged_handle;
@@ -247,6 +253,13 @@ void fastged_serve_stop(fastged_server *s);
 
 /* Stops the server if needed and releases it (unpolled results are discarded). */
 void fastged_serve_destroy(fastged_server *s);
+
+/* Tuning table of the process (size-class shape -> team shape). If the environment variable
+ * FASTGED_AUTOTUNE_FILE names a file, the table is read from it on first use and every new
+ * entry is appended to it. fastged_autotune_entries returns the number of entries;
+ * fastged_autotune_clear forgets them all (the file is left alone). */
+int fastged_autotune_entries(void);
+void fastged_autotune_clear(void);
 
 /* Integer-pipe throughput of the current device (no counterpart in the paper; it is the
  * measured peak the benchmark compares the successor evaluation against). Runs three

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -288,6 +289,95 @@ static size_t layout_total(const ClassPlan &cp, int B, int block)
     return (size_t)t.lay.smem_bytes;
 }
 
+// ------------------------------------------------------------------------------------
+// tuning table: size-class shape -> team shape (threads per CTA, CTAs per cluster)
+// ------------------------------------------------------------------------------------
+struct TuneChoice {
+    int block = 0;
+    int cluster = 1;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune;
+static bool g_tune_loaded = false;
+static TuneChoice g_tune_force;   // set only while the autotuner times a candidate
+static bool g_tune_forcing = false;
+
+static int pow2_ceil(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static std::string class_key(const ClassPlan &cp, int B, int npairs, int sm_count)
+{
+    char buf[128];
+    snprintf(buf, sizeof(buf), "w%d%s%s_b%d_k%d_n%d_%s", cp.W, cp.wide ? "x" : "",
+             cp.w32 ? "h" : "", label_instance(B), pow2_ceil(cp.kmax), pow2_ceil(cp.n2max),
+             npairs < sm_count ? "few" : "many");
+    return buf;
+}
+
+static void tune_load_locked()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("FASTGED_AUTOTUNE_FILE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int block = 0, cluster = 1;
+    while (fscanf(f, "%127s %d %d", key, &block, &cluster) == 3) {
+        TuneChoice c;
+        c.block = block;
+        c.cluster = cluster;
+        g_tune[key] = c;
+    }
+    fclose(f);
+}
+
+static bool tune_lookup(const std::string &key, TuneChoice *out)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    if (g_tune_forcing) {
+        *out = g_tune_force;
+        return true;
+    }
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+static void tune_store(const std::string &key, const TuneChoice &c, double ms)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    g_tune[key] = c;
+    const char *path = getenv("FASTGED_AUTOTUNE_FILE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %.4f\n", key.c_str(), c.block, c.cluster, ms);
+    fclose(f);
+}
+
+extern "C" int fastged_autotune_entries(void)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    return (int)g_tune.size();
+}
+
+extern "C" void fastged_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune.clear();
+    g_tune_loaded = true;
+}
+
 // Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
 // Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
 // CTAs per pair.
@@ -297,9 +387,13 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     const size_t per_sm = (size_t)h->smem_per_sm;
     const size_t max_dyn = (size_t)h->smem_optin - team_shared_static_bytes();
     const int npairs = (int)std::max<size_t>(cp.order.size(), 1);
+    TuneChoice tc;
+    const bool tuned = forced_block == 0 &&
+                       tune_lookup(class_key(cp, B, npairs, h->sm_count), &tc);
+    if (tuned) forced_block = tc.block;
     if (kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) && npairs < h->sm_count) {
         const char *env = getenv("FASTGED_CLUSTER");
-        int cl = env ? atoi(env) : 8;
+        int cl = env ? atoi(env) : (tuned ? tc.cluster : 8);
         if (cl == 1 || cl == 2 || cl == 4 || cl == 8 || cl == 16) {
             cp.cluster = cl;
         }
@@ -741,12 +835,107 @@ extern "C" int fastged_batch(fastged_handle *h, const fastged_pair_list *pairs, 
 // ------------------------------------------------------------------------------------
 // device-resident plans
 // ------------------------------------------------------------------------------------
+// Times every team shape of every size class the table does not know yet, on a sample of
+// that class's pairs (each shape run twice, the faster run counts), and records the best.
+static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
+                          const fastged_options &o)
+{
+    Batch probe;
+    int rc = flatten(h, pl, K, o, probe);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(FASTGED_ERR_CUDA, "event creation");
+    for (const ClassPlan &cp : probe.classes) {
+        const int npairs = (int)cp.order.size();
+        const std::string key = class_key(cp, probe.B, npairs, h->sm_count);
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            tune_load_locked();
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) continue;
+        }
+        std::vector<TuneChoice> cands;
+        if (kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) && npairs < h->sm_count) {
+            for (int cl : {1, 4, 8, 16}) {
+                TuneChoice c;
+                c.block = cl == 1 ? 256 : 512;
+                c.cluster = cl;
+                cands.push_back(c);
+            }
+        } else {
+            for (int bt : {128, 256, 512}) {
+                TuneChoice c;
+                c.block = bt;
+                cands.push_back(c);
+            }
+        }
+        // the class's pairs, strided down to a sample that still fills the GPU several times
+        const int cap = std::max(1, 8 * h->sm_count);
+        const int step = std::max(1, npairs / cap);
+        std::vector<int32_t> sub_pairs, sub_kpp;
+        for (int q = 0; q < npairs; q += step) {
+            const int pidx = cp.order[q];
+            sub_pairs.push_back(pl->pairs[2 * pidx]);
+            sub_pairs.push_back(pl->pairs[2 * pidx + 1]);
+            if (o.k_per_pair) sub_kpp.push_back(o.k_per_pair[pidx]);
+        }
+        fastged_pair_list sub = *pl;
+        sub.n_pairs = (int32_t)(sub_pairs.size() / 2);
+        sub.pairs = sub_pairs.data();
+        fastged_options so = o;
+        so.k_per_pair = o.k_per_pair ? sub_kpp.data() : nullptr;
+        so.form = FASTGED_FORM_BATCHED;
+        TuneChoice best;
+        double best_ms = 1e30;
+        for (const TuneChoice &c : cands) {
+            double ms_c = 1e30;
+            for (int rep = 0; rep < 2; ++rep) {
+                {
+                    std::lock_guard<std::mutex> g(g_tune_mu);
+                    g_tune_force = c;
+                    g_tune_forcing = true;
+                }
+                cudaEventRecord(e0, h->stream);
+                rc = batch_enqueue(h, &sub, K, so);
+                cudaEventRecord(e1, h->stream);
+                const cudaError_t se = cudaStreamSynchronize(h->stream);
+                {
+                    std::lock_guard<std::mutex> g(g_tune_mu);
+                    g_tune_forcing = false;
+                }
+                if (rc || se != cudaSuccess) break;   // a shape that cannot run is skipped
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_c = std::min(ms_c, (double)ms);
+            }
+            if (rc) {
+                rc = FASTGED_OK;
+                clear_error();
+                continue;
+            }
+            if (ms_c < best_ms) {
+                best_ms = ms_c;
+                best = c;
+            }
+        }
+        if (best_ms < 1e30) tune_store(key, best, best_ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return FASTGED_OK;
+}
+
 extern "C" int fastged_plan_create(fastged_handle *h, const fastged_pair_list *pairs,
                                    int32_t K, const fastged_options *opt, fastged_plan **out)
 {
     clear_error();
     if (!h || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
     const fastged_options o = opt ? *opt : default_options();
+    if (o.autotune && o.block_threads == 0) {
+        const int rc = autotune_batch(h, pairs, K, o);
+        if (rc) return rc;
+    }
     fastged_plan *p = new fastged_plan();
     p->h = h;
     int rc = flatten(h, pairs, K, o, p->b);

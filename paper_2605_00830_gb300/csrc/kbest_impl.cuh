@@ -461,25 +461,47 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int excl = incl - cnt;
             const int gtot = __shfl_sync(0xffffffffu, incl, 31);
             // successor ids in enumeration order: for each node the free g2 vertices in
-            // increasing order, then n2 for v_i -> eps (each lane walks its own node's bits)
-            if (act) {
-                const Word *im = imgw + (int64_t)(s - ioff) * W;
-                int idx = base + kw + excl;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    Word x = ~im[w];
-                    const int lim = n2 - w * WB;
-                    if (lim < WB) x &= lim > 0 ? (((Word)1 << lim) - (Word)1) : (Word)0;
+            // increasing order, then n2 for v_i -> eps. Single-word bitsets: each lane walks
+            // its own node's bits; wider ones: the warp sweeps each node's vertices 32 at a
+            // time and compacts the free ones with a ballot.
+            if (W == 1) {
+                if (act) {
+                    const Word *im = imgw + (int64_t)(s - ioff) * W;
+                    int idx = base + kw + excl;
+                    Word x = ~im[0];
+                    if (n2 < WB) x &= n2 > 0 ? (((Word)1 << n2) - (Word)1) : (Word)0;
                     while (x) {
                         const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
                         x &= x - (Word)1;
                         R.cslot[idx] = (uint16_t)s;
-                        cjv[idx] = (MapT)(w * WB + t);
+                        cjv[idx] = (MapT)t;
                         ++idx;
                     }
+                    R.cslot[idx] = (uint16_t)s;
+                    cjv[idx] = (MapT)n2;
                 }
-                R.cslot[idx] = (uint16_t)s;
-                cjv[idx] = (MapT)n2;
+            } else {
+                for (int t = 0; t < ng; ++t) {
+                    const int st_ = g0 + t;
+                    const Word *im = imgw + (int64_t)(st_ - ioff) * W;
+                    const int o0 = base + kw + __shfl_sync(0xffffffffu, excl, t);
+                    int pos = 0;
+                    for (int jb = 0; jb < n2; jb += 32) {
+                        const int j = jb + lane;
+                        const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
+                        const unsigned bal = __ballot_sync(0xffffffffu, fr);
+                        if (fr) {
+                            const int idx = o0 + pos + __popc(bal & lanemask_lt());
+                            R.cslot[idx] = (uint16_t)st_;
+                            cjv[idx] = (MapT)j;
+                        }
+                        pos += __popc(bal);
+                    }
+                    if (lane == 0) {
+                        R.cslot[o0 + pos] = (uint16_t)st_;
+                        cjv[o0 + pos] = (MapT)n2;
+                    }
+                }
             }
             __syncwarp();
             PHASE_MARK(5);

@@ -33,7 +33,8 @@ EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_
             "fastged_plan_read", "fastged_plan_info", "fastged_plan_kernel_ms",
             "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc",
             "fastged_serve_start", "fastged_serve_submit", "fastged_serve_poll",
-            "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy"]
+            "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy",
+            "fastged_autotune_entries", "fastged_autotune_clear"]
 
 
 class FastGEDError(RuntimeError):
@@ -60,7 +61,8 @@ class PairList(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("k_per_pair", ctypes.c_void_p), ("hist_window", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -108,7 +110,7 @@ class ServeStats(ctypes.Structure):
 _GRAPH_DTYPE = np.dtype({"names": ["n", "vlabel", "m", "edges", "elabel"],
                          "formats": ["<i4", "<u8", "<i4", "<u8", "<u8"],
                          "offsets": [0, 8, 16, 24, 32], "itemsize": 40})
-assert ctypes.sizeof(GraphC) == 40 and ctypes.sizeof(Options) == 32
+assert ctypes.sizeof(GraphC) == 40 and ctypes.sizeof(Options) == 40
 
 _LIB = None
 
@@ -155,9 +157,12 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_serve_stop.restype = None
     lib.fastged_serve_destroy.argtypes = [vp]
     lib.fastged_serve_destroy.restype = None
+    lib.fastged_autotune_entries.restype = ctypes.c_int
+    lib.fastged_autotune_clear.restype = None
     for name in EXPORTED:
         if name in ("fastged_destroy", "fastged_plan_destroy", "fastged_last_error",
-                    "fastged_version", "fastged_serve_stop", "fastged_serve_destroy"):
+                    "fastged_version", "fastged_serve_stop", "fastged_serve_destroy",
+                    "fastged_autotune_clear"):
             continue
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
@@ -229,12 +234,13 @@ def marshal(w) -> Marshalled:
 
 
 def make_options(form: int = FASTGED_FORM_BATCHED, variant: int = 0, k_per_pair=None,
-                 hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1):
+                 hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1,
+                 autotune: int = 0):
     kpp = None
     if k_per_pair is not None:
         kpp = np.ascontiguousarray(np.asarray(k_per_pair, dtype=np.int32))
     o = Options(form, variant, kpp.ctypes.data if kpp is not None else None, hist_window,
-                block_threads, use_cuda_graph)
+                block_threads, use_cuda_graph, autotune, 0)
     o._keep = kpp
     return o
 

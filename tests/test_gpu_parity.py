@@ -256,3 +256,28 @@ def test_cluster_teams_match_oracle(cl, monkeypatch):
     w2 = W.config4(2, seed=44, n_range=(255, 300))
     w2.K = 300
     assert_parity(w2, gpu_run(w2, variant=1), variant=1)
+
+
+def test_autotuned_plans_match_and_fill_the_table(tmp_path, monkeypatch):
+    """The autotuner times each size class's team shapes and records the fastest; the plan
+    built from the tuned table gives the same results, and the table file is written."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("FASTGED_AUTOTUNE_FILE", str(path))
+    F.load().fastged_autotune_clear()
+    w = W.concat([W.config2(500), W.config4(2, seed=45, n_range=(300, 400))], "mix")
+    w.K = 64
+    ref = gpu_run(w, K=64)
+    mm = F.marshal(w)
+    with F.FastGED(w.cost) as g:
+        plan = F.fastged_plan_create(g.h, mm, 64, F.make_options(autotune=1))
+        F.fastged_plan_run(plan)
+        c, m, n = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+                   np.zeros(mm.n_pairs, np.int64))
+        F.fastged_plan_read(plan, c, m, n)
+        F.fastged_plan_destroy(plan)
+    for x, y in zip((c, m, n), ref):
+        assert np.array_equal(x, y)
+    assert F.load().fastged_autotune_entries() >= 2
+    lines = path.read_text().strip().splitlines()
+    assert len(lines) >= 2 and all(len(l.split()) == 4 for l in lines)
+    F.load().fastged_autotune_clear()
