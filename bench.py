@@ -83,6 +83,18 @@ def workload(rank: int, n_pairs: int):
     return getattr(W, fn)(n_pairs or full, seed=seed)
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def config_dict(w, extra=None):
     d = {"workload": WORKLOADS[_ARGS.workload][3],
          "name": w.name, "n_pairs": w.n_pairs, "K": w.K, "cost": list(w.cost),
@@ -286,11 +298,8 @@ def ours(args):
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     clk = clocks.stop()
-    tot_ms = float(sum(step_ms))
+    tot_ms = max_over_ranks(float(sum(step_ms)))
     if ws > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
         torch.distributed.barrier()
     F.fastged_plan_read(plan, c_out, m_out, n_out)
     info = F.fastged_plan_info(plan)
