@@ -239,8 +239,9 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_P] = kl * W * wb;
     sz[RG_PL] = (size_t)B * kl * W * wb;
     sz[RG_IMGL] = cp.cluster > 1 ? kl * W * wb : 0;
-    sz[RG_CSLOT] = ncand * 2;
-    sz[RG_CJ] = ncand * msz;
+    // single-word classes pack the successor ids into the PED entries
+    sz[RG_CSLOT] = W == 1 ? 0 : ncand * 2;
+    sz[RG_CJ] = W == 1 ? 0 : ncand * msz;
     sz[RG_CAND] = ncand * 4;
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
@@ -532,9 +533,15 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": costs can overflow int32");
         b.map_off[p] = mtot;
         mtot += g1.n;
-        const int W = words_class(g2.n);
+        int W = words_class(g2.n);
+        // the single-word kernels pack (PED, parent slot, j) into 32 bits: a pair goes there
+        // only if every PED stays below 2^16 and its beam has at most 512 nodes
+        const long long ped_bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
+                                    (long long)g1.m * std::max(c.e_sub, c.e_del) +
+                                    (long long)g2.m * c.e_ins;
+        if (W == 1 && !packable(ped_bound, kp)) W = 2;
         const bool wide = g2.n >= 255;
-        const bool w32 = g2.n <= 32;
+        const bool w32 = W == 1 && g2.n <= 32;
         const int key = w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0);
         if (cls_of[key] < 0) {
             cls_of[key] = (int)b.classes.size();
@@ -646,8 +653,8 @@ static unsigned long long *g_phase_dev = nullptr;
 extern "C" int fastged_debug_phase_cycles(unsigned long long *out, int reset)
 {
     if (!g_phase_dev) return -3;
-    if (cudaMemcpy(out, g_phase_dev, 64, cudaMemcpyDeviceToHost) != cudaSuccess) return -3;
-    if (reset) cudaMemset(g_phase_dev, 0, 64);
+    if (cudaMemcpy(out, g_phase_dev, 128, cudaMemcpyDeviceToHost) != cudaSuccess) return -3;
+    if (reset) cudaMemset(g_phase_dev, 0, 128);
     return 0;
 }
 #endif
@@ -686,7 +693,7 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     p.gscratch = wk + b.woff_scratch + cp.scratch_off;
     p.lay = cp.lay;
 #ifdef FASTGED_PHASE_TIMERS
-    if (!g_phase_dev && cudaMalloc(&g_phase_dev, 64) == cudaSuccess) cudaMemset(g_phase_dev, 0, 64);
+    if (!g_phase_dev && cudaMalloc(&g_phase_dev, 128) == cudaSuccess) cudaMemset(g_phase_dev, 0, 128);
     p.phase_cycles = g_phase_dev;
 #endif
     return p;
@@ -870,8 +877,9 @@ static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_
                 cands.push_back(c);
             }
         }
-        // the class's pairs, strided down to a sample that still fills the GPU several times
-        const int cap = std::max(1, 8 * h->sm_count);
+        // the class's pairs, strided down to a sample that fills every candidate's teams
+        // several times over (a sample near one wave of teams is decided by its tail)
+        const int cap = std::max(1, 32 * h->sm_count);
         const int step = std::max(1, npairs / cap);
         std::vector<int32_t> sub_pairs, sub_kpp;
         for (int q = 0; q < npairs; q += step) {

@@ -70,6 +70,9 @@ int set_error(int code, const char *msg);
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);
+// The single-word kernels store a successor as PED << 16 | parent slot << 7 | j: a pair may
+// use them only if no PED reaches 2^16 and its beam holds at most 512 nodes.
+inline bool packable(long long ped_bound, long long k) { return ped_bound < 65536 && k <= 512; }
 void clear_error();
 int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const fastged_options &opt, Batch &b);

@@ -156,41 +156,62 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsig
     return m;
 }
 
+// PED stored in a successor entry: the entry itself, or for packed entries
+// (PED << 16 | parent slot << 7 | j) its upper half.
+template <bool PK>
+__device__ __forceinline__ int cand_ped(int32_t e)
+{
+    return PK ? (int)((uint32_t)e >> 16) : e;
+}
+
 // Stable compaction of the kept successors of this warp, in enumeration order: every
 // candidate with PED < T, and the first q with PED == T counted over the whole team.
 // keep_before / eq_before: kept / tied candidates of the warps before this one.
-template <typename Word>
+template <typename Word, bool PK>
 __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, int n, int T,
                                            int q, int keep_before, int eq_before)
 {
     const int lane = threadIdx.x & 31;
     const int keep0 = keep_before;
-    for (int kb = 0; kb < n; kb += 32) {
-        const int k = kb + lane;
-        const int v = k < n ? R.cand[base + k] : INT_MAX;
-        if (__ballot_sync(0xffffffffu, v <= T) == 0u) continue;
-        const bool is_eq = (v == T);
-        const unsigned eqb = __ballot_sync(0xffffffffu, is_eq);
-        const int eq_rank = eq_before + __popc(eqb & lanemask_lt());
-        const bool keep = (v < T) || (is_eq && eq_rank < q);
-        const unsigned kbm = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int pos = keep_before + __popc(kbm & lanemask_lt());
-            R.klist[pos] = base + k;
-            R.kped[pos] = v;
+    const int32_t *cand = R.cand + base;
+    // four chunks of 32 per step: their loads and threshold ballots are independent, so only
+    // chunks holding a kept candidate pay for the ordered part
+    for (int kb = 0; kb < n; kb += 128) {
+        int v[4];
+        unsigned le[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = kb + 32 * u + lane;
+            v[u] = k < n ? cand_ped<PK>(cand[k]) : INT_MAX;
         }
-        keep_before += __popc(kbm);
-        eq_before += __popc(eqb);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(0xffffffffu, v[u] <= T);
+        if ((le[0] | le[1] | le[2] | le[3]) == 0u) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (le[u] == 0u) continue;
+            const bool is_eq = (v[u] == T);
+            const unsigned eqb = __ballot_sync(0xffffffffu, is_eq);
+            const int eq_rank = eq_before + __popc(eqb & lanemask_lt());
+            const bool keep = (v[u] < T) || (is_eq && eq_rank < q);
+            const unsigned kbm = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = keep_before + __popc(kbm & lanemask_lt());
+                R.klist[pos] = base + kb + 32 * u + lane;
+                R.kped[pos] = v[u];
+            }
+            keep_before += __popc(kbm);
+            eq_before += __popc(eqb);
+        }
     }
     return keep_before - keep0;
 }
 
 // Exact selection used when the kept set reaches past the histogram window: the K-th
 // smallest PED is found by bisection over team-wide counts, the kept candidates are
-// compacted stably, and ranked by (PED, enumeration order).
-template <typename MapT, typename Word, bool CL, typename TS>
+// compacted stably, and ranked by (PED, enumeration order); sel receives successor indices.
+template <typename MapT, typename Word, bool CL, bool PK, typename TS>
 __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
-                                          const uint16_t *cslot, const uint8_t *cj_b,
                                           int32_t *sel, int32_t *selped, TS &S, int L,
                                           int stride, int newL, int lo)
 {
@@ -205,7 +226,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     R.kped = kped;
 
     int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, cand[base + k]);
+    for (int k = lane; k < n; k += 32) mx = max(mx, cand_ped<PK>(cand[base + k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -218,7 +239,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (cand[base + k] <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (cand_ped<PK>(cand[base + k]) <= mid);
         cnt = warp_sum(cnt);
         tm.sync();
         if (tid == 0) S.cnt = 0;
@@ -230,7 +251,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     const int thr = lo;
     int nlt = 0, neq = 0;
     for (int k = lane; k < n; k += 32) {
-        const int v = cand[base + k];
+        const int v = cand_ped<PK>(cand[base + k]);
         nlt += (v < thr);
         neq += (v == thr);
     }
@@ -247,10 +268,9 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
         eq_before += S.weq[w];
     }
     keep_before += min(q, eq_before);
-    compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before);
+    compact_kept<Word, PK>(R, base, n, thr, q, keep_before, eq_before);
     tm.sync();
     // rank by (PED, enumeration order); klist is in enumeration order
-    const MapT *cj = (const MapT *)cj_b;
     for (int a = tid; a < newL; a += T) {
         const int pa = kped[a];
         int rank = 0;
@@ -258,8 +278,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
             const int pb = kped[b];
             rank += (pb < pa) || (pb == pa && b < a);
         }
-        const int c = klist[a];
-        sel[rank] = ((int)cslot[c] << kSelShift) | (int)cj[c];
+        sel[rank] = klist[a];   // successor index; the caller turns it into (slot, j)
         selped[rank] = pa;
     }
 }
@@ -292,12 +311,17 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const int hwin = p.hwin;     // buckets 0..hwin-2 hold one PED each, hwin-1 the rest
     const bool fold_ie = (c.eins == c.edel);
     MapT *cjv = (MapT *)R.cj;
+    // single-word classes pack every successor into one 32-bit entry of R.cand:
+    // PED << 16 | parent slot << 7 | j (the host routes a pair here only when its PEDs stay
+    // below 2^16 and K <= 512); the other classes keep PEDs in R.cand and ids in cslot / cj
+    constexpr bool PK = (W == 1) && !CL;
+    uint32_t *ck = (uint32_t *)R.cand;
     // lane-constant masks: lane b answers for histogram bucket b
     unsigned lanebit[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) lanebit[k] = ((lane >> k) & 1) ? 0xffffffffu : 0u;
 #ifdef FASTGED_PHASE_TIMERS
-    long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long ph[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     long long ph_last = clock64();
 #endif
 
@@ -415,15 +439,24 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     Word pr = (Word)0, plr[NPL];
 #pragma unroll
                     for (int b = 0; b < NPL; ++b) plr[b] = (Word)0;
-                    for (int t = 0; t < deg; ++t) {
-                        const int e = R.nbr[n0 + t];
-                        const MapT phi = ms[e & 0xffff];
-                        if (phi == DEL) { ++dcnt; continue; }
-                        const Word pb = (Word)1 << ((int)phi % WB);
-                        pr |= pb;
+                    // four neighbours per step: list and map loads first, then the bits
+                    for (int t0 = 0; t0 < deg; t0 += 4) {
+                        int e[4];
+                        MapT phi[4];
 #pragma unroll
-                        for (int b = 0; b < NPL; ++b)
-                            if (b < B && ((e >> (16 + b)) & 1)) plr[b] |= pb;
+                        for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr[n0 + t0 + u] : -1;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) phi[u] = e[u] >= 0 ? ms[e[u] & 0xffff] : DEL;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const bool sub = phi[u] != DEL;
+                            dcnt += (e[u] >= 0 && !sub) ? 1 : 0;
+                            const Word pb = sub ? (Word)1 << ((int)phi[u] % WB) : (Word)0;
+                            pr |= pb;
+#pragma unroll
+                            for (int b = 0; b < NPL; ++b)
+                                if (b < B && ((e[u] >> (16 + b)) & 1)) plr[b] |= pb;
+                        }
                     }
                     Ps[0] = pr;
 #pragma unroll
@@ -464,7 +497,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // increasing order, then n2 for v_i -> eps. Single-word bitsets: each lane walks
             // its own node's bits; wider ones: the warp sweeps each node's vertices 32 at a
             // time and compacts the free ones with a ballot.
-            if (W == 1) {
+            if (PK) {
                 if (act) {
                     const Word *im = imgw + (int64_t)(s - ioff) * W;
                     int idx = base + kw + excl;
@@ -473,12 +506,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     while (x) {
                         const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
                         x &= x - (Word)1;
-                        R.cslot[idx] = (uint16_t)s;
-                        cjv[idx] = (MapT)t;
-                        ++idx;
+                        ck[idx++] = ((uint32_t)s << 7) | (uint32_t)t;
                     }
-                    R.cslot[idx] = (uint16_t)s;
-                    cjv[idx] = (MapT)n2;
+                    ck[idx] = ((uint32_t)s << 7) | (uint32_t)n2;
                 }
             } else {
                 for (int t = 0; t < ng; ++t) {
@@ -506,44 +536,65 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             __syncwarp();
             PHASE_MARK(5);
 
-            // S3: 32 successors at a time, in enumeration order
-            for (int kb = 0; kb < gtot; kb += 32) {
-                const int k = kb + lane;
-                if (k < gtot) {
-                    const int idx = base + kw + k;
-                    const int sc = R.cslot[idx];
-                    const int j = (int)cjv[idx];
-                    int ped;
-                    if (j == n2) {
-                        ped = pedc[sc] + delcost;
-                    } else {
-                        const Word *im = imgw + (int64_t)(sc - ioff) * W;
-                        const Word *Ps = R.P + (int64_t)(sc - cs0) * W;
-                        int x = 0, y = 0, z = 0;
+            // S3: PED of successor (node sc, column j); j == n2 is the deletion v_i -> eps.
+            // Branch-free: the substitution formula is also evaluated for the deletion (its
+            // table reads stay inside the staged rows) and discarded.
+            auto succ_ped = [&](int sc, int j) -> int {
+                const Word *im = imgw + (int64_t)(sc - ioff) * W;
+                const Word *Ps = R.P + (int64_t)(sc - cs0) * W;
+                int x = 0, y = 0, z = 0;
 #pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const Word aw = R.a2t[w * N2S + j];
-                            const Word ai = aw & im[w];
-                            const Word pw = Ps[w];
-                            if (fold_ie) {
-                                x += popcw((Word)(ai ^ pw));
-                            } else {
-                                x += popcw((Word)(ai & ~pw));
-                                y += popcw((Word)(pw & ~aw));
-                            }
-                            if (B > 0) {
-                                Word ld = (Word)0;
-                                for (int b = 0; b < B; ++b)
-                                    ld |= R.PL[((int64_t)b * KM + (sc - cs0)) * W + w] ^
-                                          R.l2t[(b * W + w) * N2S + j];
-                                z += popcw((Word)(aw & pw & ld));
-                            }
-                        }
-                        const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
-                        ped = R.sbase[sc - cs0] + cv + c.eins * x + c.edel * y + c.esub * z;
+                for (int w = 0; w < W; ++w) {
+                    const Word aw = R.a2t[w * N2S + j];
+                    const Word ai = aw & im[w];
+                    const Word pw = Ps[w];
+                    if (fold_ie) {
+                        x += popcw((Word)(ai ^ pw));
+                    } else {
+                        x += popcw((Word)(ai & ~pw));
+                        y += popcw((Word)(pw & ~aw));
                     }
-                    R.cand[idx] = ped;
-                    wmin = ped < wmin ? ped : wmin;
+                    if (B > 0) {
+                        Word ld = (Word)0;
+                        for (int b = 0; b < B; ++b)
+                            ld |= R.PL[((int64_t)b * KM + (sc - cs0)) * W + w] ^
+                                  R.l2t[(b * W + w) * N2S + j];
+                        z += popcw((Word)(aw & pw & ld));
+                    }
+                }
+                const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
+                const int sub = R.sbase[sc - cs0] + cv + c.eins * x + c.edel * y + c.esub * z;
+                return j == n2 ? pedc[sc] + delcost : sub;
+            };
+            // U chunks of 32 successors per step, their id loads and PEDs independent
+            constexpr int U = W <= 2 ? 2 : 1;
+            for (int kb = 0; kb < gtot; kb += 32 * U) {
+                int scu[U], ju[U];
+                uint32_t idu[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + 32 * u + lane;
+                    const int idx = base + kw + k;
+                    if constexpr (PK) {
+                        idu[u] = k < gtot ? ck[idx] : (((uint32_t)g0 << 7) | (uint32_t)n2);
+                        scu[u] = (int)(idu[u] >> 7);
+                        ju[u] = (int)(idu[u] & 127u);
+                    } else {
+                        scu[u] = k < gtot ? (int)R.cslot[idx] : g0;
+                        ju[u] = k < gtot ? (int)cjv[idx] : n2;
+                    }
+                }
+                int pu[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) pu[u] = succ_ped(scu[u], ju[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + 32 * u + lane;
+                    if (k < gtot) {
+                        if constexpr (PK) ck[base + kw + k] = ((uint32_t)pu[u] << 16) | idu[u];
+                        else R.cand[base + kw + k] = pu[u];
+                        wmin = pu[u] < wmin ? pu[u] : wmin;
+                    }
                 }
             }
             kw += gtot;
@@ -557,6 +608,16 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
         tm.sync();
         PHASE_MARK(1);
+        // PED of successor idx, and its (parent slot << kSelShift) | j
+        auto ped_at = [&](int idx) -> int { return cand_ped<PK>(R.cand[idx]); };
+        auto decode = [&](int idx) -> int {
+            if constexpr (PK) {
+                const uint32_t id = ck[idx];
+                return (int)(((id >> 7) & 511u) << kSelShift) | (int)(id & 127u);
+            } else {
+                return ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
+            }
+        };
 
         if (p.variant == 1 && i == n1 - 1) {
             // variant B: every successor of the last level is completed (insertions of the
@@ -585,8 +646,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             __syncwarp();
             auto leaf_total = [&](int k) -> long long {
                 const int idx = base + k;
-                const int sc = R.cslot[idx];
-                const int j = (int)cjv[idx];
+                const int v = decode(idx);
+                const int sc = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
                 const Word *im = imgc + (int64_t)sc * W;
                 int nimg = R.kped[sc], e2 = R.klist[sc];
                 if (j < n2) {
@@ -594,7 +655,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #pragma unroll
                     for (int w = 0; w < W; ++w) e2 += popcw((Word)(R.a2t[w * N2S + j] & im[w]));
                 }
-                return (long long)R.cand[idx] + (long long)c.vins * (n2 - nimg) +
+                return (long long)ped_at(idx) + (long long)c.vins * (n2 - nimg) +
                        (long long)c.eins * (m2.m - e2);
             };
             long long tmin = LLONG_MAX;
@@ -610,7 +671,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             for (int k = lane; k < kw; k += 32)
                 if (leaf_total(k) == best_total) {
                     const unsigned long long kk =
-                        ((unsigned long long)R.cand[base + k] << 32) | (unsigned)(base + k);
+                        ((unsigned long long)ped_at(base + k) << 32) | (unsigned)(base + k);
                     key = kk < key ? kk : key;
                 }
 #pragma unroll
@@ -623,7 +684,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             unsigned long long bk = S.wbest[0];
             for (int w = 1; w < NW; ++w) bk = S.wbest[w] < bk ? S.wbest[w] : bk;
             const int widx = (int)(bk & 0xffffffffull);
-            const int ws = R.cslot[widx], wj = (int)cjv[widx];
+            const int wv = decode(widx);
+            const int ws = wv >> kSelShift, wj = wv & ((1 << kSelShift) - 1);
             int all = 0;
             for (int w = 0; w < NW; ++w) all += S.wn[w];
             if (tid == 0) {
@@ -650,7 +712,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             for (int kb = 0; kb < kw; kb += 32) {
                 const int k = kb + lane;
                 const bool valid = k < kw;
-                const int d = valid ? min(R.cand[base + k] - pmin, hwin - 1) : 0;
+                const int d = valid ? min(ped_at(base + k) - pmin, hwin - 1) : 0;
                 const unsigned V = __ballot_sync(0xffffffffu, valid);
                 unsigned bb[5];
 #pragma unroll
@@ -662,7 +724,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             }
             R.hist[lane * NW + warp] = hreg;
         }
+        PHASE_MARK(10);
         tm.sync();
+        PHASE_MARK(11);
         // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
         // and the bucket-b successors of the warps before this one
         int tot = 0, mine = 0;
@@ -683,6 +747,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         // the bucket where the cumulative count reaches newL
         const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
         if (tid == 0) nevals += total;
+        PHASE_MARK(2);
         if (thr < hwin - 1) {
             // kept = every successor below the threshold bucket and the first q in it. Each
             // warp compacts its kept successors in enumeration order, then places them at
@@ -692,8 +757,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int eq_before = __shfl_sync(0xffffffffu, mine, thr);
             const int lt_before = warp_sum(lane < thr ? mine : 0);
             const int kbeg = lt_before + min(q, eq_before);
-            const int kcnt = compact_kept<Word>(R, base, kw, pmin + thr, q, kbeg, eq_before);
+            const int kcnt = compact_kept<Word, PK>(R, base, kw, pmin + thr, q, kbeg, eq_before);
             __syncwarp();
+            PHASE_MARK(8);
             int run = lane < thr ? mine : min(q, eq_before);   // kept of bucket `lane` before
             for (int xb = 0; xb < kcnt; xb += 32) {
                 const int x = kbeg + xb + lane;
@@ -707,8 +773,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                                 __shfl_sync(0xffffffffu, run, d) +
                                 __popc(same_value_lanes(V, bb, d) & lanemask_lt());
                 if (v) {
-                    const int idx = R.klist[x];
-                    R.sel[pos] = ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
+                    R.sel[pos] = decode(R.klist[x]);
                     R.selped[pos] = d + pmin;
                 }
                 unsigned m = V;
@@ -716,12 +781,18 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
                 run += __popc(m);
             }
+            PHASE_MARK(9);
         } else {
-            select_exact<MapT, Word, CL, TS>(R.cand, R.klist, R.kped, R.cslot, R.cj, R.sel,
-                                             R.selped, S, L, stride, newL, pmin + hwin - 1);
+#ifdef FASTGED_PHASE_TIMERS
+            if (threadIdx.x == 0) ph[7] += 1;   // levels that took the exact selection
+#endif
+            select_exact<MapT, Word, CL, PK, TS>(R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
+                                                 stride, newL, pmin + hwin - 1);
+            tm.sync();
+            for (int r = tid; r < newL; r += T) R.sel[r] = decode(R.sel[r]);
         }
         tm.sync();
-        PHASE_MARK(2);
+        PHASE_MARK(6);
 
         // ---- kept children, in key order (slot = rank) -----------------------------
         {
@@ -814,7 +885,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     }
 #ifdef FASTGED_PHASE_TIMERS
     if (tid == 0 && p.phase_cycles)
-        for (int k = 0; k < 6; ++k) atomicAdd(&p.phase_cycles[k], (unsigned long long)ph[k]);
+        for (int k = 0; k < 16; ++k) atomicAdd(&p.phase_cycles[k], (unsigned long long)ph[k]);
 #endif
 }
 

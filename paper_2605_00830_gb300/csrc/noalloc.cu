@@ -139,7 +139,11 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     const int Wg = (b->max_n + 63) / 64;
     ClassPlan cp;
     cp.W = Wg <= 1 ? 1 : Wg <= 2 ? 2 : Wg <= 4 ? 4 : Wg <= 8 ? 8 : 16;
-    cp.w32 = b->max_n <= 32;
+    const long long ped_bound =
+        (long long)b->max_n * std::max(cost->v_sub, cost->v_del) +
+        (long long)b->max_m * (std::max(cost->e_sub, cost->e_del) + cost->e_ins);
+    if (cp.W == 1 && !packable(ped_bound, K)) cp.W = 2;
+    cp.w32 = cp.W == 1 && b->max_n <= 32;
     cp.wide = b->max_n >= 255 || cp.W >= 8;
     cp.n1max = b->max_n;
     cp.n2max = b->max_n;

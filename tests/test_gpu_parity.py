@@ -59,6 +59,27 @@ def test_large_costs():
     assert_parity(w, gpu_run(w))
 
 
+def test_packed_single_word_entries_at_their_limits():
+    """Single-word pairs store each successor as PED << 16 | parent slot << 7 | j when no
+    PED can reach 2^16 and K <= 512; other pairs take the two-word kernels. PEDs above 2^15
+    set the top bit of the packed entry; K = 512 packs and K = 513 does not."""
+    cost = (1000, 1200, 0, 250, 300, 0)   # no insertion costs: a result is a leaf's PED
+    pairs = []
+    for k in range(12):
+        st = W.Stream(31, k)
+        big, small = W.molecule_like(st, 39), W.molecule_like(st, 5 + k % 4)
+        pairs += [(big, small), (small, big)]
+    for a, b in pairs:
+        assert a.n * 1200 + a.m * 300 < 65536
+    w = single(pairs, cost, 100)
+    gpu = gpu_run(w)
+    assert_parity(w, gpu)
+    assert int(gpu[0].max()) > 32768
+    w1 = W.config1(16)
+    for K in (512, 513):
+        assert_parity(w1, gpu_run(w1, K=K), K=K)
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_block_sizes(bt):
     w = W.config2(150)
