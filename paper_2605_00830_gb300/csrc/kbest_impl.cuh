@@ -422,7 +422,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
         // ---- S1 + S2 per-node vectors, successor lists, S3 evaluation ----------------
         int kw = 0;          // successors of this warp so far
-        int wmin = INT_MAX;
+        int wmin = INT_MAX;  // least PED this warp scored
+        // PED of successor idx
+        auto ped_at = [&](int idx) -> int { return cand_ped<PK>(R.cand[idx]); };
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
@@ -607,9 +609,36 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             S.wn[warp] = kw;
         }
         tm.sync();
+        // S4 histogram of PED - pa over this warp's successors, pa = least PED of the level
+        // (the last bucket collects every PED past the window). Ballot counting: lane b keeps
+        // the count of bucket b; lanes past the end count in the last bucket, which only
+        // bounds the threshold search from above (the level total comes from the counts kw).
+        int pa = INT_MAX;
+        for (int w = 0; w < NW; ++w) pa = min(pa, S.wmin[w]);
+        {
+            int hreg = 0;
+            for (int kb = 0; kb < kw; kb += 128) {
+                int d4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + 32 * u + lane;
+                    d4[u] = k < kw ? min(ped_at(base + k) - pa, hwin - 1) : hwin - 1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (kb + 32 * u >= kw) break;
+                    unsigned m = 0xffffffffu;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b)
+                        m &= ~(__ballot_sync(0xffffffffu, (d4[u] >> b) & 1) ^ lanebit[b]);
+                    hreg += __popc(m);
+                }
+            }
+            R.hist[lane * NW + warp] = hreg;
+        }
+        tm.sync();
         PHASE_MARK(1);
-        // PED of successor idx, and its (parent slot << kSelShift) | j
-        auto ped_at = [&](int idx) -> int { return cand_ped<PK>(R.cand[idx]); };
+        // (parent slot << kSelShift) | j of successor idx
         auto decode = [&](int idx) -> int {
             if constexpr (PK) {
                 const uint32_t id = ck[idx];
@@ -703,30 +732,6 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
 
         // ---- S4 selection ---------------------------------------------------------
-        // histogram of PED - pmin over this warp's successors (ballot counting: lane b
-        // keeps the count of bucket b; the last bucket collects every PED past the window)
-        int pmin = INT_MAX;
-        for (int w = 0; w < NW; ++w) pmin = min(pmin, S.wmin[w]);
-        {
-            int hreg = 0;
-            for (int kb = 0; kb < kw; kb += 32) {
-                const int k = kb + lane;
-                const bool valid = k < kw;
-                const int d = valid ? min(ped_at(base + k) - pmin, hwin - 1) : 0;
-                const unsigned V = __ballot_sync(0xffffffffu, valid);
-                unsigned bb[5];
-#pragma unroll
-                for (int b = 0; b < 5; ++b) bb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1);
-                unsigned m = V;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) m &= ~(bb[b] ^ lanebit[b]);
-                hreg += __popc(m);
-            }
-            R.hist[lane * NW + warp] = hreg;
-        }
-        PHASE_MARK(10);
-        tm.sync();
-        PHASE_MARK(11);
         // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
         // and the bucket-b successors of the warps before this one
         int tot = 0, mine = 0;
@@ -742,7 +747,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             if (lane >= o) incl += v;
         }
         const int bexcl = incl - tot;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int total = 0;   // successors of the level (the last bucket may hold padding)
+        for (int w = 0; w < NW; ++w) total += S.wn[w];
         const int newL = min(K, total);
         // the bucket where the cumulative count reaches newL
         const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
@@ -757,14 +763,14 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int eq_before = __shfl_sync(0xffffffffu, mine, thr);
             const int lt_before = warp_sum(lane < thr ? mine : 0);
             const int kbeg = lt_before + min(q, eq_before);
-            const int kcnt = compact_kept<Word, PK>(R, base, kw, pmin + thr, q, kbeg, eq_before);
+            const int kcnt = compact_kept<Word, PK>(R, base, kw, pa + thr, q, kbeg, eq_before);
             __syncwarp();
             PHASE_MARK(8);
             int run = lane < thr ? mine : min(q, eq_before);   // kept of bucket `lane` before
             for (int xb = 0; xb < kcnt; xb += 32) {
                 const int x = kbeg + xb + lane;
                 const bool v = xb + lane < kcnt;
-                const int d = v ? R.kped[x] - pmin : 0;
+                const int d = v ? R.kped[x] - pa : 0;
                 const unsigned V = __ballot_sync(0xffffffffu, v);
                 unsigned bb[5];
 #pragma unroll
@@ -774,7 +780,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                                 __popc(same_value_lanes(V, bb, d) & lanemask_lt());
                 if (v) {
                     R.sel[pos] = decode(R.klist[x]);
-                    R.selped[pos] = d + pmin;
+                    R.selped[pos] = d + pa;
                 }
                 unsigned m = V;
 #pragma unroll
@@ -787,7 +793,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             if (threadIdx.x == 0) ph[7] += 1;   // levels that took the exact selection
 #endif
             select_exact<MapT, Word, CL, PK, TS>(R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
-                                                 stride, newL, pmin + hwin - 1);
+                                                 stride, newL, pa + hwin - 1);
             tm.sync();
             for (int r = tid; r < newL; r += T) R.sel[r] = decode(R.sel[r]);
         }

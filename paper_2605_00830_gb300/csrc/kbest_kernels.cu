@@ -58,12 +58,20 @@ __global__ void pack_kernel(const PackParams pp)
 
 bool kbest_has_smem_variant(int W, bool wide, bool w32) { return w32 || (W <= 4 && !wide); }
 
-template <int BK>
-cudaError_t launch_kbest_bk(int W, bool wide_map, bool w32, bool sm, const KParams &p, int grid,
-                            int block, size_t smem, cudaStream_t st);
-template <int BK>
-cudaError_t kbest_occupancy_bk(int W, bool wide_map, bool w32, bool sm, int block, size_t smem,
-                               int *out);
+// the K-Best instances are compiled in kbest_b0.cu, kbest_b2.cu and kbest_b8.cu (one
+// translation unit per label-plane count, built in parallel); none are instantiated here
+#define FASTGED_EXTERN_BK(BK)                                                                  \
+    extern template cudaError_t launch_kbest_bk<BK>(int, bool, bool, bool, const KParams &, int, \
+                                                    int, size_t, cudaStream_t);                \
+    extern template cudaError_t kbest_occupancy_bk<BK>(int, bool, bool, bool, int, size_t,      \
+                                                       int *);                                 \
+    extern template cudaError_t launch_kbest_cluster_bk<BK>(int, const KParams &, int, int,     \
+                                                            size_t, int, cudaStream_t);        \
+    extern template cudaError_t kbest_cluster_occupancy_bk<BK>(int, int, size_t, int, int *);
+FASTGED_EXTERN_BK(0)
+FASTGED_EXTERN_BK(2)
+FASTGED_EXTERN_BK(8)
+#undef FASTGED_EXTERN_BK
 
 // bk: edge-label planes of the instance (0, 2 or 8; see solve_pair)
 cudaError_t launch_kbest(int W, bool wide_map, bool w32, bool sm, int bk, const KParams &p,
