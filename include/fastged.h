@@ -169,8 +169,8 @@ typedef struct {
     int64_t input_bytes;      /* resident input bytes (flattened graphs, tables)           */
     int64_t device_bytes;     /* all device bytes the plan holds                           */
     int64_t output_bytes;     /* bytes fastged_plan_read copies back (cost, map, evals)    */
-    int32_t block_threads[8]; /* per class                                                 */
-    int32_t grid[8];          /* per class                                                 */
+    int32_t block_threads[8]; /* per class (the first 8 classes)                           */
+    int32_t grid[8];          /* per class (the first 8 classes)                           */
     int32_t words[8];         /* per class: 64-bit words per bitset                        */
     int32_t smem_bytes[8];    /* per class: dynamic shared memory per team                 */
 } fastged_plan_stats;

@@ -55,6 +55,7 @@ struct Layout {
     int32_t fs;                // successors per node at most (n2max + 1)
     int32_t word_bytes;        // 4 or 8: bytes per bitset word
     int32_t B;                 // edge-label planes
+    int32_t pk;                // 1: successors packed as PED << 16 | slot << jbits | j
     int64_t smem_bytes;        // dynamic shared memory per CTA
     int64_t slice_bytes;       // global scratch bytes per team (CTA or cluster)
     int64_t team_off;          // cluster teams: offset of the team scalars in the slice

@@ -240,8 +240,11 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_PL] = (size_t)B * kl * W * wb;
     sz[RG_IMGL] = cp.cluster > 1 ? kl * W * wb : 0;
     // single-word classes pack the successor ids into the PED entries
-    sz[RG_CSLOT] = W == 1 ? 0 : ncand * 2;
-    sz[RG_CJ] = W == 1 ? 0 : ncand * msz;
+    // packed classes keep the successor ids inside the PED entries
+    const bool packed = cp.pk && cp.cluster == 1;
+    L.pk = packed ? 1 : 0;
+    sz[RG_CSLOT] = packed ? 0 : ncand * 2;
+    sz[RG_CJ] = packed ? 0 : ncand * msz;
     sz[RG_CAND] = ncand * 4;
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
@@ -313,8 +316,9 @@ static int pow2_ceil(int x)
 static std::string class_key(const ClassPlan &cp, int B, int npairs, int sm_count)
 {
     char buf[128];
-    snprintf(buf, sizeof(buf), "w%d%s%s_b%d_k%d_n%d_%s", cp.W, cp.wide ? "x" : "",
-             cp.w32 ? "h" : "", label_instance(B), pow2_ceil(cp.kmax), pow2_ceil(cp.n2max),
+    snprintf(buf, sizeof(buf), "w%d%s%s%s_b%d_k%d_n%d_%s", cp.W, cp.wide ? "x" : "",
+             cp.w32 ? "h" : "", cp.pk ? "p" : "", label_instance(B), pow2_ceil(cp.kmax),
+             pow2_ceil(cp.n2max),
              npairs < sm_count ? "few" : "many");
     return buf;
 }
@@ -534,21 +538,26 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         b.map_off[p] = mtot;
         mtot += g1.n;
         int W = words_class(g2.n);
-        // the single-word kernels pack (PED, parent slot, j) into 32 bits: a pair goes there
-        // only if every PED stays below 2^16 and its beam has at most 512 nodes
+        // packing (PED, parent slot, j) into 32 bits needs every PED below 2^16 (PEDs never
+        // count vertex insertions, and at most the g2 edges among mapped vertices) and K
+        // within the slot field
         const long long ped_bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
                                     (long long)g1.m * std::max(c.e_sub, c.e_del) +
                                     (long long)g2.m * c.e_ins;
-        if (W == 1 && !packable(ped_bound, kp)) W = 2;
+        const bool pk = packable(ped_bound, kp, g2.n);
+        if (W == 1 && !pk) W = 2;
         const bool wide = g2.n >= 255;
         const bool w32 = W == 1 && g2.n <= 32;
-        const int key = w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0);
+        const int key =
+            (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
+            (pk ? 1 : 0);
         if (cls_of[key] < 0) {
             cls_of[key] = (int)b.classes.size();
             ClassPlan cp;
             cp.W = W;
             cp.wide = wide || W >= 8;
             cp.w32 = w32;
+            cp.pk = pk;
             b.classes.push_back(cp);
         }
         ClassPlan &cp = b.classes[cls_of[key]];

@@ -11,7 +11,7 @@
 
 namespace fastged {
 
-constexpr int kMaxClasses = 8;
+constexpr int kMaxClasses = 16;
 
 struct DevBuf {
     void *p = nullptr;
@@ -33,6 +33,7 @@ struct ClassPlan {
     int W = 1;
     bool wide = false;
     bool w32 = false;             // one 32-bit word per bitset (every g2 has <= 32 vertices)
+    bool pk = false;              // successors packed into one 32-bit entry (see packable)
     bool all_smem = false;        // every region of a team fits in shared memory
     int cluster = 1;              // CTAs per team (> 1: a thread-block cluster per pair)
     int n1max = 0, n2max = 0, m1max = 0, kmax = 1;
@@ -70,9 +71,21 @@ int set_error(int code, const char *msg);
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);
-// The single-word kernels store a successor as PED << 16 | parent slot << 7 | j: a pair may
-// use them only if no PED reaches 2^16 and its beam holds at most 512 nodes.
-inline bool packable(long long ped_bound, long long k) { return ped_bound < 65536 && k <= 512; }
+// Packed classes store a successor as PED << 16 | parent slot << jbits | j with
+// jbits = bit length of n2 (j runs over 0..n2): a pair may be packed only if no PED reaches
+// 2^16 and its K fits the remaining 16 - jbits bits. The single-word kernels are always
+// packed; a single-word pair that is not packable is solved by the two-word kernels.
+inline int jbits_of(int n2)
+{
+    int b = 0;
+    while (b < 31 && (1 << b) <= n2) ++b;
+    return b;
+}
+inline bool packable(long long ped_bound, long long k, int n2)
+{
+    const int jb = jbits_of(n2);
+    return ped_bound < 65536 && jb <= 16 && k <= (1LL << (16 - jb));
+}
 void clear_error();
 int flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const fastged_options &opt, Batch &b);

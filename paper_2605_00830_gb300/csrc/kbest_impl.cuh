@@ -157,19 +157,18 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsig
 }
 
 // PED stored in a successor entry: the entry itself, or for packed entries
-// (PED << 16 | parent slot << 7 | j) its upper half.
-template <bool PK>
-__device__ __forceinline__ int cand_ped(int32_t e)
+// (PED << 16 | parent slot << jbits | j) its upper half.
+__device__ __forceinline__ int cand_ped(int32_t e, bool pk)
 {
-    return PK ? (int)((uint32_t)e >> 16) : e;
+    return pk ? (int)((uint32_t)e >> 16) : e;
 }
 
 // Stable compaction of the kept successors of this warp, in enumeration order: every
 // candidate with PED < T, and the first q with PED == T counted over the whole team.
 // keep_before / eq_before: kept / tied candidates of the warps before this one.
-template <typename Word, bool PK>
+template <typename Word>
 __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, int n, int T,
-                                           int q, int keep_before, int eq_before)
+                                           int q, int keep_before, int eq_before, bool pk)
 {
     const int lane = threadIdx.x & 31;
     const int keep0 = keep_before;
@@ -182,7 +181,7 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = kb + 32 * u + lane;
-            v[u] = k < n ? cand_ped<PK>(cand[k]) : INT_MAX;
+            v[u] = k < n ? cand_ped(cand[k], pk) : INT_MAX;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(0xffffffffu, v[u] <= T);
@@ -210,10 +209,10 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 // Exact selection used when the kept set reaches past the histogram window: the K-th
 // smallest PED is found by bisection over team-wide counts, the kept candidates are
 // compacted stably, and ranked by (PED, enumeration order); sel receives successor indices.
-template <typename MapT, typename Word, bool CL, bool PK, typename TS>
+template <typename MapT, typename Word, bool CL, typename TS>
 __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
                                           int32_t *sel, int32_t *selped, TS &S, int L,
-                                          int stride, int newL, int lo)
+                                          int stride, int newL, int lo, bool pk)
 {
     const Team<CL> tm;
     const int tid = tm.tid, lane = threadIdx.x & 31, warp = tm.warp;
@@ -226,7 +225,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     R.kped = kped;
 
     int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, cand_ped<PK>(cand[base + k]));
+    for (int k = lane; k < n; k += 32) mx = max(mx, cand_ped(cand[base + k], pk));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -239,7 +238,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (cand_ped<PK>(cand[base + k]) <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (cand_ped(cand[base + k], pk) <= mid);
         cnt = warp_sum(cnt);
         tm.sync();
         if (tid == 0) S.cnt = 0;
@@ -251,7 +250,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     const int thr = lo;
     int nlt = 0, neq = 0;
     for (int k = lane; k < n; k += 32) {
-        const int v = cand_ped<PK>(cand[base + k]);
+        const int v = cand_ped(cand[base + k], pk);
         nlt += (v < thr);
         neq += (v == thr);
     }
@@ -268,7 +267,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
         eq_before += S.weq[w];
     }
     keep_before += min(q, eq_before);
-    compact_kept<Word, PK>(R, base, n, thr, q, keep_before, eq_before);
+    compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before, pk);
     tm.sync();
     // rank by (PED, enumeration order); klist is in enumeration order
     for (int a = tid; a < newL; a += T) {
@@ -311,10 +310,14 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const int hwin = p.hwin;     // buckets 0..hwin-2 hold one PED each, hwin-1 the rest
     const bool fold_ie = (c.eins == c.edel);
     MapT *cjv = (MapT *)R.cj;
-    // single-word classes pack every successor into one 32-bit entry of R.cand:
-    // PED << 16 | parent slot << 7 | j (the host routes a pair here only when its PEDs stay
-    // below 2^16 and K <= 512); the other classes keep PEDs in R.cand and ids in cslot / cj
-    constexpr bool PK = (W == 1) && !CL;
+    // Packed classes keep every successor in one 32-bit entry of R.cand:
+    //   PED << 16 | parent slot << jbits | j,   jbits = bit length of n2 (j = 0..n2).
+    // The host packs a class only if no pair's PED can reach 2^16 and every K fits the slot
+    // field (K <= 2^(16 - jbits)); single-word classes are always packed. Other classes
+    // keep PEDs in R.cand and the ids in cslot / cj.
+    const bool pk = CL ? false : (W == 1 ? true : p.lay.pk != 0);
+    const int jbits = 32 - __clz(n2);
+    const uint32_t jmask = (1u << jbits) - 1u;
     uint32_t *ck = (uint32_t *)R.cand;
     // lane-constant masks: lane b answers for histogram bucket b
     unsigned lanebit[5];
@@ -424,7 +427,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int kw = 0;          // successors of this warp so far
         int wmin = INT_MAX;  // least PED this warp scored
         // PED of successor idx
-        auto ped_at = [&](int idx) -> int { return cand_ped<PK>(R.cand[idx]); };
+        auto ped_at = [&](int idx) -> int { return cand_ped(R.cand[idx], pk); };
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
@@ -499,7 +502,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // increasing order, then n2 for v_i -> eps. Single-word bitsets: each lane walks
             // its own node's bits; wider ones: the warp sweeps each node's vertices 32 at a
             // time and compacts the free ones with a ballot.
-            if (PK) {
+            if (W == 1 && !CL) {
                 if (act) {
                     const Word *im = imgw + (int64_t)(s - ioff) * W;
                     int idx = base + kw + excl;
@@ -508,9 +511,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     while (x) {
                         const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
                         x &= x - (Word)1;
-                        ck[idx++] = ((uint32_t)s << 7) | (uint32_t)t;
+                        ck[idx++] = ((uint32_t)s << jbits) | (uint32_t)t;
                     }
-                    ck[idx] = ((uint32_t)s << 7) | (uint32_t)n2;
+                    ck[idx] = ((uint32_t)s << jbits) | (uint32_t)n2;
                 }
             } else {
                 for (int t = 0; t < ng; ++t) {
@@ -518,20 +521,28 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     const Word *im = imgw + (int64_t)(st_ - ioff) * W;
                     const int o0 = base + kw + __shfl_sync(0xffffffffu, excl, t);
                     int pos = 0;
-                    for (int jb = 0; jb < n2; jb += 32) {
-                        const int j = jb + lane;
+                    for (int j0 = 0; j0 < n2; j0 += 32) {
+                        const int j = j0 + lane;
                         const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
                         const unsigned bal = __ballot_sync(0xffffffffu, fr);
                         if (fr) {
                             const int idx = o0 + pos + __popc(bal & lanemask_lt());
-                            R.cslot[idx] = (uint16_t)st_;
-                            cjv[idx] = (MapT)j;
+                            if (pk) {
+                                ck[idx] = ((uint32_t)st_ << jbits) | (uint32_t)j;
+                            } else {
+                                R.cslot[idx] = (uint16_t)st_;
+                                cjv[idx] = (MapT)j;
+                            }
                         }
                         pos += __popc(bal);
                     }
                     if (lane == 0) {
-                        R.cslot[o0 + pos] = (uint16_t)st_;
-                        cjv[o0 + pos] = (MapT)n2;
+                        if (pk) {
+                            ck[o0 + pos] = ((uint32_t)st_ << jbits) | (uint32_t)n2;
+                        } else {
+                            R.cslot[o0 + pos] = (uint16_t)st_;
+                            cjv[o0 + pos] = (MapT)n2;
+                        }
                     }
                 }
             }
@@ -577,11 +588,12 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 for (int u = 0; u < U; ++u) {
                     const int k = kb + 32 * u + lane;
                     const int idx = base + kw + k;
-                    if constexpr (PK) {
-                        idu[u] = k < gtot ? ck[idx] : (((uint32_t)g0 << 7) | (uint32_t)n2);
-                        scu[u] = (int)(idu[u] >> 7);
-                        ju[u] = (int)(idu[u] & 127u);
+                    if (pk) {
+                        idu[u] = k < gtot ? ck[idx] : (((uint32_t)g0 << jbits) | (uint32_t)n2);
+                        scu[u] = (int)(idu[u] >> jbits);
+                        ju[u] = (int)(idu[u] & jmask);
                     } else {
+                        idu[u] = 0u;
                         scu[u] = k < gtot ? (int)R.cslot[idx] : g0;
                         ju[u] = k < gtot ? (int)cjv[idx] : n2;
                     }
@@ -593,7 +605,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 for (int u = 0; u < U; ++u) {
                     const int k = kb + 32 * u + lane;
                     if (k < gtot) {
-                        if constexpr (PK) ck[base + kw + k] = ((uint32_t)pu[u] << 16) | idu[u];
+                        if (pk) ck[base + kw + k] = ((uint32_t)pu[u] << 16) | idu[u];
                         else R.cand[base + kw + k] = pu[u];
                         wmin = pu[u] < wmin ? pu[u] : wmin;
                     }
@@ -640,9 +652,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         PHASE_MARK(1);
         // (parent slot << kSelShift) | j of successor idx
         auto decode = [&](int idx) -> int {
-            if constexpr (PK) {
-                const uint32_t id = ck[idx];
-                return (int)(((id >> 7) & 511u) << kSelShift) | (int)(id & 127u);
+            if (pk) {
+                const uint32_t id = ck[idx] & 0xffffu;
+                return (int)((id >> jbits) << kSelShift) | (int)(id & jmask);
             } else {
                 return ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
             }
@@ -763,7 +775,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int eq_before = __shfl_sync(0xffffffffu, mine, thr);
             const int lt_before = warp_sum(lane < thr ? mine : 0);
             const int kbeg = lt_before + min(q, eq_before);
-            const int kcnt = compact_kept<Word, PK>(R, base, kw, pa + thr, q, kbeg, eq_before);
+            const int kcnt = compact_kept<Word>(R, base, kw, pa + thr, q, kbeg, eq_before, pk);
             __syncwarp();
             PHASE_MARK(8);
             int run = lane < thr ? mine : min(q, eq_before);   // kept of bucket `lane` before
@@ -792,8 +804,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #ifdef FASTGED_PHASE_TIMERS
             if (threadIdx.x == 0) ph[7] += 1;   // levels that took the exact selection
 #endif
-            select_exact<MapT, Word, CL, PK, TS>(R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
-                                                 stride, newL, pa + hwin - 1);
+            select_exact<MapT, Word, CL, TS>(R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
+                                             stride, newL, pa + hwin - 1, pk);
             tm.sync();
             for (int r = tid; r < newL; r += T) R.sel[r] = decode(R.sel[r]);
         }

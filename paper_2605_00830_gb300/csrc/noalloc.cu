@@ -142,7 +142,8 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     const long long ped_bound =
         (long long)b->max_n * std::max(cost->v_sub, cost->v_del) +
         (long long)b->max_m * (std::max(cost->e_sub, cost->e_del) + cost->e_ins);
-    if (cp.W == 1 && !packable(ped_bound, K)) cp.W = 2;
+    cp.pk = packable(ped_bound, K, b->max_n);
+    if (cp.W == 1 && !cp.pk) cp.W = 2;
     cp.w32 = cp.W == 1 && b->max_n <= 32;
     cp.wide = b->max_n >= 255 || cp.W >= 8;
     cp.n1max = b->max_n;

@@ -80,6 +80,18 @@ def test_packed_single_word_entries_at_their_limits():
         assert_parity(w1, gpu_run(w1, K=K), K=K)
 
 
+@pytest.mark.parametrize("n2,kmax", [(31, 2048), (64, 512), (100, 512), (128, 256), (200, 256)])
+def test_packed_slot_field_at_its_width(n2, kmax):
+    """The packed entry gives j the bit length of n2 and the slot the other 16 - jbits bits:
+    K = 2^(16 - jbits) fills the slot field (packed), one more takes the unpacked path."""
+    st = W.Stream(41, n2)
+    g1 = W.erdos_renyi(st, 5, 0.5, 3)
+    g2 = W.erdos_renyi(st, n2, 0.08, 3)
+    w = single([(g1, g2)], W.UNIT_COSTS, kmax)
+    for K in (kmax, kmax + 1):
+        assert_parity(w, gpu_run(w, K=K), K=K)
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_block_sizes(bt):
     w = W.config2(150)
