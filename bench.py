@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--workload", choices=["molecule", "dense", "large"], default="molecule",
                     help="molecule: the 20,000-pair batch the metric is quoted on (default); "
                          "dense / large: the 4,096-pair dense ER and 64-pair BA batches")
+    ap.add_argument("--block", type=int, default=0,
+                    help="threads per team for every size class (0 = autotuned)")
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--no-extras", action="store_true",
@@ -267,7 +269,10 @@ def ours(args):
     mm = F.marshal(w)
     g = F.FastGED(w.cost)
     # the autotuner times each size class's team shapes once, outside the timed region
-    plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options(autotune=1))
+    # (--block fixes the team size instead, so that a profiler sees only the timed launches)
+    popt = (F.make_options(block_threads=args.block) if args.block else
+            F.make_options(autotune=1))
+    plan = F.fastged_plan_create(g.h, mm, w.K, popt)
     # a dedicated stream: the legacy default stream has handle 0, which the C ABI reads as
     # "the plan's own stream"
     stream = torch.cuda.Stream()

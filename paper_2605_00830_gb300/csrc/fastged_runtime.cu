@@ -223,6 +223,7 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     L.kloc = (int32_t)kl;
     sz[RG_HIST] = (size_t)kHistMax * NW * 4;
     sz[RG_ALPHA2] = (size_t)L.n2s * 4;
+    sz[RG_CROW] = (size_t)2 * L.n2s * 4;
     sz[RG_A2T] = (size_t)W * L.n2s * wb;
     sz[RG_L2T] = (size_t)B * W * L.n2s * wb;
     sz[RG_SBASE] = kl * 4;
@@ -249,14 +250,15 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
     // shared memory is filled in order of access frequency; the rest goes to global scratch
-    static const int prio[RG_COUNT] = {RG_HIST, RG_ALPHA2, RG_SBASE, RG_PED0, RG_PED1,
+    static const int prio[RG_COUNT] = {RG_HIST, RG_CROW, RG_ALPHA2, RG_SBASE, RG_PED0, RG_PED1,
                                        RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_NOFF,
                                        RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
                                        RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1,
                                        RG_IMGL};
     // cluster teams: the per-CTA tables the CTA writes (P, PL, sbase, staged Img) must be in
     // shared memory, so they come first
-    static const int prio_cl[RG_COUNT] = {RG_SBASE, RG_P, RG_PL, RG_IMGL, RG_ALPHA2, RG_NOFF,
+    static const int prio_cl[RG_COUNT] = {RG_SBASE, RG_P, RG_PL, RG_IMGL, RG_CROW, RG_ALPHA2,
+                                          RG_NOFF,
                                           RG_A2T, RG_L2T, RG_NBR, RG_HIST, RG_PED0, RG_PED1,
                                           RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_IMG0,
                                           RG_IMG1, RG_CSLOT, RG_CJ, RG_CAND, RG_MAP0, RG_MAP1};
@@ -264,7 +266,7 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     // of the read-only target-graph tables and neighbour lists, everything else is global
     auto cta_local = [](int r) {
         return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR ||
-               r == RG_P || r == RG_PL || r == RG_SBASE || r == RG_IMGL;
+               r == RG_P || r == RG_PL || r == RG_SBASE || r == RG_IMGL || r == RG_CROW;
     };
     size_t s_used = 0, g_used = 0;
     L.smem_mask = 0;
@@ -406,7 +408,8 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     if (cp.cluster > 1) {
         const int block = forced_block ? forced_block : 512;
         plan_layout(cp, B, block, max_dyn);
-        const uint32_t need = (1u << RG_SBASE) | (1u << RG_P) | (1u << RG_PL) | (1u << RG_IMGL);
+        const uint32_t need = (1u << RG_SBASE) | (1u << RG_P) | (1u << RG_PL) | (1u << RG_IMGL) |
+                              (1u << RG_CROW);
         if ((cp.lay.smem_mask & need) != need) cp.cluster = 1;   // too large: one CTA per pair
     }
     if (cp.cluster > 1) {

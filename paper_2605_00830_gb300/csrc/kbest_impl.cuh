@@ -119,7 +119,7 @@ struct Team {
 
 template <typename Word>
 struct Regions {
-    int32_t *hist, *alpha2, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
+    int32_t *hist, *alpha2, *crow, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
     int32_t *ped0, *ped1;
     Word *a2t, *l2t, *img0, *img1, *P, *PL, *imgl;
     uint16_t *cslot;
@@ -347,6 +347,16 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             }
         }
         for (int u = ltid; u < n2; u += LT) R.alpha2[u] = p.vlab[m2.lab_off + u];
+        // column n2 of the target tables is the deletion v_i -> eps: no g2 neighbours, so the
+        // substitution formula scores it with the deletion's edge costs (see succ_ped)
+        for (int w = ltid; w < W; w += LT) R.a2t[w * N2S + n2] = (Word)0;
+        for (int x = ltid; x < B * W; x += LT) R.l2t[x * N2S + n2] = (Word)0;
+        // S1 cost row of level 0 (the row of level i + 1 is written during level i)
+        if (n1 > 0) {
+            const int a10 = p.vlab[m1.lab_off];
+            for (int u = ltid; u <= n2; u += LT)
+                R.crow[u] = u < n2 ? ((p.vlab[m2.lab_off + u] != a10) ? c.vsub : 0) : c.vdel;
+        }
         // number of neighbours v_k of v_i with k < i
         for (int v = ltid; v < n1; v += LT) {
             const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
@@ -399,13 +409,12 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     uint8_t *mapc = R.map0, *mapn = R.map1;
     Word *imgc = R.img0, *imgn = R.img1;
     int32_t *pedc = R.ped0, *pedn = R.ped1;
+    int32_t *crc = R.crow, *crn = R.crow + N2S;   // S1 cost rows of this level and the next
     tm.sync();
     PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
-        const int a1 = p.vlab[m1.lab_off + i];
         const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
-        const int delcost = c.vdel + c.edel * deg;   // v_i -> eps takes its edges to v_0..v_{i-1}
         const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
         const int base = s_lo * stride;              // this warp's successor storage
         // node tables the warp prepares and evaluates are indexed from cs0: 0 for a one-CTA
@@ -549,9 +558,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             __syncwarp();
             PHASE_MARK(5);
 
-            // S3: PED of successor (node sc, column j); j == n2 is the deletion v_i -> eps.
-            // Branch-free: the substitution formula is also evaluated for the deletion (its
-            // table reads stay inside the staged rows) and discarded.
+            // S3: PED of successor (node sc, column j). Column j == n2 is the deletion
+            // v_i -> eps: its A2 column is empty, so the implied-edge terms count every
+            // substituted neighbour in P as a deleted edge (with the dcnt deleted neighbours in
+            // sbase, all deg edges to v_0..v_{i-1}), and the cost row holds c_vdel there.
             auto succ_ped = [&](int sc, int j) -> int {
                 const Word *im = imgw + (int64_t)(sc - ioff) * W;
                 const Word *Ps = R.P + (int64_t)(sc - cs0) * W;
@@ -575,9 +585,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         z += popcw((Word)(aw & pw & ld));
                     }
                 }
-                const int cv = (R.alpha2[j] != a1) ? c.vsub : 0;   // S1: cost row entry
-                const int sub = R.sbase[sc - cs0] + cv + c.eins * x + c.edel * y + c.esub * z;
-                return j == n2 ? pedc[sc] + delcost : sub;
+                return R.sbase[sc - cs0] + crc[j] + c.eins * x + c.edel * y + c.esub * z;
             };
             // U chunks of 32 successors per step, their id loads and PEDs independent
             constexpr int U = W <= 2 ? 2 : 1;
@@ -851,8 +859,15 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 }
             }
         }
+        // S1 cost row of the next level (each CTA keeps its own copy)
+        if (i + 1 < n1) {
+            const int a1n = p.vlab[m1.lab_off + i + 1];
+            for (int u = ltid; u <= n2; u += LT)
+                crn[u] = u < n2 ? ((R.alpha2[u] != a1n) ? c.vsub : 0) : c.vdel;
+        }
         tm.sync();
         PHASE_MARK(3);
+        { int32_t *t = crc; crc = crn; crn = t; }
         { uint8_t *t = mapc; mapc = mapn; mapn = t; }
         { Word *t = imgc; imgc = imgn; imgn = t; }
         { int32_t *t = pedc; pedc = pedn; pedn = t; }
@@ -914,6 +929,7 @@ __device__ __forceinline__ Regions<Word> make_regions(F base)
     Regions<Word> R;
     R.hist = (int32_t *)base(RG_HIST);
     R.alpha2 = (int32_t *)base(RG_ALPHA2);
+    R.crow = (int32_t *)base(RG_CROW);
     R.a2t = (Word *)base(RG_A2T);
     R.l2t = (Word *)base(RG_L2T);
     R.sbase = (int32_t *)base(RG_SBASE);
