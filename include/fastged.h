@@ -108,8 +108,15 @@ typedef struct {
                              /* shape (threads per CTA, or CTAs per cluster for large pairs)  */
                              /* on a sample of its pairs, and record the fastest; 0 = use the */
                              /* table's entries where present, built-in rules elsewhere       */
-    int32_t pad;
+    int32_t vertex_order;    /* order in which the levels branch the source vertices:        */
+                             /* FASTGED_ORDER_INDEX (0, the paper's v_0..v_{n1-1}) or         */
+                             /* FASTGED_ORDER_DEGREE (1: descending degree, ties by index;    */
+                             /* an extension, not part of the paper). Maps are returned in   */
+                             /* source index order either way                                 */
 } fastged_options;
+
+#define FASTGED_ORDER_INDEX 0
+#define FASTGED_ORDER_DEGREE 1
 
 typedef struct fastged_handle fastged_handle;
 typedef struct fastged_plan fastged_plan;
@@ -260,6 +267,70 @@ void fastged_serve_destroy(fastged_server *s);
  * fastged_autotune_clear forgets them all (the file is left alone). */
 int fastged_autotune_entries(void);
 void fastged_autotune_clear(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Edit paths and GED matrices (Sec. 6 of the paper uses both: the edit path between two
+ * architectures, half of whose operations are applied to cross them over, and the GED of
+ * every test graph to every training graph for nearest-neighbour classification).
+ * --------------------------------------------------------------------------------------- */
+#define FASTGED_OP_VINS 0   /* insert g2 vertex g2_u                                       */
+#define FASTGED_OP_VSUB 1   /* relabel g1 vertex g1_u to the label of g2 vertex g2_u        */
+#define FASTGED_OP_EDEL 2   /* delete g1 edge (g1_u, g1_v)                                 */
+#define FASTGED_OP_ESUB 3   /* relabel g1 edge (g1_u, g1_v) to the label of g2 edge        */
+                            /* (g2_u, g2_v)                                                */
+#define FASTGED_OP_EINS 4   /* insert g2 edge (g2_u, g2_v)                                 */
+#define FASTGED_OP_VDEL 5   /* delete g1 vertex g1_u                                       */
+
+typedef struct {
+    int32_t kind;   /* FASTGED_OP_*                                                        */
+    int32_t cost;   /* the operation's cost under the cost model                           */
+    int32_t g1_u;   /* source-side vertex, or first edge endpoint; -1 if none              */
+    int32_t g1_v;   /* source-side second edge endpoint; -1 if none                        */
+    int32_t g2_u;   /* target-side vertex, or first edge endpoint (the image of g1_u for   */
+                    /* an edge substitution); -1 if none                                  */
+    int32_t g2_v;   /* target-side second edge endpoint; -1 if none                        */
+} fastged_edit_op;
+
+/* The edit path that the vertex map `mapping` (n1 entries: the g2 image of each g1 vertex,
+ * -1 = deleted; as fastged_batch returns it) induces from g1 to g2 (Sec. 2.2-2.4): only
+ * operations that change something are listed (a substitution keeping the label is not an
+ * edit), in this order, each group by increasing index (edges in input order):
+ *   vertex insertions (g2 vertices outside the image), vertex substitutions (label
+ *   changes), edge deletions (g1 edges whose image is not a g2 edge), edge substitutions
+ *   (label changes), edge insertions (g2 edges that are no image), vertex deletions.
+ * Every prefix of the list is a valid sequence: inserted vertices exist before edges use
+ * them, and a vertex is deleted only after its edges.
+ *   ops        array of capacity `cap`, or NULL to only count
+ *   n_ops      receives the number of operations (at most n1 + n2 + m1 + m2)
+ *   total_cost receives their summed cost (= the cost of the map); may be NULL
+ * Errors: FASTGED_ERR_INVALID_ARG for an invalid graph, a map that is not an injective
+ * partial map into g2, or ops != NULL with cap < the number of operations (nothing is
+ * written then except n_ops). Host function; no GPU work. */
+int fastged_edit_path(const fastged_cost_model *cost, const fastged_graph *g1,
+                      const fastged_graph *g2, const int32_t *mapping, fastged_edit_op *ops,
+                      int32_t cap, int32_t *n_ops, int64_t *total_cost);
+
+/* Applies the first n_apply operations of the edit path that `mapping` induces from g1 to
+ * g2 (as fastged_edit_path lists them) to g1 and writes the resulting graph (the map tells
+ * which g1 vertex an inserted edge's endpoint is): its vertices are the g1 vertices not
+ * deleted (in g1 order) followed by the inserted g2 vertices (in operation order); edges
+ * refer to those new ids. With every operation applied the result equals g2 up to the
+ * vertex renaming the map gives. Output capacities: out_vlabel n1 + n2 entries, out_edges
+ * 2 (m1 + m2), out_elabel m1 + m2 (NULL when neither graph has edge labels).
+ * Errors: FASTGED_ERR_INVALID_ARG for invalid graphs or operations. Host function. */
+int fastged_apply_edit_ops(const fastged_graph *g1, const fastged_graph *g2,
+                           const int32_t *mapping, const fastged_edit_op *ops,
+                           int32_t n_apply, int32_t *out_n,
+                           int32_t *out_vlabel, int32_t *out_m, int32_t *out_edges,
+                           int32_t *out_elabel);
+
+/* GED matrix: out[r * n_cols + c] = K-Best GED (upper bound) from graphs[rows[r]] to
+ * graphs[cols[c]], every entry computed as one pair of a single batch (with rows == cols it
+ * is the all-pairs matrix of a set; the diagonal is computed too). opt as in
+ * fastged_batch_ex (NULL = defaults; k_per_pair must be NULL). Errors as fastged_batch_ex. */
+int fastged_cross(fastged_handle *h, const fastged_graph *graphs, int32_t n_graphs,
+                  const int32_t *rows, int32_t n_rows, const int32_t *cols, int32_t n_cols,
+                  int32_t K, const fastged_options *opt, int32_t *out);
 
 /* Integer-pipe throughput of the current device (no counterpart in the paper; it is the
  * measured peak the benchmark compares the successor evaluation against). Runs three

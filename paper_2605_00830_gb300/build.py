@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["kbest_kernels.cu", "kbest_b0.cu", "kbest_b2.cu", "kbest_b8.cu", "fastged_runtime.cu",
-           "probe_kernels.cu", "noalloc.cu", "serve.cu"]
+           "probe_kernels.cu", "noalloc.cu", "serve.cu", "paths.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

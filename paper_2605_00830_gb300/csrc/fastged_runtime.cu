@@ -448,6 +448,72 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     return FASTGED_OK;
 }
 
+// Source graphs relabelled so that vertex k is the k-th in descending-degree order (ties by
+// index): every graph that is a pair's source gets a relabelled copy appended to the graph
+// list, and the pairs point at the copies. perm of a copy maps new ids to original ids.
+struct Reordered {
+    fastged_pair_list list{};
+    std::vector<fastged_graph> graphs;
+    std::vector<std::vector<int32_t>> store;   // labels, edges and edge labels of the copies
+    std::vector<int32_t> pairs;
+    std::vector<int> copy_of;                  // graph -> index of its copy, or -1
+    std::vector<std::vector<int32_t>> perm;    // per copy: new id -> original id
+};
+
+static bool reorder_sources(const fastged_pair_list *pl, Reordered &ro)
+{
+    const int ng = pl->n_graphs, np = pl->n_pairs;
+    ro.graphs.assign(pl->graphs, pl->graphs + ng);
+    ro.pairs.assign(pl->pairs, pl->pairs + 2 * (size_t)np);
+    ro.copy_of.assign(ng, -1);
+    for (int p = 0; p < np; ++p) {
+        const int g = pl->pairs[2 * p];
+        if (g < 0 || g >= ng) continue;   // reported by the pair validation
+        if (ro.copy_of[g] < 0) {
+            const fastged_graph &G = pl->graphs[g];
+            if (G.n < 0 || G.n > FASTGED_MAX_N || G.m < 0 || (G.n > 0 && !G.vlabel) ||
+                (G.m > 0 && !G.edges))
+                continue;   // reported by the graph validation
+            bool ok = true;
+            std::vector<int> deg(G.n, 0);
+            for (int k = 0; k < G.m && ok; ++k) {
+                const int u = G.edges[2 * k], v = G.edges[2 * k + 1];
+                if (u < 0 || v < 0 || u >= G.n || v >= G.n) ok = false;
+                else { ++deg[u]; ++deg[v]; }
+            }
+            if (!ok) continue;
+            std::vector<int32_t> perm(G.n), inv(G.n);
+            for (int v = 0; v < G.n; ++v) perm[v] = v;
+            std::stable_sort(perm.begin(), perm.end(),
+                             [&](int a, int c) { return deg[a] > deg[c]; });
+            for (int k = 0; k < G.n; ++k) inv[perm[k]] = k;
+            std::vector<int32_t> lab(G.n), edg(2 * (size_t)G.m), el;
+            for (int k = 0; k < G.n; ++k) lab[k] = G.vlabel[perm[k]];
+            for (int k = 0; k < G.m; ++k) {
+                edg[2 * k] = inv[G.edges[2 * k]];
+                edg[2 * k + 1] = inv[G.edges[2 * k + 1]];
+            }
+            if (G.elabel) el.assign(G.elabel, G.elabel + G.m);
+            ro.store.push_back(std::move(lab));
+            ro.store.push_back(std::move(edg));
+            ro.store.push_back(std::move(el));
+            fastged_graph C = G;
+            C.vlabel = ro.store[ro.store.size() - 3].data();
+            C.edges = ro.store[ro.store.size() - 2].data();
+            C.elabel = G.elabel ? ro.store[ro.store.size() - 1].data() : nullptr;
+            ro.copy_of[g] = (int)ro.graphs.size();
+            ro.graphs.push_back(C);
+            ro.perm.push_back(std::move(perm));
+        }
+        ro.pairs[2 * p] = ro.copy_of[g];
+    }
+    ro.list.n_graphs = (int32_t)ro.graphs.size();
+    ro.list.graphs = ro.graphs.data();
+    ro.list.n_pairs = np;
+    ro.list.pairs = ro.pairs.data();
+    return true;
+}
+
 int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
                      const fastged_options &opt, Batch &b)
 {
@@ -464,6 +530,14 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     if (opt.block_threads != 0 && opt.block_threads != 128 && opt.block_threads != 256 &&
         opt.block_threads != 512)
         return set_error(FASTGED_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+    if (opt.vertex_order != FASTGED_ORDER_INDEX && opt.vertex_order != FASTGED_ORDER_DEGREE)
+        return set_error(FASTGED_ERR_INVALID_ARG, "vertex_order must be 0 or 1");
+    b.perm.clear();
+    Reordered ro;
+    if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
+        reorder_sources(pl, ro);
+        pl = &ro.list;
+    }
 
     const int ng = pl->n_graphs, np = pl->n_pairs;
     b.n_graphs = ng;
@@ -572,6 +646,15 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         pair_class[p] = cls_of[key];
     }
     b.map_total = mtot;
+    if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
+        b.perm.assign((size_t)mtot, 0);
+        const int ng0 = (int)ro.copy_of.size();
+        for (int p = 0; p < np; ++p) {
+            const int c = pl->pairs[2 * p] - ng0;
+            if (c < 0) continue;   // no copy: the source graph fails validation below
+            std::copy(ro.perm[c].begin(), ro.perm[c].end(), b.perm.begin() + b.map_off[p]);
+        }
+    }
     // heaviest pairs first inside each class (longest-processing-time order)
     for (auto &cp : b.classes) {
         std::vector<std::pair<long long, int>> wk(cp.order.size());
@@ -800,7 +883,19 @@ int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *ou
     if (err) return set_error(FASTGED_ERR_CUDA, "device error flag " + std::to_string(err));
     if (out_cost) memcpy(out_cost, host_out + b.woff_cost, 4 * (size_t)b.n_pairs);
     if (out_nevals) memcpy(out_nevals, host_out + b.woff_nev, 8 * (size_t)b.n_pairs);
-    if (out_mapping) memcpy(out_mapping, host_out + b.woff_map, 4 * (size_t)b.map_total);
+    if (out_mapping) {
+        const int32_t *res = (const int32_t *)(host_out + b.woff_map);
+        if (b.perm.empty()) {
+            memcpy(out_mapping, res, 4 * (size_t)b.map_total);
+        } else {
+            // level k branched source vertex perm[k]: return the map in source index order
+            for (int p = 0; p < b.n_pairs; ++p) {
+                const int64_t o = b.map_off[p];
+                const int64_t e = p + 1 < b.n_pairs ? b.map_off[p + 1] : b.map_total;
+                for (int64_t k = o; k < e; ++k) out_mapping[o + b.perm[k]] = res[k];
+            }
+        }
+    }
     return FASTGED_OK;
 }
 

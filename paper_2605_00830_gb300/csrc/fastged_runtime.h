@@ -54,6 +54,9 @@ struct Batch {
     fastged_options opt{};
     std::vector<GraphMeta> meta;
     std::vector<int64_t> map_off;
+    // FASTGED_ORDER_DEGREE: for map entry map_off[p] + k, the source vertex branched at level
+    // k (empty in index order)
+    std::vector<int32_t> perm;
     int64_t n_vlab = 0, n_edges = 0, adj_words = 0, plane_words = 0, map_total = 0;
     std::vector<ClassPlan> classes;
     // input region (pinned staging == device input buffer)

@@ -27,6 +27,8 @@ FASTGED_ERR_BUSY = -5
 FASTGED_ERR_STOPPED = -6
 FASTGED_FORM_BATCHED = 0
 FASTGED_FORM_PLAIN = 1
+FASTGED_ORDER_INDEX = 0
+FASTGED_ORDER_DEGREE = 1
 
 EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
             "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
@@ -34,7 +36,8 @@ EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_
             "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc",
             "fastged_serve_start", "fastged_serve_submit", "fastged_serve_poll",
             "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy",
-            "fastged_autotune_entries", "fastged_autotune_clear"]
+            "fastged_autotune_entries", "fastged_autotune_clear", "fastged_edit_path",
+            "fastged_apply_edit_ops", "fastged_cross"]
 
 
 class FastGEDError(RuntimeError):
@@ -62,7 +65,7 @@ class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("k_per_pair", ctypes.c_void_p), ("hist_window", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("vertex_order", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -157,6 +160,12 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_serve_stop.restype = None
     lib.fastged_serve_destroy.argtypes = [vp]
     lib.fastged_serve_destroy.restype = None
+    lib.fastged_edit_path.argtypes = [ctypes.POINTER(CostModel), ctypes.POINTER(GraphC),
+                                      ctypes.POINTER(GraphC), vp, vp, i32, vp, vp]
+    lib.fastged_apply_edit_ops.argtypes = [ctypes.POINTER(GraphC), ctypes.POINTER(GraphC), vp,
+                                           vp, i32, vp, vp, vp, vp, vp]
+    lib.fastged_cross.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, ctypes.POINTER(Options),
+                                  vp]
     lib.fastged_autotune_entries.restype = ctypes.c_int
     lib.fastged_autotune_clear.restype = None
     for name in EXPORTED:
@@ -235,12 +244,12 @@ def marshal(w) -> Marshalled:
 
 def make_options(form: int = FASTGED_FORM_BATCHED, variant: int = 0, k_per_pair=None,
                  hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1,
-                 autotune: int = 0):
+                 autotune: int = 0, vertex_order: int = FASTGED_ORDER_INDEX):
     kpp = None
     if k_per_pair is not None:
         kpp = np.ascontiguousarray(np.asarray(k_per_pair, dtype=np.int32))
     o = Options(form, variant, kpp.ctypes.data if kpp is not None else None, hist_window,
-                block_threads, use_cuda_graph, autotune, 0)
+                block_threads, use_cuda_graph, autotune, vertex_order)
     o._keep = kpp
     return o
 
@@ -448,3 +457,108 @@ class Server:
         except Exception:
             pass
 
+
+
+# ------------------------------------------------------------------------------------------
+# edit paths and GED matrices
+# ------------------------------------------------------------------------------------------
+FASTGED_OP_VINS, FASTGED_OP_VSUB, FASTGED_OP_EDEL = 0, 1, 2
+FASTGED_OP_ESUB, FASTGED_OP_EINS, FASTGED_OP_VDEL = 3, 4, 5
+EDIT_OP_DTYPE = np.dtype([("kind", "<i4"), ("cost", "<i4"), ("g1_u", "<i4"), ("g1_v", "<i4"),
+                          ("g2_u", "<i4"), ("g2_v", "<i4")])
+
+
+class _OneGraph:
+    """One graph as a fastged_graph struct (its arrays kept alive with it)."""
+
+    def __init__(self, g):
+        self.vl = np.ascontiguousarray(np.asarray(g.vlabel, dtype=np.int32).reshape(-1))
+        self.ed = np.ascontiguousarray(np.asarray(g.edges, dtype=np.int32).reshape(-1))
+        self.el = (None if g.elabel is None else
+                   np.ascontiguousarray(np.asarray(g.elabel, dtype=np.int32).reshape(-1)))
+        self.st = GraphC(int(g.n), self.vl.ctypes.data if self.vl.size else None,
+                         int(self.ed.size // 2), self.ed.ctypes.data if self.ed.size else None,
+                         self.el.ctypes.data if self.el is not None and self.el.size else None)
+
+
+def _cost_model(cost: Sequence[int]) -> CostModel:
+    return CostModel(*[int(x) for x in cost])
+
+
+def fastged_edit_path(cost: Sequence[int], g1, g2, mapping) -> Tuple[np.ndarray, int]:
+    """(operations as an EDIT_OP_DTYPE array, their total cost) of the edit path the vertex
+    map induces from g1 to g2."""
+    lib = load()
+    a, b = _OneGraph(g1), _OneGraph(g2)
+    mp = np.ascontiguousarray(np.asarray(mapping, dtype=np.int32).reshape(-1))
+    cm = _cost_model(cost)
+    n = ctypes.c_int32(0)
+    tot = ctypes.c_int64(0)
+    _check(lib, lib.fastged_edit_path(ctypes.byref(cm), ctypes.byref(a.st), ctypes.byref(b.st),
+                                      mp.ctypes.data if mp.size else None, None, 0,
+                                      ctypes.byref(n), None))
+    ops = np.zeros(n.value, dtype=EDIT_OP_DTYPE)
+    _check(lib, lib.fastged_edit_path(ctypes.byref(cm), ctypes.byref(a.st), ctypes.byref(b.st),
+                                      mp.ctypes.data if mp.size else None,
+                                      ops.ctypes.data if ops.size else None, int(ops.size),
+                                      ctypes.byref(n), ctypes.byref(tot)))
+    return ops, int(tot.value)
+
+
+def fastged_apply_edit_ops(g1, g2, mapping, ops: np.ndarray, n_apply: int):
+    """The graph obtained from g1 by applying the first n_apply operations of its edit path
+    to g2 (vertex ids: surviving g1 vertices in order, then inserted g2 vertices)."""
+    from .workloads import Graph
+    lib = load()
+    a, b = _OneGraph(g1), _OneGraph(g2)
+    mp = np.ascontiguousarray(np.asarray(mapping, dtype=np.int32).reshape(-1))
+    ops = np.ascontiguousarray(ops, dtype=EDIT_OP_DTYPE)
+    nmax = int(g1.n) + int(g2.n)
+    mmax = a.ed.size // 2 + b.ed.size // 2
+    vl = np.zeros(max(nmax, 1), np.int32)
+    ed = np.zeros(max(2 * mmax, 1), np.int32)
+    labelled = a.el is not None or b.el is not None
+    el = np.zeros(max(mmax, 1), np.int32) if labelled else None
+    on, om = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib, lib.fastged_apply_edit_ops(ctypes.byref(a.st), ctypes.byref(b.st),
+                                           mp.ctypes.data if mp.size else None,
+                                           ops.ctypes.data if ops.size else None, int(n_apply),
+                                           ctypes.byref(on), vl.ctypes.data, ctypes.byref(om),
+                                           ed.ctypes.data,
+                                           el.ctypes.data if el is not None else None))
+    return Graph(on.value, vl[:on.value].copy(), ed[:2 * om.value].reshape(-1, 2).copy(),
+                 el[:om.value].copy() if el is not None else None)
+
+
+def fastged_cross(h: int, graphs, rows, cols, K: int, opt: Optional[Options] = None
+                  ) -> np.ndarray:
+    """GED matrix [len(rows), len(cols)] from graphs[rows[r]] to graphs[cols[c]]."""
+    lib = load()
+    mm = Marshalled(graphs, np.zeros((0, 2), np.int32))
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1))
+    c = np.ascontiguousarray(np.asarray(cols, dtype=np.int32).reshape(-1))
+    out = np.zeros((r.size, c.size), np.int32)
+    _check(lib, lib.fastged_cross(h, mm.gs.ctypes.data if len(graphs) else None, len(graphs),
+                                  r.ctypes.data if r.size else None, int(r.size),
+                                  c.ctypes.data if c.size else None, int(c.size), int(K),
+                                  ctypes.byref(opt) if opt is not None else None,
+                                  out.ctypes.data if out.size else None))
+    return out
+
+
+def knn_classify(cost: Sequence[int], train, train_labels, test, K: int, k: int = 1
+                 ) -> np.ndarray:
+    """Label of each test graph by majority among its k nearest training graphs under the
+    K-Best GED (ties: the smaller label); one GED matrix batch computes every distance."""
+    graphs = list(train) + list(test)
+    rows = np.arange(len(train), len(graphs))
+    cols = np.arange(len(train))
+    with FastGED(cost) as g:
+        d = fastged_cross(g.h, graphs, rows, cols, K)
+    lab = np.asarray(train_labels)
+    out = np.zeros(len(test), dtype=lab.dtype)
+    for t in range(len(test)):
+        near = np.argsort(d[t], kind="stable")[:k]
+        vals, cnt = np.unique(lab[near], return_counts=True)
+        out[t] = vals[np.argmax(cnt)]
+    return out

@@ -16,18 +16,18 @@ def gpu_run(w, K=None, **opts):
         return g.run(w, K, **opts)
 
 
-def oracle_run(w, idx, K=None, variant=0):
-    return O.kbest_workload(w, idx, K=K, variant=variant, threads=THREADS)
+def oracle_run(w, idx, K=None, variant=0, order=0):
+    return O.kbest_workload(w, idx, K=K, variant=variant, threads=THREADS, order=order)
 
 
-def assert_parity(w, gpu, idx=None, K=None, variant=0):
+def assert_parity(w, gpu, idx=None, K=None, variant=0, order=0):
     """Bit-exact cost, vertex map and evaluation count on the pairs idx (all by default)."""
     cost, maps, nev = gpu
     mm = F.marshal(w)
     if idx is None:
         idx = range(w.n_pairs)
     idx = list(idx)
-    ref = oracle_run(w, idx, K=K, variant=variant)
+    ref = oracle_run(w, idx, K=K, variant=variant, order=order)
     bad = []
     for p, (rc, rm, rn) in zip(idx, ref):
         gm = maps[mm.map_off[p]:mm.map_off[p + 1]]

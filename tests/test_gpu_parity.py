@@ -92,6 +92,37 @@ def test_packed_slot_field_at_its_width(n2, kmax):
         assert_parity(w, gpu_run(w, K=K), K=K)
 
 
+@pytest.mark.parametrize("cfg", ["config1", "config2", "config3"])
+def test_degree_vertex_order(cfg):
+    """FASTGED_ORDER_DEGREE branches the source vertices by descending degree (ties by
+    index) and returns maps in the original ids; the oracle runs Algorithm 1 on the same
+    relabelled source graph."""
+    w = {"config1": lambda: W.config1(200), "config2": lambda: W.config2(160),
+         "config3": lambda: W.subset(W.config3(6), range(6))}[cfg]()
+    gpu = gpu_run(w, vertex_order=F.FASTGED_ORDER_DEGREE)
+    assert_parity(w, gpu, order=1)
+    # a plan returns the same maps (the permutation is undone when reading results)
+    mm = F.marshal(w)
+    with F.FastGED(w.cost) as g:
+        plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options(vertex_order=1))
+        F.fastged_plan_run(plan)
+        c, m, n = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
+                   np.zeros(mm.n_pairs, np.int64))
+        F.fastged_plan_read(plan, c, m, n)
+        F.fastged_plan_destroy(plan)
+    for x, y in zip((c, m, n), gpu):
+        assert np.array_equal(x, y)
+
+
+def test_setting2_costs():
+    """The paper's cost setting 2 (expensive insertions and deletions) on molecule-like and
+    dense pairs, both branching orders."""
+    for w in (W.config2(150), W.subset(W.config3(8), range(8))):
+        w.cost = W.SETTING2_COSTS
+        assert_parity(w, gpu_run(w))
+        assert_parity(w, gpu_run(w, vertex_order=1), order=1)
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_block_sizes(bt):
     w = W.config2(150)

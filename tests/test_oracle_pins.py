@@ -224,3 +224,56 @@ def test_kbest_leaves_sorted_and_distinct():
             ins = [u for u in range(g2.n) if u not in set(mp[s].tolist())]
             e_ins = sum(1 for a, b in g2.edges if a in ins or b in ins)
             assert O.full_cost(g1, g2, w.cost, mp[s]) == ped[s] + len(ins) * w.cost[2] + e_ins * w.cost[5]
+
+
+# --------------------------------------------------------------------------------------
+# optional branching order of the source vertices (descending degree; an extension)
+# --------------------------------------------------------------------------------------
+
+def test_degree_order_of_a_known_graph():
+    # path 0-1-2 plus a star around 3: degrees 1, 2, 1, 3, 1, 1, 1
+    g = W.Graph(7, np.arange(7, dtype=np.int32),
+                np.array([[0, 1], [1, 2], [3, 4], [3, 5], [3, 6]], dtype=np.int32))
+    assert O.degree_order(g) == [3, 1, 0, 2, 4, 5, 6]
+    r = O.relabel(g, O.degree_order(g))
+    assert list(r.vlabel) == [3, 1, 0, 2, 4, 5, 6]
+    assert sorted(map(tuple, np.sort(r.edges, axis=1).tolist())) == [(0, 4), (0, 5), (0, 6), (1, 2), (1, 3)]
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_degree_ordered_kbest_exhaustive_is_exact(seed):
+    """In the exhaustive limit the branching order cannot matter: the ordered search reaches
+    the exact GED, its map (in the original ids) costs exactly what it reports, and the
+    number of evaluations is the exhaustive count."""
+    g1, g2 = _rand_pair(seed + 100, 0, 6, 0.5, 3, ne=3 if seed % 2 else 0)
+    c = _rand_cost(seed) if seed % 3 else W.SETTING2_COSTS
+    Kx = max(_level_width(i, g2.n) for i in range(g1.n + 1))
+    cost, mp, nev = O.kbest(g1, g2, c, Kx, order=1)
+    assert cost == O.brute_ged(g1, g2, c)[0]
+    assert O.full_cost(g1, g2, c, mp) == cost
+    assert nev == _exhaustive_evals(g1.n, g2.n)
+
+
+def test_degree_order_equals_index_order_when_already_sorted():
+    # a star centred at 0 followed by a path: index order is already descending degree
+    g1 = W.Graph(6, np.array([1, 2, 1, 0, 2, 1], dtype=np.int32),
+                 np.array([[0, 1], [0, 2], [0, 3], [0, 4], [4, 5]], dtype=np.int32))
+    assert O.degree_order(g1) == [0, 4, 1, 2, 3, 5]
+    g1 = O.relabel(g1, O.degree_order(g1))
+    assert O.degree_order(g1) == list(range(6))
+    g2 = W.erdos_renyi(W.Stream(5, 5), 7, 0.4, 3)
+    for K in (1, 3, 10):
+        a = O.kbest(g1, g2, W.SETTING1_COSTS, K, order=0)
+        b = O.kbest(g1, g2, W.SETTING1_COSTS, K, order=1)
+        assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1])
+
+
+def test_degree_ordered_kbest_on_config1_is_a_valid_path():
+    w = W.config1(40)
+    for p in range(w.n_pairs):
+        g1, g2 = w.graphs[2 * p], w.graphs[2 * p + 1]
+        cost, mp, _ = O.kbest(g1, g2, w.cost, w.K, order=1)
+        img = mp[mp >= 0]
+        assert len(np.unique(img)) == len(img) and np.all(mp < g2.n)
+        assert O.full_cost(g1, g2, w.cost, mp) == cost
+        assert cost >= O.brute_ged(g1, g2, w.cost)[0]
