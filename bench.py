@@ -46,9 +46,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pairs", type=int, default=0, help="0 = the workload's full size")
-    ap.add_argument("--workload", choices=["molecule", "dense", "large"], default="molecule",
+    ap.add_argument("--workload", choices=["molecule", "dense", "large", "widebeam"],
+                    default="molecule",
                     help="molecule: the 20,000-pair batch the metric is quoted on (default); "
-                         "dense / large: the 4,096-pair dense ER and 64-pair BA batches")
+                         "dense / large: the 4,096-pair dense ER and 64-pair BA batches; "
+                         "widebeam: 16 molecule-sized pairs at K = 100,000")
     ap.add_argument("--block", type=int, default=0,
                     help="threads per team for every size class (0 = autotuned)")
     ap.add_argument("--plain-sample", type=int, default=2000)
@@ -74,6 +76,8 @@ WORKLOADS = {
               "dense ER batch: 4,096 pairs, 50-200 vertices, density 0.05-0.5, K=256, unit costs"),
     "large": ("config4", 64, 4,
               "large sparse BA batch: 64 pairs, 500-1,000 vertices, K=1024, unit costs"),
+    "widebeam": ("config_wide_beam", 16, 6,
+                 "wide-beam batch: 16 pairs, 18-22 vertices, K=100,000, setting-1 costs"),
 }
 _ARGS = None
 

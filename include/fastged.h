@@ -56,7 +56,7 @@ extern "C" {
 
 /* limits of this build */
 #define FASTGED_MAX_N      1024      /* vertices per graph                                  */
-#define FASTGED_MAX_K      65536     /* beam width                                          */
+#define FASTGED_MAX_K      1048576   /* beam width (2^20)                                   */
 #define FASTGED_MAX_ELABEL 255       /* edge labels are 0..255                              */
 
 /* Cost model (Sec. 2.4; the six explicit costs of Sec. 5). All entries must be >= 0.

@@ -59,6 +59,10 @@ struct Layout {
     int64_t smem_bytes;        // dynamic shared memory per CTA
     int64_t slice_bytes;       // global scratch bytes per team (CTA or cluster)
     int64_t team_off;          // cluster teams: offset of the team scalars in the slice
+    // cluster teams: per-CTA tables that did not fit shared memory live in a block of the
+    // slice per CTA (at cta_off + cluster rank * cta_bytes; their off[] is inside the block)
+    uint32_t cta_mask;
+    int64_t cta_off, cta_bytes;
 };
 
 struct KParams {

@@ -244,7 +244,7 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     // packed classes keep the successor ids inside the PED entries
     const bool packed = cp.pk && cp.cluster == 1;
     L.pk = packed ? 1 : 0;
-    sz[RG_CSLOT] = packed ? 0 : ncand * 2;
+    sz[RG_CSLOT] = packed ? 0 : ncand * 4;
     sz[RG_CJ] = packed ? 0 : ncand * msz;
     sz[RG_CAND] = ncand * 4;
     sz[RG_MAP0] = km * L.mrow;
@@ -268,8 +268,9 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
         return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR ||
                r == RG_P || r == RG_PL || r == RG_SBASE || r == RG_IMGL || r == RG_CROW;
     };
-    size_t s_used = 0, g_used = 0;
+    size_t s_used = 0, g_used = 0, c_used = 0;
     L.smem_mask = 0;
+    L.cta_mask = 0;
     for (int k = 0; k < RG_COUNT; ++k) {
         const int r = cp.cluster > 1 ? prio_cl[k] : prio[k];
         const size_t a = align_up(sz[r], 16);
@@ -277,13 +278,24 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
             L.off[r] = (int64_t)s_used;
             L.smem_mask |= 1u << r;
             s_used += a;
+        } else if (cp.cluster > 1 && cta_local(r)) {
+            L.off[r] = (int64_t)c_used;   // one copy per CTA of the cluster
+            L.cta_mask |= 1u << r;
+            c_used += a;
         } else {
             L.off[r] = (int64_t)g_used;
             g_used += a;
         }
     }
     L.team_off = (int64_t)align_up(g_used, 256);
-    if (cp.cluster > 1) g_used = (size_t)L.team_off + team_shared_cluster_bytes();
+    L.cta_off = 0;
+    L.cta_bytes = 0;
+    if (cp.cluster > 1) {
+        g_used = (size_t)L.team_off + team_shared_cluster_bytes();
+        L.cta_off = (int64_t)align_up(g_used, 256);
+        L.cta_bytes = (int64_t)align_up(c_used, 256);
+        g_used = (size_t)L.cta_off + (size_t)cp.cluster * (size_t)L.cta_bytes;
+    }
     L.smem_bytes = (int64_t)s_used;
     L.slice_bytes = (int64_t)align_up(g_used, 256);
 }
@@ -385,6 +397,15 @@ extern "C" void fastged_autotune_clear(void)
     g_tune_loaded = true;
 }
 
+// A class whose pairs are fewer than the SMs may give each pair a cluster of CTAs: classes of
+// large graphs (four or more words), and two-word classes whose beam holds at least 2^16
+// successors per level.
+static bool cluster_eligible(const ClassPlan &cp, int npairs, int sm_count)
+{
+    if (!kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) || npairs >= sm_count) return false;
+    return cp.W >= 4 || (int64_t)cp.kmax * (cp.n2max + 1) >= 65536;
+}
+
 // Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
 // Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
 // CTAs per pair.
@@ -398,7 +419,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     const bool tuned = forced_block == 0 &&
                        tune_lookup(class_key(cp, B, npairs, h->sm_count), &tc);
     if (tuned) forced_block = tc.block;
-    if (kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) && npairs < h->sm_count) {
+    if (cluster_eligible(cp, npairs, h->sm_count)) {
         const char *env = getenv("FASTGED_CLUSTER");
         int cl = env ? atoi(env) : (tuned ? tc.cluster : 8);
         if (cl == 1 || cl == 2 || cl == 4 || cl == 8 || cl == 16) {
@@ -406,13 +427,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
         }
     }
     if (cp.cluster > 1) {
-        const int block = forced_block ? forced_block : 512;
-        plan_layout(cp, B, block, max_dyn);
-        const uint32_t need = (1u << RG_SBASE) | (1u << RG_P) | (1u << RG_PL) | (1u << RG_IMGL) |
-                              (1u << RG_CROW);
-        if ((cp.lay.smem_mask & need) != need) cp.cluster = 1;   // too large: one CTA per pair
-    }
-    if (cp.cluster > 1) {
+        plan_layout(cp, B, forced_block ? forced_block : 512, max_dyn);
         const int block = cp.block = forced_block ? forced_block : 512;
         int nclu = 0;
         cudaError_t e = kbest_cluster_occupancy(cp.W, label_instance(B), block,
@@ -672,6 +687,20 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     }
     if ((int)b.classes.size() > kMaxClasses)
         return set_error(FASTGED_ERR_INVALID_ARG, "too many size classes");
+    // very wide beams: fewer resident teams, so that their global scratch stays within half
+    // of the free device memory (each team still solves its pairs one after another)
+    {
+        size_t fr = 0, tot = 0, need = 0;
+        for (const auto &cp : b.classes)
+            need += (size_t)cp.lay.slice_bytes * (size_t)(cp.grid / cp.cluster);
+        if (need > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && need > fr / 2) {
+            const double f = (double)(fr / 2) / (double)need;
+            for (auto &cp : b.classes) {
+                const int teams = std::max(1, (int)((double)(cp.grid / cp.cluster) * f));
+                cp.grid = teams * cp.cluster;
+            }
+        }
+    }
 
     // staging layout (one pinned buffer, one copy)
     size_t o = 0;
@@ -970,7 +999,7 @@ static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_
             if (it != g_tune.end()) continue;
         }
         std::vector<TuneChoice> cands;
-        if (kbest_has_cluster_variant(cp.W, cp.wide, cp.w32) && npairs < h->sm_count) {
+        if (cluster_eligible(cp, npairs, h->sm_count)) {
             for (int cl : {1, 4, 8, 16}) {
                 TuneChoice c;
                 c.block = cl == 1 ? 256 : 512;

@@ -122,7 +122,7 @@ struct Regions {
     int32_t *hist, *alpha2, *crow, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
     int32_t *ped0, *ped1;
     Word *a2t, *l2t, *img0, *img1, *P, *PL, *imgl;
-    uint16_t *cslot;
+    uint32_t *cslot;
     uint8_t *map0, *map1, *cj;
 };
 
@@ -269,16 +269,54 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     keep_before += min(q, eq_before);
     compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before, pk);
     tm.sync();
-    // rank by (PED, enumeration order); klist is in enumeration order
-    for (int a = tid; a < newL; a += T) {
-        const int pa = kped[a];
-        int rank = 0;
-        for (int b = 0; b < newL; ++b) {
-            const int pb = kped[b];
-            rank += (pb < pa) || (pb == pa && b < a);
+    // order by (PED, enumeration order); klist is in enumeration order and its entries are
+    // increasing, so (kped, klist) is that key
+    if (newL <= 2048) {
+        for (int a = tid; a < newL; a += T) {
+            const int pa = kped[a];
+            int rank = 0;
+            for (int b = 0; b < newL; ++b) {
+                const int pb = kped[b];
+                rank += (pb < pa) || (pb == pa && b < a);
+            }
+            sel[rank] = klist[a];   // successor index; the caller turns it into (slot, j)
+            selped[rank] = pa;
         }
-        sel[rank] = klist[a];   // successor index; the caller turns it into (slot, j)
-        selped[rank] = pa;
+        return;
+    }
+    // large beams: bitonic sort of (kped, klist) in place. Every comparator puts the smaller
+    // key at the lower index (each merge starts with a reversed-partner stage), so entries
+    // past newL act as +infinity padding up to the next power of two and are never touched.
+    int N = 1;
+    while (N < newL) N <<= 1;
+    auto cmpswap = [&](int i, int j) {
+        if (j >= newL) return;
+        const int pi = kped[i], pj = kped[j];
+        const int li = klist[i], lj = klist[j];
+        if (pj < pi || (pj == pi && lj < li)) {
+            kped[i] = pj; kped[j] = pi;
+            klist[i] = lj; klist[j] = li;
+        }
+    };
+    for (int size = 2; size <= N; size <<= 1) {
+        const int half = size >> 1;
+        for (int t = tid; t < N / 2; t += T) {
+            const int blk = t / half, off = t - blk * half;
+            cmpswap(blk * size + off, blk * size + size - 1 - off);
+        }
+        tm.sync();
+        for (int stride = half >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < N / 2; t += T) {
+                const int blk = t / stride, off = t - blk * stride;
+                const int i = blk * 2 * stride + off;
+                cmpswap(i, i + stride);
+            }
+            tm.sync();
+        }
+    }
+    for (int a = tid; a < newL; a += T) {
+        sel[a] = klist[a];
+        selped[a] = kped[a];
     }
 }
 
@@ -539,7 +577,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                             if (pk) {
                                 ck[idx] = ((uint32_t)st_ << jbits) | (uint32_t)j;
                             } else {
-                                R.cslot[idx] = (uint16_t)st_;
+                                R.cslot[idx] = (uint32_t)st_;
                                 cjv[idx] = (MapT)j;
                             }
                         }
@@ -549,7 +587,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         if (pk) {
                             ck[o0 + pos] = ((uint32_t)st_ << jbits) | (uint32_t)n2;
                         } else {
-                            R.cslot[o0 + pos] = (uint16_t)st_;
+                            R.cslot[o0 + pos] = (uint32_t)st_;
                             cjv[o0 + pos] = (MapT)n2;
                         }
                     }
@@ -945,7 +983,7 @@ __device__ __forceinline__ Regions<Word> make_regions(F base)
     R.img1 = (Word *)base(RG_IMG1);
     R.P = (Word *)base(RG_P);
     R.PL = (Word *)base(RG_PL);
-    R.cslot = (uint16_t *)base(RG_CSLOT);
+    R.cslot = (uint32_t *)base(RG_CSLOT);
     R.cj = base(RG_CJ);
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
@@ -985,8 +1023,10 @@ __global__ void __launch_bounds__(512, 1) kbest_cluster_kernel(const KParams p)
     extern __shared__ __align__(16) uint8_t smem[];
     const unsigned crank = cluster_rank(), csize = cluster_size();
     uint8_t *gs = p.gscratch + (int64_t)(blockIdx.x / csize) * p.lay.slice_bytes;
+    uint8_t *gc = gs + p.lay.cta_off + (int64_t)crank * p.lay.cta_bytes;   // this CTA's block
     auto base = [&](int r) -> uint8_t * {
-        return ((p.lay.smem_mask >> r) & 1u ? smem : gs) + p.lay.off[r];
+        if ((p.lay.smem_mask >> r) & 1u) return smem + p.lay.off[r];
+        return ((p.lay.cta_mask >> r) & 1u ? gc : gs) + p.lay.off[r];
     };
     const Regions<Word> R = make_regions<Word>(base);
     TeamSharedCl &S = *(TeamSharedCl *)(gs + p.lay.team_off);
@@ -1132,6 +1172,7 @@ static cudaError_t cluster_occupancy_one(int block, size_t smem, int cluster, in
 #define FASTGED_CLUSTER_DISPATCH(W_, CALL)                                               \
     do {                                                                                 \
         switch (W_) {                                                                    \
+        case 2: return CALL(2, uint8_t, uint64_t);                                       \
         case 4: return CALL(4, uint16_t, uint64_t);                                      \
         case 8: return CALL(8, uint16_t, uint64_t);                                      \
         case 16: return CALL(16, uint16_t, uint64_t);                                    \

@@ -96,7 +96,10 @@ cudaError_t launch_kbest_cluster_bk(int W, const KParams &p, int grid, int block
 template <int BK>
 cudaError_t kbest_cluster_occupancy_bk(int W, int block, size_t smem, int cluster, int *out);
 
-bool kbest_has_cluster_variant(int W, bool wide, bool w32) { return !w32 && wide && W >= 4; }
+bool kbest_has_cluster_variant(int W, bool wide, bool w32)
+{
+    return !w32 && ((wide && W >= 4) || (W == 2 && !wide));
+}
 
 cudaError_t launch_kbest_cluster(int W, int bk, const KParams &p, int grid, int block,
                                  size_t smem, int cluster, cudaStream_t st)

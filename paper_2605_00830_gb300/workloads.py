@@ -319,6 +319,18 @@ def config4(n_pairs: int = 64, seed: int = 4, n_range=(500, 1000)) -> Workload:
     return Workload("ba_m3_n500-1000_K1024", graphs, pairs, UNIT_COSTS, 1024)
 
 
+def config_wide_beam(n_pairs: int = 16, seed: int = 6, K: int = 100000) -> Workload:
+    """Wide-beam regime (the paper's K sweep up to 10^5-10^6 on ~20-vertex graphs):
+    molecule-like graphs with 18-22 vertices, the paper's setting-1 costs, K = 100,000."""
+    graphs = []
+    for p in range(n_pairs):
+        for role in (0, 1):
+            st = Stream(seed, 6, p, role)
+            graphs.append(molecule_like(st, int(st.randint(18, 22, 1)[0])))
+    pairs = np.arange(2 * n_pairs, dtype=np.int32).reshape(-1, 2)
+    return Workload(f"molecule_n18-22_K{K}", graphs, pairs, SETTING1_COSTS, K)
+
+
 def config5(duration_s: float = 60.0, rate: float = 5000.0, seed: int = 5,
             max_requests: Optional[int] = None) -> Workload:
     """Serving stream: Poisson arrivals at `rate` req/s for `duration_s`; 70 % molecule-like

@@ -123,6 +123,35 @@ def test_setting2_costs():
         assert_parity(w, gpu_run(w, vertex_order=1), order=1)
 
 
+@pytest.mark.parametrize("case", ["k5000", "k100000", "kmax"])
+def test_huge_k(case):
+    """The wide-beam regime: K = 5000 on molecule-sized pairs, K = 100,000 on ~14-vertex
+    graphs and K = 2^20 on 8-9 vertex graphs, with the default histogram window and with a
+    window of 2 (every level then orders its kept beam with the exact selection's sort)."""
+    if case == "k5000":
+        w = W.config2(6, seed=11)
+        K = 5000
+    elif case == "k100000":
+        st = W.Stream(12, 1)
+        pairs = [(W.erdos_renyi(st, 13, 0.3, 4), W.erdos_renyi(st, 14, 0.3, 4)) for _ in range(2)]
+        w = single(pairs, W.UNIT_COSTS, 100000)
+        K = 100000
+    else:
+        st = W.Stream(13, 1)
+        w = single([(W.erdos_renyi(st, 8, 0.4, 3), W.erdos_renyi(st, 9, 0.4, 3))],
+                   W.SETTING1_COSTS, 1 << 20)
+        K = 1 << 20
+    ref = None
+    for hw in (0, 2):
+        gpu = gpu_run(w, K=K, hist_window=hw)
+        if ref is None:
+            assert_parity(w, gpu, K=K)
+            ref = gpu
+        else:
+            for x, y in zip(gpu, ref):
+                assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_block_sizes(bt):
     w = W.config2(150)
@@ -265,7 +294,7 @@ def test_invalid_inputs():
                 fg.run(w)
             assert ei.value.code == F.FASTGED_ERR_INVALID_ARG
         w = single([(g, h)], W.UNIT_COSTS, 4)
-        for K in (0, -3, 70000):
+        for K in (0, -3, (1 << 20) + 1):
             with pytest.raises(F.FastGEDError):
                 fg.run(w, K=K)
         # an invalid call leaves the handle usable

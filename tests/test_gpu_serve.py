@@ -95,7 +95,7 @@ def test_invalid_submissions_and_stop():
     mm = F.marshal(w)
     srv = F.Server(w.cost)
     assert srv.submit(mm, 0, 1, 0, 1) == F.FASTGED_ERR_INVALID_ARG
-    assert srv.submit(mm, 0, 1, 70000, 1) == F.FASTGED_ERR_INVALID_ARG
+    assert srv.submit(mm, 0, 1, (1 << 20) + 1, 1) == F.FASTGED_ERR_INVALID_ARG
     for p in range(4):
         assert srv.submit(mm, w.pairs[p][0], w.pairs[p][1], 100, p) == F.FASTGED_OK
     srv.stop()                                   # drains every queued query
