@@ -263,12 +263,12 @@ def test_plan_replay_matches_batch_and_is_repeatable():
 
 def test_config2_full_batch_bench_configuration():
     """The full 20,000-pair molecule-like batch in the launch configuration the benchmark
-    times (plan + CUDA-graph replay): a seeded sample of pairs is checked bit-exactly
-    against the oracle, and every pair against the edit-path properties."""
+    times (autotuned plan + CUDA-graph replay): a seeded sample of pairs is checked
+    bit-exactly against the oracle, and every pair against the edit-path properties."""
     w = W.config2()
     mm = F.marshal(w)
     with F.FastGED(w.cost) as g:
-        plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options())
+        plan = F.fastged_plan_create(g.h, mm, w.K, F.make_options(autotune=1))
         F.fastged_plan_run(plan)
         c, m, n = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
                    np.zeros(mm.n_pairs, np.int64))
