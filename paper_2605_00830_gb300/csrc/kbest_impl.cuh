@@ -675,6 +675,63 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         for (int w = 0; w < NW; ++w) pa = min(pa, S.wmin[w]);
         {
             int hreg = 0;
+            if (kw >= 1024 && kw <= 65000) {
+                // many candidates: each lane counts its own in 4-bit fields (two 64-bit words
+                // for 32 buckets), widened every 12 chunks into 16-bit fields, then a five-
+                // round shuffle reduce-scatter leaves bucket b's warp total in lane b (16-bit
+                // fields hold it: the warp has at most 65,000 candidates plus padding)
+                unsigned long long c0 = 0ull, c1 = 0ull, acc[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] = 0ull;
+                int pending = 0;
+                for (int kb = 0; kb < kw; kb += 128) {
+                    int d4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = kb + 32 * u + lane;
+                        d4[u] = k < kw ? min(ped_at(base + k) - pa, hwin - 1) : hwin - 1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned long long inc = 1ull << (4 * (d4[u] & 15));
+                        if (d4[u] < 16) c0 += inc; else c1 += inc;
+                    }
+                    pending += 4;
+                    if (pending >= 12 || kb + 128 >= kw) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            acc[m] += (c0 >> (4 * m)) & 0x000F000F000F000Full;
+                            acc[4 + m] += (c1 >> (4 * m)) & 0x000F000F000F000Full;
+                        }
+                        c0 = c1 = 0ull;
+                        pending = 0;
+                    }
+                }
+                const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+                const bool b1 = (lane >> 1) & 1, b0 = lane & 1;
+                unsigned q[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const unsigned long long send = b4 ? acc[m] : acc[4 + m];
+                    const unsigned long long keep = b4 ? acc[4 + m] : acc[m];
+                    const unsigned long long r = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    const unsigned lo = (unsigned)r, hi = (unsigned)(r >> 32);
+                    q[m] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+                }
+                unsigned t[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const unsigned lo = q[m] & 0xffffu, hi = q[m] >> 16;
+                    t[m] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+                }
+                unsigned u2[2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+                    u2[m] = (b1 ? t[2 + m] : t[m]) + __shfl_xor_sync(0xffffffffu, b1 ? t[m] : t[2 + m], 2);
+                hreg = (int)((b0 ? u2[1] : u2[0]) + __shfl_xor_sync(0xffffffffu, b0 ? u2[0] : u2[1], 1));
+            } else
+            // few candidates: five bit ballots per chunk, lane b counts the lanes whose
+            // bucket is b
             for (int kb = 0; kb < kw; kb += 128) {
                 int d4[4];
 #pragma unroll
@@ -877,7 +934,36 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     }
                     pedn[r] = R.selped[r];
                 }
+            } else if (!CL) {
+                // long maps, one-CTA team: every thread takes (child, 16-byte vector) items
+                // (the last vector of a child also carries its new entry i) and one more item
+                // per child writes Img, the PED and entry i when it starts a new vector
+                const int nb = i * (int)sizeof(MapT);
+                const int per = nvec + 1;
+                const int items = newL * per;
+                for (int t = tid; t < items; t += T) {
+                    const int r = t / per, v = t - r * per;
+                    const int sv = R.sel[r];
+                    const int s = sv >> kSelShift, j = sv & ((1 << kSelShift) - 1);
+                    const MapT val = (j < n2) ? (MapT)j : DEL;
+                    uint8_t *dst = mapn + (int64_t)r * mrow;
+                    if (v < nvec) {
+                        uint4 x = ((const uint4 *)(mapc + (int64_t)s * mrow))[v];
+                        if (v == nvec - 1 && nb < 16 * nvec)
+                            ((MapT *)&x)[(nb - 16 * v) / (int)sizeof(MapT)] = val;
+                        ((uint4 *)dst)[v] = x;
+                    } else {
+                        if (nb == 16 * nvec) ((MapT *)dst)[i] = val;
+                        for (int w = 0; w < W; ++w) {
+                            Word x = imgc[(int64_t)s * W + w];
+                            if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
+                            imgn[(int64_t)r * W + w] = x;
+                        }
+                        pedn[r] = R.selped[r];
+                    }
+                }
             } else {
+                // cluster teams: a warp per child
                 for (int r = warp; r < newL; r += NW) {
                     const int v = R.sel[r];
                     const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);

@@ -50,6 +50,9 @@ def test_exact_selection_fallback(hw):
     assert_parity(w, gpu_run(w, hist_window=hw))
     w1 = W.config1(60)
     assert_parity(w1, gpu_run(w1, hist_window=hw))
+    # dense pairs: warps hold thousands of candidates, so the histogram is counted per lane
+    w3 = W.subset(W.config3(4), range(4))
+    assert_parity(w3, gpu_run(w3, hist_window=hw))
 
 
 def test_large_costs():
