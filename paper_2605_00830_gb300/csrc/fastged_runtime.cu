@@ -13,12 +13,18 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/fastged.h"
@@ -125,6 +131,115 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // kernel instance for B edge-label planes: 0, exactly 2, or up to 8
 int fastged::label_instance(int B) { return B == 0 ? 0 : (B == 2 ? 2 : 8); }
+
+// ------------------------------------------------------------------------------------
+// host thread pool for the batch flattening (validation and staging copies)
+// ------------------------------------------------------------------------------------
+// A process-wide pool of worker threads, created on first use. parallel_for(n, grain, f)
+// runs f(lo, hi) over [0, n) in chunks of `grain` on the workers and the calling thread and
+// returns when every chunk is done; a call made while another one is running (from another
+// host thread) runs serially in the caller instead.
+class HostPool {
+public:
+    static HostPool &get()
+    {
+        static HostPool pool;
+        return pool;
+    }
+
+    void parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)> &f)
+    {
+        grain = std::max<int64_t>(grain, 1);
+        if (n <= grain || workers_.empty() || !busy_.try_lock()) {
+            for (int64_t lo = 0; lo < n; lo += grain) f(lo, std::min(n, lo + grain));
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            job_ = &f;
+            n_ = n;
+            grain_ = grain;
+            next_.store(0);
+            ++gen_;
+        }
+        cv_.notify_all();
+        run(&f, n, grain);
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            done_cv_.wait(lk, [&] { return active_ == 0; });
+            job_ = nullptr;
+        }
+        busy_.unlock();
+    }
+
+private:
+    HostPool()
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nw = (int)std::min(15u, hw > 1 ? hw - 1 : 0u);
+        for (int k = 0; k < nw; ++k) workers_.emplace_back([this] { loop(); });
+    }
+    ~HostPool()
+    {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            quit_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : workers_) t.join();
+    }
+    void run(const std::function<void(int64_t, int64_t)> *f, int64_t n, int64_t grain)
+    {
+        for (;;) {
+            const int64_t lo = next_.fetch_add(grain);
+            if (lo >= n) break;
+            (*f)(lo, std::min(n, lo + grain));
+        }
+    }
+    void loop()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&] { return quit_ || (gen_ != seen && job_ != nullptr); });
+            if (quit_) return;
+            seen = gen_;
+            const auto *f = job_;
+            const int64_t n = n_, grain = grain_;
+            ++active_;
+            lk.unlock();
+            run(f, n, grain);
+            lk.lock();
+            if (--active_ == 0) done_cv_.notify_all();
+        }
+    }
+
+    std::vector<std::thread> workers_;
+    std::mutex mu_, busy_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int64_t, int64_t)> *job_ = nullptr;
+    int64_t n_ = 0, grain_ = 1;
+    std::atomic<int64_t> next_{0};
+    uint64_t gen_ = 0;
+    int active_ = 0;
+    bool quit_ = false;
+};
+
+// The error of the lowest index among those reported from parallel chunks.
+struct FirstError {
+    std::mutex mu;
+    int64_t idx = INT64_MAX;
+    std::string msg;
+    void put(int64_t i, std::string m)
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (i < idx) {
+            idx = i;
+            msg = std::move(m);
+        }
+    }
+    int report() const { return set_error(FASTGED_ERR_INVALID_ARG, msg); }
+};
 
 static int words_class(int n)
 {
@@ -561,37 +676,51 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     b.opt = opt;
     b.has_kpp = opt.k_per_pair != nullptr;
     b.meta.resize(ng);
-    int64_t nv = 0, ne = 0, adjw = 0;
+    HostPool &pool = HostPool::get();
+    FirstError ferr;
+    // graphs: validation, words per row, edge-label range (chunks of graphs in parallel)
+    std::mutex red_mu;
     int maxlab = 0;
     bool labelled = false;
+    pool.parallel_for(ng, 2048, [&](int64_t lo, int64_t hi) {
+        int ml = 0;
+        bool lab = false;
+        for (int g = (int)lo; g < (int)hi; ++g) {
+            const fastged_graph &G = pl->graphs[g];
+            auto where = [g] { return "graph " + std::to_string(g); };
+            if (G.n < 0 || G.n > FASTGED_MAX_N) { ferr.put(g, where() + ": n out of range"); break; }
+            if (G.m < 0 || (int64_t)G.m > (int64_t)G.n * (G.n - 1) / 2) { ferr.put(g, where() + ": m out of range"); break; }
+            if ((G.n > 0 && !G.vlabel) || (G.m > 0 && !G.edges)) { ferr.put(g, where() + ": null array"); break; }
+            GraphMeta &M = b.meta[g];
+            M.n = G.n;
+            M.m = G.m;
+            M.W = std::max(1, (G.n + 63) / 64);
+            M.pad = 0;
+            bool bad = false;
+            if (G.elabel && G.m > 0) {
+                lab = true;
+                for (int k = 0; k < G.m; ++k) {
+                    const int l = G.elabel[k];
+                    if (l < 0 || l > FASTGED_MAX_ELABEL) { bad = true; break; }
+                    ml = std::max(ml, l);
+                }
+            }
+            if (bad) { ferr.put(g, where() + ": edge label out of range"); break; }
+        }
+        std::lock_guard<std::mutex> gl(red_mu);
+        maxlab = std::max(maxlab, ml);
+        labelled = labelled || lab;
+    });
+    if (ferr.idx != INT64_MAX) return ferr.report();
+    int64_t nv = 0, ne = 0, adjw = 0;
     for (int g = 0; g < ng; ++g) {
-        const fastged_graph &G = pl->graphs[g];
-        if (G.n < 0 || G.n > FASTGED_MAX_N)
-            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": n out of range");
-        if (G.m < 0 || (int64_t)G.m > (int64_t)G.n * (G.n - 1) / 2)
-            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": m out of range");
-        if ((G.n > 0 && !G.vlabel) || (G.m > 0 && !G.edges))
-            return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": null array");
         GraphMeta &M = b.meta[g];
-        M.n = G.n;
-        M.m = G.m;
-        M.W = std::max(1, (G.n + 63) / 64);
-        M.pad = 0;
         M.lab_off = nv;
         M.edge_off = ne;
         M.adj_off = adjw;
-        nv += G.n;
-        ne += G.m;
-        adjw += (int64_t)G.n * M.W;
-        if (G.elabel && G.m > 0) {
-            labelled = true;
-            for (int k = 0; k < G.m; ++k) {
-                const int l = G.elabel[k];
-                if (l < 0 || l > FASTGED_MAX_ELABEL)
-                    return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": edge label out of range");
-                maxlab = std::max(maxlab, l);
-            }
-        }
+        nv += M.n;
+        ne += M.m;
+        adjw += (int64_t)M.n * M.W;
     }
     int B = 0;
     while ((1 << B) <= maxlab) ++B;   // planes needed for labels 0..maxlab
@@ -612,34 +741,44 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     int cls_of[32];
     for (int k = 0; k < 32; ++k) cls_of[k] = -1;
     b.classes.clear();
-    std::vector<int> pair_class(np);
-    for (int p = 0; p < np; ++p) {
-        const int a = pl->pairs[2 * p], d = pl->pairs[2 * p + 1];
-        if (a < 0 || a >= ng || d < 0 || d >= ng)
-            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": graph index out of range");
-        const int kp = kpp ? kpp[p] : K;
-        if (kp < 1 || kp > K)
-            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": per-pair K out of range");
-        const GraphMeta &g1 = b.meta[a], &g2 = b.meta[d];
-        const long long bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
-                                (long long)g2.n * c.v_ins +
-                                (long long)g1.m * std::max(c.e_sub, c.e_del) +
-                                (long long)g2.m * c.e_ins;
-        if (bound >= (long long)INT32_MAX)
-            return set_error(FASTGED_ERR_INVALID_ARG, "pair " + std::to_string(p) + ": costs can overflow int32");
-        b.map_off[p] = mtot;
-        mtot += g1.n;
-        int W = words_class(g2.n);
-        // packing (PED, parent slot, j) into 32 bits needs every PED below 2^16 (PEDs never
-        // count vertex insertions, and at most the g2 edges among mapped vertices) and K
-        // within the slot field
-        const long long ped_bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
+    // pairs: validation and size class of each (chunks of pairs in parallel), then the
+    // classes in order of first appearance
+    struct PairClass { int8_t W, wide, w32, pk; };
+    std::vector<PairClass> pcls((size_t)np);
+    pool.parallel_for(np, 4096, [&](int64_t lo, int64_t hi) {
+        for (int p = (int)lo; p < (int)hi; ++p) {
+            const int a = pl->pairs[2 * p], d = pl->pairs[2 * p + 1];
+            auto where = [p] { return "pair " + std::to_string(p); };
+            if (a < 0 || a >= ng || d < 0 || d >= ng) { ferr.put(p, where() + ": graph index out of range"); break; }
+            const int kp = kpp ? kpp[p] : K;
+            if (kp < 1 || kp > K) { ferr.put(p, where() + ": per-pair K out of range"); break; }
+            const GraphMeta &g1 = b.meta[a], &g2 = b.meta[d];
+            const long long bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
+                                    (long long)g2.n * c.v_ins +
                                     (long long)g1.m * std::max(c.e_sub, c.e_del) +
                                     (long long)g2.m * c.e_ins;
-        const bool pk = packable(ped_bound, kp, g2.n);
-        if (W == 1 && !pk) W = 2;
-        const bool wide = g2.n >= 255;
-        const bool w32 = W == 1 && g2.n <= 32;
+            if (bound >= (long long)INT32_MAX) { ferr.put(p, where() + ": costs can overflow int32"); break; }
+            int W = words_class(g2.n);
+            // packing (PED, parent slot, j) into 32 bits needs every PED below 2^16 (PEDs
+            // never count vertex insertions, and at most the g2 edges among mapped vertices)
+            // and K within the slot field
+            const long long ped_bound = (long long)g1.n * std::max(c.v_sub, c.v_del) +
+                                        (long long)g1.m * std::max(c.e_sub, c.e_del) +
+                                        (long long)g2.m * c.e_ins;
+            const bool pk = packable(ped_bound, kp, g2.n);
+            if (W == 1 && !pk) W = 2;
+            pcls[p] = PairClass{(int8_t)W, (int8_t)(g2.n >= 255), (int8_t)(W == 1 && g2.n <= 32),
+                                (int8_t)pk};
+        }
+    });
+    if (ferr.idx != INT64_MAX) return ferr.report();
+    for (int p = 0; p < np; ++p) {
+        const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
+        const int kp = kpp ? kpp[p] : K;
+        b.map_off[p] = mtot;
+        mtot += g1.n;
+        const int W = pcls[p].W;
+        const bool wide = pcls[p].wide, w32 = pcls[p].w32, pk = pcls[p].pk;
         const int key =
             (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
             (pk ? 1 : 0);
@@ -658,7 +797,6 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         cp.n2max = std::max(cp.n2max, g2.n);
         cp.kmax = std::max(cp.kmax, kp);
         cp.order.push_back(p);
-        pair_class[p] = cls_of[key];
     }
     b.map_total = mtot;
     if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
@@ -670,18 +808,36 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             std::copy(ro.perm[c].begin(), ro.perm[c].end(), b.perm.begin() + b.map_off[p]);
         }
     }
-    // heaviest pairs first inside each class (longest-processing-time order)
-    for (auto &cp : b.classes) {
-        std::vector<std::pair<long long, int>> wk(cp.order.size());
-        for (size_t k = 0; k < cp.order.size(); ++k) {
-            const int p = cp.order[k];
-            const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
-            const long long kp = kpp ? kpp[p] : K;
-            wk[k] = {-(long long)g1.n * std::min<long long>(kp, 1 + (long long)g2.n * g1.n) * (g2.n + 1),
-                     p};
+    // heaviest pairs first inside each class (longest-processing-time order, which only
+    // shortens the tail: results do not depend on the order). Work estimate
+    // n1 * min(K, n1 n2 + 1) * (n2 + 1), bucketed at 1/16 of a power of two and counting-
+    // sorted (descending bucket, then pair index); classes in parallel.
+    pool.parallel_for((int64_t)b.classes.size(), 1, [&](int64_t lo, int64_t hi) {
+        constexpr int kBuckets = 64 * 16;
+        for (int64_t ci = lo; ci < hi; ++ci) {
+            ClassPlan &cp = b.classes[ci];
+            const size_t n = cp.order.size();
+            std::vector<uint16_t> bk(n);
+            std::vector<int> cnt(kBuckets + 1, 0);
+            for (size_t k = 0; k < n; ++k) {
+                const int p = cp.order[k];
+                const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
+                const long long kp = kpp ? kpp[p] : K;
+                const double wt = (double)g1.n *
+                                  (double)std::min<long long>(kp, 1 + (long long)g2.n * g1.n) *
+                                  (double)(g2.n + 1);
+                int q = wt < 1.0 ? 0 : (int)(std::log2(wt) * 16.0);
+                q = std::min(std::max(q, 0), kBuckets - 1);
+                bk[k] = (uint16_t)(kBuckets - 1 - q);   // heavier first
+                ++cnt[bk[k] + 1];
+            }
+            for (int q = 0; q < kBuckets; ++q) cnt[q + 1] += cnt[q];
+            std::vector<int32_t> out(n);
+            for (size_t k = 0; k < n; ++k) out[cnt[bk[k]]++] = cp.order[k];
+            cp.order.swap(out);
         }
-        std::sort(wk.begin(), wk.end());
-        for (size_t k = 0; k < wk.size(); ++k) cp.order[k] = wk[k].second;
+    });
+    for (auto &cp : b.classes) {
         int rc = tune_class(h, cp, B, opt.block_threads);
         if (rc) return rc;
     }
@@ -737,23 +893,30 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     int32_t *vl = (int32_t *)(S + b.off_vlab);
     int32_t *ed = (int32_t *)(S + b.off_edges);
     int32_t *el = (int32_t *)(S + b.off_elab);
-    for (int g = 0; g < ng; ++g) {
-        const fastged_graph &G = pl->graphs[g];
-        const GraphMeta &M = b.meta[g];
-        if (G.n) memcpy(vl + M.lab_off, G.vlabel, 4 * (size_t)G.n);
-        int32_t *dst = ed + 2 * M.edge_off;
-        for (int k = 0; k < G.m; ++k) {
-            const int u = G.edges[2 * k], v = G.edges[2 * k + 1];
-            if (u < 0 || v < 0 || u >= G.n || v >= G.n || u == v)
-                return set_error(FASTGED_ERR_INVALID_ARG, "graph " + std::to_string(g) + ": bad edge endpoint or self-loop");
-            dst[2 * k] = u;
-            dst[2 * k + 1] = v;
+    pool.parallel_for(ng, 1024, [&](int64_t lo, int64_t hi) {
+        for (int g = (int)lo; g < (int)hi; ++g) {
+            const fastged_graph &G = pl->graphs[g];
+            const GraphMeta &M = b.meta[g];
+            if (G.n) memcpy(vl + M.lab_off, G.vlabel, 4 * (size_t)G.n);
+            int32_t *dst = ed + 2 * M.edge_off;
+            bool bad = false;
+            for (int k = 0; k < G.m; ++k) {
+                const int u = G.edges[2 * k], v = G.edges[2 * k + 1];
+                if (u < 0 || v < 0 || u >= G.n || v >= G.n || u == v) { bad = true; break; }
+                dst[2 * k] = u;
+                dst[2 * k + 1] = v;
+            }
+            if (bad) {
+                ferr.put(g, "graph " + std::to_string(g) + ": bad edge endpoint or self-loop");
+                break;
+            }
+            if (b.labelled) {
+                if (G.elabel) memcpy(el + M.edge_off, G.elabel, 4 * (size_t)G.m);
+                else memset(el + M.edge_off, 0, 4 * (size_t)G.m);
+            }
         }
-        if (b.labelled) {
-            if (G.elabel) memcpy(el + M.edge_off, G.elabel, 4 * (size_t)G.m);
-            else memset(el + M.edge_off, 0, 4 * (size_t)G.m);
-        }
-    }
+    });
+    if (ferr.idx != INT64_MAX) return ferr.report();
     memcpy(S + b.off_pairs, pl->pairs, 8 * (size_t)np);
     {
         int32_t *ord = (int32_t *)(S + b.off_order);
