@@ -1,12 +1,16 @@
-// kbest_impl.cuh -- sm_103a kernels of the K-Best GED path (templates; instantiated per
-// edge-label plane count in kbest_b0.cu, kbest_b2.cu and kbest_b8.cu).
+// kbest_impl.cuh -- sm_103a K-Best kernels (templates; instantiated per edge-label plane
+// count in kbest_b0.cu, kbest_b2.cu and kbest_b8.cu; the S0 packing kernel and the dispatch
+// live in kbest_kernels.cu).
 //
-//   pack_kernel   S0: edge lists -> adjacency bitsets and edge-label bit-planes
-//   kbest_kernel  S1-S5 for every pair of a size class: persistent teams pull pairs from a
-//                 device work queue; per level they stage the vertex-cost row, build per-node
-//                 neighbour bitsets, score every successor with AND/XOR + popcount, select the
-//                 best K with a deterministic stable counting sort, write the kept children in
-//                 key order, and finally complete the leaves and take the argmin.
+//   kbest_kernel          S1-S5 for every pair of a size class: persistent one-CTA teams pull
+//                         pairs from a device work queue; per level they build per-node
+//                         neighbour bitsets, score every successor with AND/XOR + popcount
+//                         against the staged vertex-cost row, select the best K exactly
+//                         (a PED histogram, a stable compaction and a counting placement),
+//                         write the kept children in key order and stage the next cost row;
+//                         finally they complete the leaves and take the argmin.
+//   kbest_cluster_kernel  the same with a team of 2-16 CTAs in a thread-block cluster, for
+//                         classes with fewer pairs than SMs and large pairs or beams.
 //
 // Method: Algorithm 1 of Dabah & Herten (branching Sec. 4.1.1, evaluation Sec. 4.1.2 and
 // Algorithm 2, selection Sec. 4.2, leaf insertions Sec. 4.4). The paper's GPU design

@@ -1,24 +1,15 @@
-// kbest_kernels.cu -- sm_103a kernels of the K-Best GED path.
+// kbest_kernels.cu -- the S0 packing kernel and the host-side dispatch onto the K-Best
+// kernel instances.
 //
 //   pack_kernel   S0: edge lists -> adjacency bitsets and edge-label bit-planes
-//   kbest_kernel  S1-S5 (templates in kbest_impl.cuh) for every pair of a size class: persistent teams pull pairs from a
-//                 device work queue; per level they stage the vertex-cost row, build per-node
-//                 neighbour bitsets, score every successor with AND/XOR + popcount, select the
-//                 best K with a deterministic stable counting sort, write the kept children in
-//                 key order, and finally complete the leaves and take the argmin.
+//   launch_kbest / kbest_occupancy / launch_kbest_cluster / kbest_cluster_occupancy:
+//                 pick the instance (words per bitset, map entry width, all-shared-memory or
+//                 not, label planes) of the S1-S5 kernels in kbest_impl.cuh, which are
+//                 compiled in kbest_b0.cu, kbest_b2.cu and kbest_b8.cu.
 //
 // Method: Algorithm 1 of Dabah & Herten (branching Sec. 4.1.1, evaluation Sec. 4.1.2 and
-// Algorithm 2, selection Sec. 4.2, leaf insertions Sec. 4.4). The paper's GPU design
-// (one block per node, a lambda walk per successor, atomic top-L lists) is replaced here:
-// the implied edge cost of substituting v_i by u is computed from bitsets,
-//     P     = images of the already-substituted g1 neighbours of v_i,
-//     Img   = images of every substituted g1 vertex,
-//     A2[u] = neighbours of u in g2,
-//   inserted edges   = popc(A2[u] & Img & ~P)
-//   deleted edges    = popc(P & ~A2[u]) + (# g1 neighbours of v_i that were deleted)
-//   relabelled edges = popc(A2[u] & P & OR_b(PL_b ^ L2_b[u]))
-// and when insertion and deletion cost the same, the first two fold into one
-// popc((A2[u] & Img) ^ P) since P is a subset of Img.
+// Algorithm 2, selection Sec. 4.2, leaf insertions Sec. 4.4); kbest_impl.cuh states how the
+// implied edge costs are computed from bitsets.
 #include "kbest_impl.cuh"
 
 namespace fastged {
