@@ -155,6 +155,32 @@ def test_huge_k(case):
                 assert np.array_equal(x, y)
 
 
+def test_concurrent_batches_from_two_host_threads():
+    """Two handles used from two host threads at once (the batch flattening shares one host
+    thread pool; a call that finds it busy runs serially): results equal serial runs."""
+    import threading
+    ws = [W.config2(600, seed=21), W.subset(W.config3(12, seed=22), range(12))]
+    ref = [gpu_run(w) for w in ws]
+    out, errs = [None, None], []
+
+    def work(k):
+        try:
+            with F.FastGED(ws[k].cost) as g:
+                for _ in range(4):
+                    out[k] = g.run(ws[k])
+                    for x, y in zip(out[k], ref[k]):
+                        assert np.array_equal(x, y)
+        except Exception as e:   # surfaced in the main thread
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_block_sizes(bt):
     w = W.config2(150)

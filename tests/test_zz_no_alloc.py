@@ -46,10 +46,16 @@ def _device_batch(w, torch):
     return b, keep, mm
 
 
-@pytest.mark.parametrize("name", ["molecule", "dense"])
+@pytest.mark.parametrize("name", ["molecule", "dense", "wide_k"])
 def test_noalloc_matches_batch_ex_twice(name):
     torch = pytest.importorskip("torch")
-    w = W.config2(400) if name == "molecule" else W.config3(6)
+    if name == "molecule":
+        w = W.config2(400)
+    elif name == "dense":
+        w = W.config3(6)
+    else:   # K past the single-word packing limit: the two-word unpacked kernels
+        w = W.config1(40)
+        w.K = 5000
     with F.FastGED(w.cost) as g:
         ref_c, ref_m, ref_n = g.run(w)
     b, keep, mm = _device_batch(w, torch)
