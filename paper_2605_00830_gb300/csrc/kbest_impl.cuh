@@ -1106,9 +1106,11 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
 
 // One pair per thread-block cluster: every CTA of the cluster belongs to the team. Each
 // CTA keeps its own copy of the read-only target-graph tables; what the team writes lives in
-// the cluster's slice of global scratch, together with the team scalars.
+// the cluster's slice of global scratch, together with the team scalars. Two-word teams are
+// held to 64 registers so that two CTAs share an SM (more clusters resident at once); wider
+// ones keep 128 (their 16-word evaluation would spill).
 template <int W, typename MapT, typename Word, int BK>
-__global__ void __launch_bounds__(512, 1) kbest_cluster_kernel(const KParams p)
+__global__ void __launch_bounds__(512, (W <= 2) ? 2 : 1) kbest_cluster_kernel(const KParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const unsigned crank = cluster_rank(), csize = cluster_size();
