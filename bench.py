@@ -120,7 +120,7 @@ def workload(rank: int, n_pairs: int):
     fn, full, seed0, _ = WORKLOADS[_ARGS.workload]
     seed = seed0 if rank == 0 else seed0 + 7919 * rank
     w = getattr(W, fn)(n_pairs or full, seed=seed)
-    if _ARGS.k:
+    if getattr(_ARGS, "k", 0):
         w.K = _ARGS.k
     return w
 
@@ -141,7 +141,7 @@ def config_dict(w, extra=None):
     d = {"workload": WORKLOADS[_ARGS.workload][3],
          "name": w.name, "n_pairs": w.n_pairs, "K": w.K, "cost": list(w.cost),
          "l2": "flushed (256 MB write) between timed steps", "seed": WORKLOADS[_ARGS.workload][2]}
-    if _ARGS.k:
+    if getattr(_ARGS, "k", 0):
         d["workload"] += f"; K set to {w.K} for every pair"
     if extra:
         d.update(extra)

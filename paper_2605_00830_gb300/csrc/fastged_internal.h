@@ -37,7 +37,7 @@ struct GraphMeta {
 
 enum Region : int {
     RG_HIST = 0, RG_ALPHA2, RG_A2T, RG_L2T, RG_SBASE, RG_PED0, RG_PED1, RG_SEL, RG_SELPED,
-    RG_KLIST, RG_KPED, RG_NOFF, RG_NBR, RG_IMG0, RG_IMG1, RG_P, RG_PL, RG_CSLOT, RG_CJ,
+    RG_KLIST, RG_KPED, RG_NOFF, RG_NBR, RG_IMG0, RG_IMG1, RG_P, RG_PL,
     RG_CAND, RG_MAP0, RG_MAP1, RG_IMGL, RG_CROW,
     RG_COUNT
 };

@@ -356,27 +356,24 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     sz[RG_PL] = (size_t)B * kl * W * wb;
     sz[RG_IMGL] = cp.cluster > 1 ? kl * W * wb : 0;
     // single-word classes pack the successor ids into the PED entries
-    // packed classes keep the successor ids inside the PED entries
+    // one entry per successor: 32 bits when packed, else 64 (PED, parent slot, j)
     const bool packed = cp.pk && cp.cluster == 1;
     L.pk = packed ? 1 : 0;
-    sz[RG_CSLOT] = packed ? 0 : ncand * 4;
-    sz[RG_CJ] = packed ? 0 : ncand * msz;
-    sz[RG_CAND] = ncand * 4;
+    sz[RG_CAND] = ncand * (packed ? 4 : 8);
     sz[RG_MAP0] = km * L.mrow;
     sz[RG_MAP1] = km * L.mrow;
     // shared memory is filled in order of access frequency; the rest goes to global scratch
     static const int prio[RG_COUNT] = {RG_HIST, RG_CROW, RG_ALPHA2, RG_SBASE, RG_PED0, RG_PED1,
                                        RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_NOFF,
                                        RG_A2T, RG_L2T, RG_IMG0, RG_IMG1, RG_P, RG_PL,
-                                       RG_CSLOT, RG_CJ, RG_CAND, RG_NBR, RG_MAP0, RG_MAP1,
-                                       RG_IMGL};
+                                       RG_CAND, RG_NBR, RG_MAP0, RG_MAP1, RG_IMGL};
     // cluster teams: the per-CTA tables the CTA writes (P, PL, sbase, staged Img) must be in
     // shared memory, so they come first
     static const int prio_cl[RG_COUNT] = {RG_SBASE, RG_P, RG_PL, RG_IMGL, RG_CROW, RG_ALPHA2,
                                           RG_NOFF,
                                           RG_A2T, RG_L2T, RG_NBR, RG_HIST, RG_PED0, RG_PED1,
                                           RG_SEL, RG_SELPED, RG_KLIST, RG_KPED, RG_IMG0,
-                                          RG_IMG1, RG_CSLOT, RG_CJ, RG_CAND, RG_MAP0, RG_MAP1};
+                                          RG_IMG1, RG_CAND, RG_MAP0, RG_MAP1};
     // a cluster team shares only global memory: its CTAs keep private shared-memory copies
     // of the read-only target-graph tables and neighbour lists, everything else is global
     auto cta_local = [](int r) {

@@ -126,8 +126,7 @@ struct Regions {
     int32_t *hist, *alpha2, *crow, *sbase, *sel, *selped, *klist, *kped, *noff, *nbr, *cand;
     int32_t *ped0, *ped1;
     Word *a2t, *l2t, *img0, *img1, *P, *PL, *imgl;
-    uint32_t *cslot;
-    uint8_t *map0, *map1, *cj;
+    uint8_t *map0, *map1;
 };
 
 // A kept child is stored in the selection list as (parent slot << 11) | j, j = 0..n2.
@@ -160,11 +159,12 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsig
     return m;
 }
 
-// PED stored in a successor entry: the entry itself, or for packed entries
-// (PED << 16 | parent slot << jbits | j) its upper half.
-__device__ __forceinline__ int cand_ped(int32_t e, bool pk)
+// PED of successor entry k: a packed 32-bit entry (PED << 16 | parent slot << jbits | j) or
+// an unpacked 64-bit one (PED << 32 | parent slot << kSelShift | j).
+__device__ __forceinline__ int entry_ped(const int32_t *cand, int64_t k, bool pk)
 {
-    return pk ? (int)((uint32_t)e >> 16) : e;
+    return pk ? (int)(((const uint32_t *)cand)[k] >> 16)
+              : (int)(((const uint64_t *)cand)[k] >> 32);
 }
 
 // Stable compaction of the kept successors of this warp, in enumeration order: every
@@ -176,7 +176,7 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 {
     const int lane = threadIdx.x & 31;
     const int keep0 = keep_before;
-    const int32_t *cand = R.cand + base;
+
     // four chunks of 32 per step: their loads and threshold ballots are independent, so only
     // chunks holding a kept candidate pay for the ordered part
     for (int kb = 0; kb < n; kb += 128) {
@@ -185,7 +185,7 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = kb + 32 * u + lane;
-            v[u] = k < n ? cand_ped(cand[k], pk) : INT_MAX;
+            v[u] = k < n ? entry_ped(R.cand, (int64_t)base + k, pk) : INT_MAX;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(0xffffffffu, v[u] <= T);
@@ -229,7 +229,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     R.kped = kped;
 
     int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, cand_ped(cand[base + k], pk));
+    for (int k = lane; k < n; k += 32) mx = max(mx, entry_ped(cand, base + k, pk));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -242,7 +242,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (cand_ped(cand[base + k], pk) <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (entry_ped(cand, base + k, pk) <= mid);
         cnt = warp_sum(cnt);
         tm.sync();
         if (tid == 0) S.cnt = 0;
@@ -254,7 +254,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     const int thr = lo;
     int nlt = 0, neq = 0;
     for (int k = lane; k < n; k += 32) {
-        const int v = cand_ped(cand[base + k], pk);
+        const int v = entry_ped(cand, base + k, pk);
         nlt += (v < thr);
         neq += (v == thr);
     }
@@ -351,16 +351,16 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const CostModel c = p.cost;
     const int hwin = p.hwin;     // buckets 0..hwin-2 hold one PED each, hwin-1 the rest
     const bool fold_ie = (c.eins == c.edel);
-    MapT *cjv = (MapT *)R.cj;
-    // Packed classes keep every successor in one 32-bit entry of R.cand:
-    //   PED << 16 | parent slot << jbits | j,   jbits = bit length of n2 (j = 0..n2).
-    // The host packs a class only if no pair's PED can reach 2^16 and every K fits the slot
-    // field (K <= 2^(16 - jbits)); single-word classes are always packed. Other classes
-    // keep PEDs in R.cand and the ids in cslot / cj.
+    // Every successor is one entry of R.cand. Packed classes use 32 bits:
+    //   PED << 16 | parent slot << jbits | j,   jbits = bit length of n2 (j = 0..n2);
+    // the host packs a class only if no pair's PED can reach 2^16 and every K fits the slot
+    // field (K <= 2^(16 - jbits)); single-word classes are always packed. The others use
+    // 64 bits: PED << 32 | parent slot << kSelShift | j (the low half is the selection code).
     const bool pk = CL ? false : (W == 1 ? true : p.lay.pk != 0);
     const int jbits = 32 - __clz(n2);
     const uint32_t jmask = (1u << jbits) - 1u;
     uint32_t *ck = (uint32_t *)R.cand;
+    uint64_t *ck64 = (uint64_t *)R.cand;
     // lane-constant masks: lane b answers for histogram bucket b
     unsigned lanebit[5];
 #pragma unroll
@@ -478,7 +478,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int kw = 0;          // successors of this warp so far
         int wmin = INT_MAX;  // least PED this warp scored
         // PED of successor idx
-        auto ped_at = [&](int idx) -> int { return cand_ped(R.cand[idx], pk); };
+        auto ped_at = [&](int idx) -> int { return entry_ped(R.cand, idx, pk); };
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
@@ -578,22 +578,14 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         const unsigned bal = __ballot_sync(0xffffffffu, fr);
                         if (fr) {
                             const int idx = o0 + pos + __popc(bal & lanemask_lt());
-                            if (pk) {
-                                ck[idx] = ((uint32_t)st_ << jbits) | (uint32_t)j;
-                            } else {
-                                R.cslot[idx] = (uint32_t)st_;
-                                cjv[idx] = (MapT)j;
-                            }
+                            if (pk) ck[idx] = ((uint32_t)st_ << jbits) | (uint32_t)j;
+                            else ck64[idx] = ((uint64_t)st_ << kSelShift) | (uint64_t)j;
                         }
                         pos += __popc(bal);
                     }
                     if (lane == 0) {
-                        if (pk) {
-                            ck[o0 + pos] = ((uint32_t)st_ << jbits) | (uint32_t)n2;
-                        } else {
-                            R.cslot[o0 + pos] = (uint32_t)st_;
-                            cjv[o0 + pos] = (MapT)n2;
-                        }
+                        if (pk) ck[o0 + pos] = ((uint32_t)st_ << jbits) | (uint32_t)n2;
+                        else ck64[o0 + pos] = ((uint64_t)st_ << kSelShift) | (uint64_t)n2;
                     }
                 }
             }
@@ -643,9 +635,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         scu[u] = (int)(idu[u] >> jbits);
                         ju[u] = (int)(idu[u] & jmask);
                     } else {
-                        idu[u] = 0u;
-                        scu[u] = k < gtot ? (int)R.cslot[idx] : g0;
-                        ju[u] = k < gtot ? (int)cjv[idx] : n2;
+                        idu[u] = k < gtot ? (uint32_t)ck64[idx]
+                                          : (((uint32_t)g0 << kSelShift) | (uint32_t)n2);
+                        scu[u] = (int)(idu[u] >> kSelShift);
+                        ju[u] = (int)(idu[u] & ((1u << kSelShift) - 1u));
                     }
                 }
                 int pu[U];
@@ -656,7 +649,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     const int k = kb + 32 * u + lane;
                     if (k < gtot) {
                         if (pk) ck[base + kw + k] = ((uint32_t)pu[u] << 16) | idu[u];
-                        else R.cand[base + kw + k] = pu[u];
+                        else ck64[base + kw + k] = ((uint64_t)(uint32_t)pu[u] << 32) | idu[u];
                         wmin = pu[u] < wmin ? pu[u] : wmin;
                     }
                 }
@@ -763,7 +756,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 const uint32_t id = ck[idx] & 0xffffu;
                 return (int)((id >> jbits) << kSelShift) | (int)(id & jmask);
             } else {
-                return ((int)R.cslot[idx] << kSelShift) | (int)cjv[idx];
+                return (int)(uint32_t)ck64[idx];
             }
         };
 
@@ -1073,8 +1066,6 @@ __device__ __forceinline__ Regions<Word> make_regions(F base)
     R.img1 = (Word *)base(RG_IMG1);
     R.P = (Word *)base(RG_P);
     R.PL = (Word *)base(RG_PL);
-    R.cslot = (uint32_t *)base(RG_CSLOT);
-    R.cj = base(RG_CJ);
     R.cand = (int32_t *)base(RG_CAND);
     R.map0 = base(RG_MAP0);
     R.map1 = base(RG_MAP1);
