@@ -1067,6 +1067,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
 int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *out_cost,
                             int32_t *out_mapping, int64_t *out_nevals)
 {
+    NvtxRange r("fastged results");
     const int32_t err = *(const int32_t *)(host_out + b.woff_err);
     if (err & kErrDuplicateEdge) return set_error(FASTGED_ERR_INVALID_ARG, "duplicate edge in a graph");
     if (err) return set_error(FASTGED_ERR_CUDA, "device error flag " + std::to_string(err));
@@ -1095,9 +1096,14 @@ int fastged::batch_enqueue(fastged_handle *h, const fastged_pair_list *pairs, in
                            const fastged_options &o)
 {
     Batch &b = h->batch;
-    int rc = flatten(h, pairs, K, o, b);
+    int rc;
+    {
+        NvtxRange r("fastged flatten");
+        rc = flatten(h, pairs, K, o, b);
+    }
     if (rc) return rc;
     if (b.n_pairs == 0) return FASTGED_OK;
+    NvtxRange r("fastged upload + launch");
     if ((rc = h->dev_in.ensure(b.in_bytes))) return rc;
     if ((rc = h->dev_work.ensure(b.work_bytes))) return rc;
     cudaStream_t st = h->stream;
@@ -1269,6 +1275,7 @@ extern "C" int fastged_plan_run(fastged_plan *p, void *stream)
     clear_error();
     if (!p) return set_error(FASTGED_ERR_INVALID_ARG, "null plan");
     const Batch &b = p->b;
+    NvtxRange r("fastged plan run");
     cudaStream_t st = stream ? (cudaStream_t)stream : p->stream;
     p->last_stream = st;
     if (b.n_pairs == 0) return FASTGED_OK;

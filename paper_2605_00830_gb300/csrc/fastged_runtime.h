@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fastged.h"
 #include "fastged_internal.h"
 
@@ -74,6 +76,13 @@ int set_error(int code, const char *msg);
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);
+// An NVTX range for timeline tools (Nsight Systems); free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // Packed classes store a successor as PED << 16 | parent slot << jbits | j with
 // jbits = bit length of n2 (j runs over 0..n2): a pair may be packed only if no PED reaches
 // 2^16 and its K fits the remaining 16 - jbits bits. The single-word kernels are always

@@ -163,6 +163,7 @@ static void collect_lane(fastged_server *s, Lane &l)
 // batch is flattened and launched).
 static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex> &lk)
 {
+    NvtxRange r("fastged serve batch");
     const int np = (int)l.reqs.size();
     l.graphs.resize(2 * (size_t)np);
     l.pairs.resize(2 * (size_t)np);
