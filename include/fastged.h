@@ -332,6 +332,30 @@ int fastged_cross(fastged_handle *h, const fastged_graph *graphs, int32_t n_grap
                   const int32_t *rows, int32_t n_rows, const int32_t *cols, int32_t n_cols,
                   int32_t K, const fastged_options *opt, int32_t *out);
 
+/* ---------------------------------------------------------------------------------------
+ * Failure handling (no counterpart in the paper).
+ *
+ * fastged_set_timeout bounds how long fastged_batch / fastged_batch_ex on this handle wait for
+ * the device: past `ms` milliseconds (0 = no bound, the default) they return
+ * FASTGED_ERR_TIMEOUT without results while the batch finishes in the background; the next
+ * call on the handle first waits for it, so the handle stays usable. The wait polls an event;
+ * no kernel ever spins, traps or is cut short.
+ *
+ * fastged_inject_fault arms a one-shot host-side fault for tests: the `countdown`-th event of
+ * `kind` from now fails (countdown 0 disarms). Kinds: FASTGED_INJECT_ALLOC (a device or
+ * pinned allocation reports FASTGED_ERR_OOM; the buffer it would replace is kept),
+ * FASTGED_INJECT_LAUNCH (a K-Best launch is skipped and the call reports FASTGED_ERR_CUDA),
+ * FASTGED_INJECT_ADMISSION (the server's admission check refuses a batch once, as if device
+ * memory were short; the batch waits and is retried). Faults are process-wide and touch no
+ * GPU state: the calls that fail leave their handle or server usable.
+ * --------------------------------------------------------------------------------------- */
+#define FASTGED_INJECT_ALLOC 0
+#define FASTGED_INJECT_LAUNCH 1
+#define FASTGED_INJECT_ADMISSION 2
+
+int fastged_set_timeout(fastged_handle *h, int32_t ms);
+int fastged_inject_fault(int32_t kind, int32_t countdown);
+
 /* Integer-pipe throughput of the current device (no counterpart in the paper; it is the
  * measured peak the benchmark compares the successor evaluation against). Runs three
  * short probe kernels issuing independent 32-bit LOP3, IADD and POPC chains on every SM

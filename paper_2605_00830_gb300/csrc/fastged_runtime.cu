@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <condition_variable>
@@ -82,6 +83,8 @@ static int cuda_fail(cudaError_t e, const char *what)
 int DevBuf::ensure(size_t n)
 {
     if (n <= cap) return 0;
+    if (inject_fire(FASTGED_INJECT_ALLOC))
+        return set_error(FASTGED_ERR_OOM, "injected device allocation failure");
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -106,6 +109,8 @@ void DevBuf::release()
 int PinBuf::ensure(size_t n)
 {
     if (n <= cap) return 0;
+    if (inject_fire(FASTGED_INJECT_ALLOC))
+        return set_error(FASTGED_ERR_OOM, "injected pinned allocation failure");
     if (p) cudaFreeHost(p);
     p = nullptr;
     cap = 0;
@@ -241,6 +246,36 @@ struct FirstError {
     int report() const { return set_error(FASTGED_ERR_INVALID_ARG, msg); }
 };
 
+// ------------------------------------------------------------------------------------
+// host-side fault injection (tests) and the handle's wait bound
+// ------------------------------------------------------------------------------------
+static std::atomic<int> g_inject[3];   // countdown per kind; 0 = disarmed
+
+bool fastged::inject_fire(int kind)
+{
+    int c = g_inject[kind].load();
+    while (c > 0)
+        if (g_inject[kind].compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
+extern "C" int fastged_inject_fault(int32_t kind, int32_t countdown)
+{
+    clear_error();
+    if (kind < 0 || kind > 2 || countdown < 0)
+        return set_error(FASTGED_ERR_INVALID_ARG, "fault kind or countdown out of range");
+    g_inject[kind].store(countdown);
+    return FASTGED_OK;
+}
+
+extern "C" int fastged_set_timeout(fastged_handle *h, int32_t ms)
+{
+    clear_error();
+    if (!h || ms < 0) return set_error(FASTGED_ERR_INVALID_ARG, "null handle or negative timeout");
+    h->timeout_ms = ms;
+    return FASTGED_OK;
+}
+
 static int words_class(int n)
 {
     const int w = (n + 63) / 64;
@@ -278,6 +313,7 @@ extern "C" int fastged_create(const fastged_cost_model *cost, fastged_handle **o
         e = cudaStreamCreateWithFlags(&h->class_stream[k], cudaStreamNonBlocking);
     for (int k = 0; k < kMaxClasses + 1 && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fastged_destroy(h);
         return cuda_fail(e, "stream/event creation");
@@ -297,6 +333,7 @@ extern "C" void fastged_destroy(fastged_handle *h)
         }
     for (int k = 0; k < kMaxClasses + 1; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->done) cudaEventDestroy(h->done);
     if (h->stream) cudaStreamDestroy(h->stream);
     h->dev_in.release();
     h->dev_work.release();
@@ -1007,6 +1044,8 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
         ++nl;
     }
     const int nc = (int)b.classes.size();
+    if (inject_fire(FASTGED_INJECT_LAUNCH))
+        return set_error(FASTGED_ERR_CUDA, "injected launch failure (no K-Best kernel launched)");
     if (t0) CK(cudaEventRecordWithFlags(t0, st, evflag));
     if (b.opt.form == FASTGED_FORM_PLAIN) {
         // one launch per pair, in pair order, single team, on the caller's stream
@@ -1092,9 +1131,20 @@ int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *ou
 // ------------------------------------------------------------------------------------
 // one-shot batch
 // ------------------------------------------------------------------------------------
+// A batch that timed out may still be running on the handle's stream and writing into its
+// buffers: wait for it before they are reused.
+static void drain(fastged_handle *h)
+{
+    if (!h->inflight) return;
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    h->inflight = false;
+}
+
 int fastged::batch_enqueue(fastged_handle *h, const fastged_pair_list *pairs, int32_t K,
                            const fastged_options &o)
 {
+    drain(h);
     Batch &b = h->batch;
     int rc;
     {
@@ -1130,8 +1180,29 @@ extern "C" int fastged_batch_ex(fastged_handle *h, const fastged_pair_list *pair
     if (!h) return set_error(FASTGED_ERR_INVALID_ARG, "null handle");
     const fastged_options o = opt ? *opt : default_options();
     int rc = batch_enqueue(h, pairs, K, o);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(h->stream));
+    if (rc) {
+        // work enqueued before the failure must finish before the buffers are reused
+        cudaStreamSynchronize(h->stream);
+        cudaGetLastError();
+        return rc;
+    }
+    if (h->timeout_ms > 0) {
+        CK(cudaEventRecord(h->done, h->stream));
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            const cudaError_t q = cudaEventQuery(h->done);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return cuda_fail(q, "batch");
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(h->timeout_ms)) {
+                h->inflight = true;
+                return set_error(FASTGED_ERR_TIMEOUT,
+                                 "batch exceeded the handle's timeout; it finishes in the background");
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    } else {
+        CK(cudaStreamSynchronize(h->stream));
+    }
     return batch_results(h, out_cost, out_mapping, out_nevals);
 }
 
@@ -1241,6 +1312,7 @@ extern "C" int fastged_plan_create(fastged_handle *h, const fastged_pair_list *p
 {
     clear_error();
     if (!h || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
+    drain(h);
     const fastged_options o = opt ? *opt : default_options();
     if (o.autotune && o.block_threads == 0) {
         const int rc = autotune_batch(h, pairs, K, o);

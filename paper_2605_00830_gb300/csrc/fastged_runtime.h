@@ -76,6 +76,9 @@ int set_error(int code, const char *msg);
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);
+// One-shot host-side fault injection (fastged_inject_fault): true when the armed fault of
+// this kind fires now.
+bool inject_fire(int kind);
 // An NVTX range for timeline tools (Nsight Systems); free when no tool is attached.
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
@@ -129,6 +132,9 @@ struct fastged_handle {
     fastged::DevBuf dev_in, dev_work;
     fastged::PinBuf pin;
     fastged::Batch batch;
+    int32_t timeout_ms = 0;         // 0: fastged_batch_ex waits without a bound
+    bool inflight = false;          // a timed-out batch may still be running on `stream`
+    cudaEvent_t done = nullptr;     // recorded after a batch, polled under a timeout
 };
 
 struct fastged_plan {

@@ -288,7 +288,8 @@ static void dispatcher_main(fastged_server *s)
                 size_t free_b = 0, total_b = 0;
                 cudaMemGetInfo(&free_b, &total_b);
                 const size_t need = footprint(take) + (size_t)s->cfg.hbm_reserve_bytes;
-                if (free_b < need && busy > 0) {
+                const bool refuse = (free_b < need && busy > 0) || inject_fire(FASTGED_INJECT_ADMISSION);
+                if (refuse) {
                     // wait for a running batch to release memory; keep arrival order
                     for (auto it = take.rbegin(); it != take.rend(); ++it) s->pending.push_front(*it);
                     s->st.admission_waits++;

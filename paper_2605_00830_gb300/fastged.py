@@ -27,6 +27,9 @@ FASTGED_ERR_BUSY = -5
 FASTGED_ERR_STOPPED = -6
 FASTGED_FORM_BATCHED = 0
 FASTGED_FORM_PLAIN = 1
+FASTGED_INJECT_ALLOC = 0
+FASTGED_INJECT_LAUNCH = 1
+FASTGED_INJECT_ADMISSION = 2
 FASTGED_ORDER_INDEX = 0
 FASTGED_ORDER_DEGREE = 1
 
@@ -37,7 +40,8 @@ EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_
             "fastged_serve_start", "fastged_serve_submit", "fastged_serve_poll",
             "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy",
             "fastged_autotune_entries", "fastged_autotune_clear", "fastged_edit_path",
-            "fastged_apply_edit_ops", "fastged_cross"]
+            "fastged_apply_edit_ops", "fastged_cross", "fastged_set_timeout",
+            "fastged_inject_fault"]
 
 
 class FastGEDError(RuntimeError):
@@ -166,6 +170,8 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
                                            vp, i32, vp, vp, vp, vp, vp]
     lib.fastged_cross.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, ctypes.POINTER(Options),
                                   vp]
+    lib.fastged_set_timeout.argtypes = [vp, i32]
+    lib.fastged_inject_fault.argtypes = [i32, i32]
     lib.fastged_autotune_entries.restype = ctypes.c_int
     lib.fastged_autotune_clear.restype = None
     for name in EXPORTED:
@@ -562,3 +568,13 @@ def knn_classify(cost: Sequence[int], train, train_labels, test, K: int, k: int 
         vals, cnt = np.unique(lab[near], return_counts=True)
         out[t] = vals[np.argmax(cnt)]
     return out
+
+
+def fastged_set_timeout(h: int, ms: int) -> None:
+    lib = load()
+    _check(lib, lib.fastged_set_timeout(h, int(ms)))
+
+
+def fastged_inject_fault(kind: int, countdown: int) -> None:
+    lib = load()
+    _check(lib, lib.fastged_inject_fault(int(kind), int(countdown)))
