@@ -117,6 +117,18 @@ def test_degree_vertex_order(cfg):
         assert np.array_equal(x, y)
 
 
+def test_option_combinations():
+    """Degree order with per-pair K, degree order with variant B, and variant B solved by a
+    cluster team (one large pair, fewer pairs than SMs)."""
+    w = W.config2(90, seed=31)
+    w.k_per_pair = W.Stream(31, 2).randint(1, 100, w.n_pairs).astype(np.int32)
+    assert_parity(w, gpu_run(w, vertex_order=1), order=1)
+    w1 = W.config1(80)
+    assert_parity(w1, gpu_run(w1, vertex_order=1, variant=1), order=1, variant=1)
+    big = W.config4(1, seed=13, n_range=(300, 340))
+    assert_parity(big, gpu_run(big, K=64, variant=1), K=64, variant=1)
+
+
 def test_setting2_costs():
     """The paper's cost setting 2 (expensive insertions and deletions) on molecule-like and
     dense pairs, both branching orders."""
