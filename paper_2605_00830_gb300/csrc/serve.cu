@@ -205,6 +205,11 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
     int rc = batch_enqueue(l.h, &pl, kmax, o);
     if (rc == FASTGED_OK && cudaLaunchHostFunc(l.h->stream, lane_done_cb, &l) != cudaSuccess)
         rc = FASTGED_ERR_CUDA;
+    if (rc != FASTGED_OK) {
+        // copies queued before the failure finish before the lane's buffers are reused
+        cudaStreamSynchronize(l.h->stream);
+        cudaGetLastError();
+    }
     lk.lock();
     if (rc != FASTGED_OK) {
         // nothing is in flight on this lane: report the failure for every request

@@ -96,3 +96,37 @@ def test_fault_arguments_are_checked():
     for kind, cd in ((3, 1), (-1, 1), (0, -2)):
         with pytest.raises(F.FastGEDError):
             F.fastged_inject_fault(kind, cd)
+
+
+def test_injected_launch_failure_while_serving():
+    """A served batch whose launch fails reports the error for each of its queries; the
+    server keeps serving, and the failed queries succeed when submitted again."""
+    w = W.config2(40)
+    ref = gpu_run(w)
+    mm = F.marshal(w)
+    srv = F.Server(w.cost, F.serve_config(lanes=2, min_batch_pairs=8))
+    F.fastged_inject_fault(F.FASTGED_INJECT_LAUNCH, 1)
+
+    def serve(tags):
+        for t in tags:
+            p = t % 1000
+            assert srv.submit(mm, w.pairs[p][0], w.pairs[p][1], w.K, t) == F.FASTGED_OK
+        got, deadline = {}, time.time() + 120
+        while len(got) < len(tags) and time.time() < deadline:
+            for r in srv.poll(timeout_ms=50):
+                got[int(r[0])] = r
+        assert len(got) == len(tags)
+        return got
+
+    got = serve(list(range(w.n_pairs)))
+    failed = [t for t, r in got.items() if r[1] != F.FASTGED_OK]
+    assert failed and all(got[t][1] == F.FASTGED_ERR_CUDA for t in failed)
+    for t, r in got.items():
+        if r[1] == F.FASTGED_OK:
+            assert r[2] == ref[0][t]
+    again = serve([1000 + t for t in failed])
+    for t, r in again.items():
+        assert r[1] == F.FASTGED_OK and r[2] == ref[0][t - 1000]
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == len(failed)
