@@ -167,6 +167,20 @@ def test_huge_k(case):
                 assert np.array_equal(x, y)
 
 
+def test_results_do_not_depend_on_pair_order():
+    """The same pairs in a permuted order (so other neighbours in the queue, other teams,
+    other class positions) give the same per-pair results."""
+    w = W.config2(300, seed=41)
+    base = gpu_run(w)
+    perm = np.random.RandomState(3).permutation(w.n_pairs)
+    wp = W.Workload(w.name, w.graphs, w.pairs[perm], w.cost, w.K)
+    c, m, n = gpu_run(wp)
+    mm, mp = F.marshal(w), F.marshal(wp)
+    assert np.array_equal(c, base[0][perm]) and np.array_equal(n, base[2][perm])
+    for q, p in enumerate(perm):
+        assert np.array_equal(m[mp.map_off[q]:mp.map_off[q + 1]], base[1][mm.map_off[p]:mm.map_off[p + 1]])
+
+
 def test_concurrent_batches_from_two_host_threads():
     """Two handles used from two host threads at once (the batch flattening shares one host
     thread pool; a call that finds it busy runs serially): results equal serial runs."""

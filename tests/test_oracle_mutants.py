@@ -95,3 +95,77 @@ def test_mutant_is_caught(name, tmp_path):
     path.write_text(src.replace(old, new))
     lib = O._bind(O.compile_c(str(path), str(tmp_path / "libmutant.so")))
     assert not _pins_pass(lib), f"pins did not catch mutant {name}"
+
+
+# --------------------------------------------------------------------------------------
+# planted mistakes in the Python parts of the oracle (edit paths, branching order)
+# --------------------------------------------------------------------------------------
+import inspect  # noqa: E402
+
+PY_MUTANTS = {
+    "edit_path": {
+        "deletion_costed_as_insertion": ("ops.append((OP_EDEL, c_edel, u, v, -1, -1))",
+                                         "ops.append((OP_EDEL, c_eins, u, v, -1, -1))"),
+        "edge_relabel_always": ("if l2 is not None and l2 != el1[k]:", "if l2 is not None:"),
+        "insertions_between_mapped_missed": (
+            "if x not in pre or y not in pre or frozenset((pre[x], pre[y])) not in g1_edge:",
+            "if x not in pre or y not in pre:"),
+        "vertex_relabel_always": ("if phi[v] >= 0 and lab1[v] != lab2[phi[v]]:", "if phi[v] >= 0:"),
+        "deleted_vertex_edges_kept": (
+            "if phi[u] < 0 or phi[v] < 0 or frozenset((phi[u], phi[v])) not in g2_edge:",
+            "if phi[u] >= 0 and phi[v] >= 0 and frozenset((phi[u], phi[v])) not in g2_edge:"),
+    },
+    "degree_order": {
+        "ascending_degree": ("key=lambda v: (-deg[v], v)", "key=lambda v: (deg[v], v)"),
+        "ties_by_reverse_index": ("key=lambda v: (-deg[v], v)", "key=lambda v: (-deg[v], -v)"),
+    },
+}
+
+
+def _mutant_fn(name, old, new):
+    src = inspect.getsource(getattr(O, name))
+    assert src.count(old) == 1, (name, old)
+    ns = dict(vars(O))
+    exec(src.replace(old, new), ns)   # noqa: S102 - a planted mistake in test code
+    return ns[name]
+
+
+def _edit_path_pins_pass(fn) -> bool:
+    g1 = W.Graph(3, np.array([0, 1, 2], np.int32), np.array([[0, 1], [1, 2]], np.int32),
+                 np.array([0, 1], np.int32))
+    g2 = W.Graph(3, np.array([0, 1, 1], np.int32), np.array([[0, 1], [0, 2]], np.int32),
+                 np.array([1, 0], np.int32))
+    if fn(g1, g2, W.SETTING1_COSTS, [0, 1, -1]) != [
+            (O.OP_VINS, 4, -1, -1, 2, -1), (O.OP_EDEL, 2, 1, 2, -1, -1),
+            (O.OP_ESUB, 1, 0, 1, 0, 1), (O.OP_EINS, 2, -1, -1, 0, 2),
+            (O.OP_VDEL, 4, 2, -1, -1, -1)]:
+        return False
+    for s in range(40):
+        st = W.Stream(s, 71)
+        a = W.random_small(st, 0, 7, 0.45, 3, 3 if s % 2 else 0)
+        b = W.random_small(st, 0, 7, 0.45, 3, 3 if s % 2 else 0)
+        perm = list(np.argsort(st.uniform(b.n))) if b.n else []
+        mp = [int(perm.pop()) if perm and st.uniform(1)[0] < 0.75 else -1 for _ in range(a.n)]
+        cost = (3, 5, 7, 2, 11, 13)   # distinct, so a swapped cost changes the total
+        if sum(o[1] for o in fn(a, b, cost, mp)) != O.full_cost(a, b, cost, mp):
+            return False
+    return True
+
+
+def _degree_order_pins_pass(fn) -> bool:
+    g = W.Graph(7, np.arange(7, dtype=np.int32),
+                np.array([[0, 1], [1, 2], [3, 4], [3, 5], [3, 6]], dtype=np.int32))
+    return fn(g) == [3, 1, 0, 2, 4, 5, 6]
+
+
+def test_python_oracle_pins_pass_on_the_real_functions():
+    assert _edit_path_pins_pass(O.edit_path)
+    assert _degree_order_pins_pass(O.degree_order)
+
+
+@pytest.mark.parametrize("fname,mut", [(f, m) for f, ms in PY_MUTANTS.items() for m in ms])
+def test_python_oracle_mutant_is_rejected(fname, mut):
+    old, new = PY_MUTANTS[fname][mut]
+    fn = _mutant_fn(fname, old, new)
+    check = _edit_path_pins_pass if fname == "edit_path" else _degree_order_pins_pass
+    assert not check(fn), f"the pins accept the mutant {fname}:{mut}"

@@ -186,6 +186,25 @@ def test_kbest_on_config1_is_upper_bound():
     assert n_opt > 0
 
 
+def test_kbest_result_is_the_best_completed_leaf():
+    """The result is the cheapest completion of the final kept list (Algorithm 1, insertions
+    at the leaf): min over the leaves of the independent full-path cost. Hence it equals the
+    exact GED whenever some leaf's map is optimal (config 1, K = 16)."""
+    w = W.config1()
+    n_opt = 0
+    for p in range(0, w.n_pairs, 2):
+        g1, g2 = w.graphs[2 * p], w.graphs[2 * p + 1]
+        cost, _, _ = O.kbest(g1, g2, w.cost, w.K)
+        _, maps = O.kbest_leaves(g1, g2, w.cost, w.K)
+        best_leaf = min(O.full_cost(g1, g2, w.cost, m) for m in maps)
+        assert cost == best_leaf
+        ged = O.brute_ged(g1, g2, w.cost)[0]
+        if best_leaf == ged:
+            assert cost == ged
+            n_opt += 1
+    assert n_opt > 0
+
+
 def test_kbest_k1_evals_closed_form():
     """With K = 1 the search follows one path: level i scores (n2 - #substitutions so far)
     + 1 successors, and one leaf is completed."""
