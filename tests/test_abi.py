@@ -73,3 +73,43 @@ def test_marshalling_offsets():
     addr = int(mm.gs["edges"][7])
     buf = (ctypes.c_int32 * (2 * g.m)).from_address(addr)
     assert list(buf) == list(g.edges.reshape(-1))
+
+
+def test_host_entry_points_called_from_c(tmp_path):
+    """A C program linked against the library calls the host-only entry points (edit path,
+    partial application, fault-argument checks, error strings) on a hand-worked example."""
+    path = B.build()
+    prog = tmp_path / "use.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include "fastged.h"
+int main(void) {
+    const int32_t vl1[3] = {0, 1, 2}, ed1[4] = {0, 1, 1, 2}, el1[2] = {0, 1};
+    const int32_t vl2[3] = {0, 1, 1}, ed2[4] = {0, 1, 0, 2}, el2[2] = {1, 0};
+    fastged_graph g1 = {3, vl1, 2, ed1, el1}, g2 = {3, vl2, 2, ed2, el2};
+    fastged_cost_model c = {2, 4, 4, 1, 2, 2};
+    const int32_t map[3] = {0, 1, -1};
+    fastged_edit_op ops[16];
+    int32_t n = 0;
+    int64_t tot = 0;
+    if (fastged_edit_path(&c, &g1, &g2, map, ops, 16, &n, &tot) != FASTGED_OK) return 1;
+    printf("ops %d total %lld kinds", n, (long long)tot);
+    for (int k = 0; k < n; ++k) printf(" %d", ops[k].kind);
+    int32_t on = 0, om = 0, vl[6], ed[8], el[4];
+    if (fastged_apply_edit_ops(&g1, &g2, map, ops, n, &on, vl, &om, ed, el) != FASTGED_OK) return 2;
+    printf(" | applied n %d m %d", on, om);
+    const int32_t bad[3] = {0, 0, -1};
+    const int rc = fastged_edit_path(&c, &g1, &g2, bad, NULL, 0, &n, NULL);
+    printf(" | bad map %d (%s)", rc, fastged_last_error(NULL) ? "msg" : "none");
+    printf(" | inject %d %d\n", fastged_inject_fault(7, 1), fastged_inject_fault(0, 0));
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog),
+                           path, "-o", str(exe), f"-Wl,-rpath,{os.path.dirname(path)}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == ("ops 5 total 13 kinds 0 2 3 4 5 | applied n 3 m 2 | "
+                                  f"bad map {F.FASTGED_ERR_INVALID_ARG} (msg) | "
+                                  f"inject {F.FASTGED_ERR_INVALID_ARG} 0")
