@@ -434,6 +434,8 @@ def ours(args):
                               "batched_over_plain": value / ws / plain}
         # serving: continuous batching under a Poisson stream
         line["serve"] = serving_leg(args.serve_window)
+        # the same stream at a load the GPU sustains (the 5,000 req/s stream saturates it)
+        line["serve_sustained"] = serving_leg(args.serve_window, rate=1000.0)
         # CPU oracle on a bounded sample, all host cores
         threads = os.cpu_count() or 1
         idx = list(range(min(args.cpu_sample, w.n_pairs)))
@@ -441,6 +443,12 @@ def ours(args):
         line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
                                 "sample": f"first {len(idx)} of the 20,000 pairs"}
+        # and on one host core (a smaller sample)
+        idx1 = list(range(min(max(args.cpu_sample // 16, 50), w.n_pairs)))
+        dt1, _ = run_cpu_oracle(w, idx1, 1)
+        line["cpu_baseline_1core"] = {"value": len(idx1) / dt1, "unit": UNIT, "cores": 1,
+                                      "kind": "oracle",
+                                      "sample": f"first {len(idx1)} of the 20,000 pairs"}
     F.fastged_plan_destroy(plan)
     g.close()
     if rank == 0:
