@@ -143,7 +143,11 @@ int fastged::label_instance(int B) { return B == 0 ? 0 : (B == 2 ? 2 : 8); }
 // A process-wide pool of worker threads, created on first use. parallel_for(n, grain, f)
 // runs f(lo, hi) over [0, n) in chunks of `grain` on the workers and the calling thread and
 // returns when every chunk is done; a call made while another one is running (from another
-// host thread) runs serially in the caller instead.
+// host thread) runs serially in the caller instead. The passes of one batch follow each other
+// within microseconds, so an idle worker polls for the next job for a short while (yielding
+// its core) before it sleeps, and the caller polls for the workers to finish before it
+// sleeps; a job is still taken up and released under the mutex, so no worker can run a job
+// whose call has returned.
 class HostPool {
 public:
     static HostPool &get()
@@ -151,6 +155,9 @@ public:
         static HostPool pool;
         return pool;
     }
+
+    // threads that run a parallel_for: the workers and the caller
+    int64_t threads() const { return (int64_t)workers_.size() + 1; }
 
     void parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)> &f)
     {
@@ -165,19 +172,22 @@ public:
             n_ = n;
             grain_ = grain;
             next_.store(0);
-            ++gen_;
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         run(&f, n, grain);
+        poll_until([&] { return active_.load(std::memory_order_acquire) == 0; });
         {
             std::unique_lock<std::mutex> lk(mu_);
-            done_cv_.wait(lk, [&] { return active_ == 0; });
+            done_cv_.wait(lk, [&] { return active_.load() == 0; });
             job_ = nullptr;
         }
         busy_.unlock();
     }
 
 private:
+    static constexpr int kPollUs = 200;
+
     HostPool()
     {
         const unsigned hw = std::thread::hardware_concurrency();
@@ -188,10 +198,16 @@ private:
     {
         {
             std::lock_guard<std::mutex> g(mu_);
-            quit_ = true;
+            quit_.store(true);
         }
         cv_.notify_all();
         for (auto &t : workers_) t.join();
+    }
+    template <typename Pred>
+    static void poll_until(Pred done)
+    {
+        const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(kPollUs);
+        while (!done() && std::chrono::steady_clock::now() < until) std::this_thread::yield();
     }
     void run(const std::function<void(int64_t, int64_t)> *f, int64_t n, int64_t grain)
     {
@@ -204,30 +220,31 @@ private:
     void loop()
     {
         uint64_t seen = 0;
-        std::unique_lock<std::mutex> lk(mu_);
         for (;;) {
-            cv_.wait(lk, [&] { return quit_ || (gen_ != seen && job_ != nullptr); });
-            if (quit_) return;
-            seen = gen_;
+            poll_until([&] { return gen_.load(std::memory_order_acquire) != seen || quit_.load(); });
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_.wait(lk, [&] { return quit_.load() || (gen_.load() != seen && job_ != nullptr); });
+            if (quit_.load()) return;
+            seen = gen_.load();
             const auto *f = job_;
             const int64_t n = n_, grain = grain_;
-            ++active_;
+            active_.fetch_add(1);
             lk.unlock();
             run(f, n, grain);
             lk.lock();
-            if (--active_ == 0) done_cv_.notify_all();
+            if (active_.fetch_sub(1, std::memory_order_acq_rel) == 1) done_cv_.notify_all();
         }
     }
 
     std::vector<std::thread> workers_;
     std::mutex mu_, busy_;
     std::condition_variable cv_, done_cv_;
-    const std::function<void(int64_t, int64_t)> *job_ = nullptr;
-    int64_t n_ = 0, grain_ = 1;
+    const std::function<void(int64_t, int64_t)> *job_ = nullptr;   // guarded by mu_
+    int64_t n_ = 0, grain_ = 1;                                     // guarded by mu_
     std::atomic<int64_t> next_{0};
-    uint64_t gen_ = 0;
-    int active_ = 0;
-    bool quit_ = false;
+    std::atomic<uint64_t> gen_{0};   // written under mu_, polled without it
+    std::atomic<int> active_{0};     // workers inside run(); changed under mu_
+    std::atomic<bool> quit_{false};
 };
 
 // The error of the lowest index among those reported from parallel chunks.
@@ -712,13 +729,23 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     b.meta.resize(ng);
     HostPool &pool = HostPool::get();
     FirstError ferr;
-    // graphs: validation, words per row, edge-label range (chunks of graphs in parallel)
-    std::mutex red_mu;
-    int maxlab = 0;
-    bool labelled = false;
-    pool.parallel_for(ng, 2048, [&](int64_t lo, int64_t hi) {
-        int ml = 0;
+    // Graphs and pairs are processed in fixed chunks on the host pool; each chunk keeps its
+    // own partial results (sizes, maxima, class histograms) and a short serial step combines
+    // them, so nothing depends on how many threads ran.
+    const int64_t nthr = pool.threads();
+    const int64_t gch = std::max<int64_t>(1024, (ng + 4 * nthr - 1) / (4 * nthr));
+    const int64_t pch = std::max<int64_t>(2048, (np + 2 * nthr - 1) / (2 * nthr));
+    const int ngc = (int)((ng + gch - 1) / gch), npc = (int)((np + pch - 1) / pch);
+
+    // graphs: validation, words per row, edge-label range, sizes per chunk
+    struct GraphChunk {
+        int64_t nv = 0, ne = 0, adjw = 0;   // sizes of the chunk, then its base offsets
+        int maxlab = 0;
         bool lab = false;
+    };
+    std::vector<GraphChunk> gcs(ngc);
+    pool.parallel_for(ng, gch, [&](int64_t lo, int64_t hi) {
+        GraphChunk &C = gcs[lo / gch];
         for (int g = (int)lo; g < (int)hi; ++g) {
             const fastged_graph &G = pl->graphs[g];
             auto where = [g] { return "graph " + std::to_string(g); };
@@ -730,56 +757,73 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             M.m = G.m;
             M.W = std::max(1, (G.n + 63) / 64);
             M.pad = 0;
-            bool bad = false;
+            C.nv += G.n;
+            C.ne += G.m;
+            C.adjw += (int64_t)G.n * M.W;
             if (G.elabel && G.m > 0) {
-                lab = true;
+                C.lab = true;
+                int ml = 0, lo_l = 0;
                 for (int k = 0; k < G.m; ++k) {
-                    const int l = G.elabel[k];
-                    if (l < 0 || l > FASTGED_MAX_ELABEL) { bad = true; break; }
-                    ml = std::max(ml, l);
+                    ml = std::max(ml, G.elabel[k]);
+                    lo_l = std::min(lo_l, G.elabel[k]);
                 }
+                if (lo_l < 0 || ml > FASTGED_MAX_ELABEL) { ferr.put(g, where() + ": edge label out of range"); break; }
+                C.maxlab = std::max(C.maxlab, ml);
             }
-            if (bad) { ferr.put(g, where() + ": edge label out of range"); break; }
         }
-        std::lock_guard<std::mutex> gl(red_mu);
-        maxlab = std::max(maxlab, ml);
-        labelled = labelled || lab;
     });
     if (ferr.idx != INT64_MAX) return ferr.report();
     int64_t nv = 0, ne = 0, adjw = 0;
-    for (int g = 0; g < ng; ++g) {
-        GraphMeta &M = b.meta[g];
-        M.lab_off = nv;
-        M.edge_off = ne;
-        M.adj_off = adjw;
-        nv += M.n;
-        ne += M.m;
-        adjw += (int64_t)M.n * M.W;
+    int maxlab = 0;
+    bool labelled = false;
+    for (GraphChunk &C : gcs) {
+        const GraphChunk t = C;
+        C.nv = nv;
+        C.ne = ne;
+        C.adjw = adjw;
+        nv += t.nv;
+        ne += t.ne;
+        adjw += t.adjw;
+        maxlab = std::max(maxlab, t.maxlab);
+        labelled = labelled || t.lab;
     }
     int B = 0;
     while ((1 << B) <= maxlab) ++B;   // planes needed for labels 0..maxlab
     if (B == 1) B = 2;                // served by the two-plane kernel (second plane all zero)
     b.B = B;
     b.labelled = labelled && B > 0;
-    for (int g = 0; g < ng; ++g) b.meta[g].plane_off = b.meta[g].adj_off * B;
     b.n_vlab = nv;
     b.n_edges = ne;
     b.adj_words = adjw;
     b.plane_words = adjw * B;
 
-    // pairs: validation, cost bound, classes
+    // pairs: validation, size class and work bucket of each, with per-chunk class statistics
+    // and (class, bucket) histograms. Classes are numbered in order of first appearance;
+    // inside a class the pairs run heaviest first (longest-processing-time order, which only
+    // shortens the tail: results do not depend on the order), by a work estimate
+    // n1 * min(K, n1 n2 + 1) * (n2 + 1) bucketed at 1/16 of a power of two, ties by index.
     const fastged_cost_model &c = h->cost;
     const int32_t *kpp = opt.k_per_pair;
     b.map_off.resize(np);
-    int64_t mtot = 0;
-    int cls_of[32];
-    for (int k = 0; k < 32; ++k) cls_of[k] = -1;
     b.classes.clear();
-    // pairs: validation and size class of each (chunks of pairs in parallel), then the
-    // classes in order of first appearance
-    struct PairClass { int8_t W, wide, w32, pk; };
-    std::vector<PairClass> pcls((size_t)np);
-    pool.parallel_for(np, 4096, [&](int64_t lo, int64_t hi) {
+    constexpr int kKeys = 32, kBuckets = 64 * 16;
+    struct KeyClass {
+        int first = INT_MAX;   // first pair of this class key
+        int8_t W = 1, wide = 0, w32 = 0, pk = 0;
+        int n1max = 0, n2max = 0, m1max = 0, kmax = 1;
+        int bmin = kBuckets, bmax = -1;
+    };
+    struct PairChunk {
+        int64_t maps = 0;                // map entries of the chunk, then its base offset
+        KeyClass key[kKeys];
+        std::vector<int32_t> hist;       // [key][bucket] counts, then output positions
+    };
+    std::vector<PairChunk> pcs(npc);
+    std::vector<uint8_t> pkey((size_t)np);
+    std::vector<uint16_t> pbk((size_t)np);
+    pool.parallel_for(np, pch, [&](int64_t lo, int64_t hi) {
+        PairChunk &C = pcs[lo / pch];
+        C.hist.assign((size_t)kKeys * kBuckets, 0);
         for (int p = (int)lo; p < (int)hi; ++p) {
             const int a = pl->pairs[2 * p], d = pl->pairs[2 * p + 1];
             auto where = [p] { return "pair " + std::to_string(p); };
@@ -801,76 +845,99 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
                                         (long long)g2.m * c.e_ins;
             const bool pk = packable(ped_bound, kp, g2.n);
             if (W == 1 && !pk) W = 2;
-            pcls[p] = PairClass{(int8_t)W, (int8_t)(g2.n >= 255), (int8_t)(W == 1 && g2.n <= 32),
-                                (int8_t)pk};
+            const bool wide = g2.n >= 255, w32 = W == 1 && g2.n <= 32;
+            const int key =
+                (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
+                (pk ? 1 : 0);
+            const double wt = (double)g1.n *
+                              (double)std::min<long long>(kp, 1 + (long long)g2.n * g1.n) *
+                              (double)(g2.n + 1);
+            int q = wt < 1.0 ? 0 : (int)(std::log2(wt) * 16.0);
+            q = std::min(std::max(q, 0), kBuckets - 1);
+            const int bk = kBuckets - 1 - q;   // heavier first
+            pkey[p] = (uint8_t)key;
+            pbk[p] = (uint16_t)bk;
+            ++C.hist[(size_t)key * kBuckets + bk];
+            KeyClass &kc = C.key[key];
+            if (kc.first == INT_MAX) {
+                kc.first = p;
+                kc.W = (int8_t)W;
+                kc.wide = (int8_t)wide;
+                kc.w32 = (int8_t)w32;
+                kc.pk = (int8_t)pk;
+            }
+            kc.n1max = std::max(kc.n1max, g1.n);
+            kc.m1max = std::max(kc.m1max, g1.m);
+            kc.n2max = std::max(kc.n2max, g2.n);
+            kc.kmax = std::max(kc.kmax, kp);
+            kc.bmin = std::min(kc.bmin, bk);
+            kc.bmax = std::max(kc.bmax, bk);
+            C.maps += g1.n;
         }
     });
     if (ferr.idx != INT64_MAX) return ferr.report();
-    for (int p = 0; p < np; ++p) {
-        const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
-        const int kp = kpp ? kpp[p] : K;
-        b.map_off[p] = mtot;
-        mtot += g1.n;
-        const int W = pcls[p].W;
-        const bool wide = pcls[p].wide, w32 = pcls[p].w32, pk = pcls[p].pk;
-        const int key =
-            (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
-            (pk ? 1 : 0);
-        if (cls_of[key] < 0) {
-            cls_of[key] = (int)b.classes.size();
-            ClassPlan cp;
-            cp.W = W;
-            cp.wide = wide || W >= 8;
-            cp.w32 = w32;
-            cp.pk = pk;
-            b.classes.push_back(cp);
+    // combine: classes in order of first appearance, their statistics, and the output position
+    // of every (chunk, class, bucket) run: buckets ascending, then chunks, then pair order
+    int cls_of[kKeys];
+    {
+        KeyClass all[kKeys];
+        for (const PairChunk &C : pcs)
+            for (int k = 0; k < kKeys; ++k) {
+                const KeyClass &x = C.key[k];
+                if (x.first == INT_MAX) continue;
+                KeyClass &y = all[k];
+                if (x.first < y.first) {
+                    y.first = x.first;
+                    y.W = x.W;
+                    y.wide = x.wide;
+                    y.w32 = x.w32;
+                    y.pk = x.pk;
+                }
+                y.n1max = std::max(y.n1max, x.n1max);
+                y.m1max = std::max(y.m1max, x.m1max);
+                y.n2max = std::max(y.n2max, x.n2max);
+                y.kmax = std::max(y.kmax, x.kmax);
+                y.bmin = std::min(y.bmin, x.bmin);
+                y.bmax = std::max(y.bmax, x.bmax);
+            }
+        int keys[kKeys], nk = 0;
+        for (int k = 0; k < kKeys; ++k) {
+            cls_of[k] = -1;
+            if (all[k].first != INT_MAX) keys[nk++] = k;
         }
-        ClassPlan &cp = b.classes[cls_of[key]];
-        cp.n1max = std::max(cp.n1max, g1.n);
-        cp.m1max = std::max(cp.m1max, g1.m);
-        cp.n2max = std::max(cp.n2max, g2.n);
-        cp.kmax = std::max(cp.kmax, kp);
-        cp.order.push_back(p);
+        std::sort(keys, keys + nk, [&](int x, int y) { return all[x].first < all[y].first; });
+        for (int ci = 0; ci < nk; ++ci) {
+            const int k = keys[ci];
+            const KeyClass &y = all[k];
+            cls_of[k] = ci;
+            ClassPlan cp;
+            cp.W = y.W;
+            cp.wide = y.wide || y.W >= 8;
+            cp.w32 = y.w32;
+            cp.pk = y.pk;
+            cp.n1max = y.n1max;
+            cp.m1max = y.m1max;
+            cp.n2max = y.n2max;
+            cp.kmax = y.kmax;
+            int32_t run = 0;
+            for (int bk = y.bmin; bk <= y.bmax; ++bk)
+                for (PairChunk &C : pcs) {
+                    int32_t &slot = C.hist[(size_t)k * kBuckets + bk];
+                    const int32_t cnt = slot;
+                    slot = run;
+                    run += cnt;
+                }
+            cp.order.resize((size_t)run);
+            b.classes.push_back(std::move(cp));
+        }
+    }
+    int64_t mtot = 0;
+    for (PairChunk &C : pcs) {
+        const int64_t t = C.maps;
+        C.maps = mtot;
+        mtot += t;
     }
     b.map_total = mtot;
-    if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
-        b.perm.assign((size_t)mtot, 0);
-        const int ng0 = (int)ro.copy_of.size();
-        for (int p = 0; p < np; ++p) {
-            const int c = pl->pairs[2 * p] - ng0;
-            if (c < 0) continue;   // no copy: the source graph fails validation below
-            std::copy(ro.perm[c].begin(), ro.perm[c].end(), b.perm.begin() + b.map_off[p]);
-        }
-    }
-    // heaviest pairs first inside each class (longest-processing-time order, which only
-    // shortens the tail: results do not depend on the order). Work estimate
-    // n1 * min(K, n1 n2 + 1) * (n2 + 1), bucketed at 1/16 of a power of two and counting-
-    // sorted (descending bucket, then pair index); classes in parallel.
-    pool.parallel_for((int64_t)b.classes.size(), 1, [&](int64_t lo, int64_t hi) {
-        constexpr int kBuckets = 64 * 16;
-        for (int64_t ci = lo; ci < hi; ++ci) {
-            ClassPlan &cp = b.classes[ci];
-            const size_t n = cp.order.size();
-            std::vector<uint16_t> bk(n);
-            std::vector<int> cnt(kBuckets + 1, 0);
-            for (size_t k = 0; k < n; ++k) {
-                const int p = cp.order[k];
-                const GraphMeta &g1 = b.meta[pl->pairs[2 * p]], &g2 = b.meta[pl->pairs[2 * p + 1]];
-                const long long kp = kpp ? kpp[p] : K;
-                const double wt = (double)g1.n *
-                                  (double)std::min<long long>(kp, 1 + (long long)g2.n * g1.n) *
-                                  (double)(g2.n + 1);
-                int q = wt < 1.0 ? 0 : (int)(std::log2(wt) * 16.0);
-                q = std::min(std::max(q, 0), kBuckets - 1);
-                bk[k] = (uint16_t)(kBuckets - 1 - q);   // heavier first
-                ++cnt[bk[k] + 1];
-            }
-            for (int q = 0; q < kBuckets; ++q) cnt[q + 1] += cnt[q];
-            std::vector<int32_t> out(n);
-            for (size_t k = 0; k < n; ++k) out[cnt[bk[k]]++] = cp.order[k];
-            cp.order.swap(out);
-        }
-    });
     for (auto &cp : b.classes) {
         int rc = tune_class(h, cp, B, opt.block_threads);
         if (rc) return rc;
@@ -913,9 +980,12 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     b.woff_queue = w;  w = align_up(w + 4 * ((size_t)np + kMaxClasses), 256);
     b.woff_pool = w;   w = align_up(w + 8 * (size_t)(b.adj_words + b.plane_words), 256);
     size_t scratch = 0;
+    int64_t q = 0;
     for (auto &cp : b.classes) {
         cp.scratch_off = scratch;
         scratch += align_up((size_t)cp.lay.slice_bytes * (size_t)(cp.grid / cp.cluster), 256);
+        cp.order_off = q;
+        q += (int64_t)cp.order.size();
     }
     b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
     b.work_bytes = w;
@@ -923,45 +993,80 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     int rc = h->pin.ensure(std::max<size_t>(std::max(b.in_bytes, b.out_bytes), 256));
     if (rc) return rc;
     uint8_t *S = (uint8_t *)h->pin.p;
-    memcpy(S + b.off_meta, b.meta.data(), sizeof(GraphMeta) * (size_t)ng);
+    GraphMeta *smeta = (GraphMeta *)(S + b.off_meta);
     int32_t *vl = (int32_t *)(S + b.off_vlab);
     int32_t *ed = (int32_t *)(S + b.off_edges);
     int32_t *el = (int32_t *)(S + b.off_elab);
-    pool.parallel_for(ng, 1024, [&](int64_t lo, int64_t hi) {
-        for (int g = (int)lo; g < (int)hi; ++g) {
-            const fastged_graph &G = pl->graphs[g];
-            const GraphMeta &M = b.meta[g];
-            if (G.n) memcpy(vl + M.lab_off, G.vlabel, 4 * (size_t)G.n);
-            int32_t *dst = ed + 2 * M.edge_off;
-            bool bad = false;
-            for (int k = 0; k < G.m; ++k) {
-                const int u = G.edges[2 * k], v = G.edges[2 * k + 1];
-                if (u < 0 || v < 0 || u >= G.n || v >= G.n || u == v) { bad = true; break; }
-                dst[2 * k] = u;
-                dst[2 * k + 1] = v;
+    int32_t *sord = (int32_t *)(S + b.off_order);
+    int64_t *smo = (int64_t *)(S + b.off_mapoff);
+    // one pass over every chunk: a pair chunk places its pairs in their class order and sets
+    // their map offsets; a graph chunk sets the pool offsets of its graphs and stages their
+    // labels and edges (checking every endpoint)
+    pool.parallel_for((int64_t)npc + ngc, 1, [&](int64_t lo, int64_t hi) {
+        for (int64_t u = lo; u < hi; ++u) {
+            if (u < npc) {
+                PairChunk &C = pcs[u];
+                int64_t mo = C.maps;
+                const int p1 = (int)std::min<int64_t>(np, (u + 1) * pch);
+                for (int p = (int)(u * pch); p < p1; ++p) {
+                    b.map_off[p] = mo;
+                    smo[p] = mo;
+                    mo += b.meta[pl->pairs[2 * p]].n;
+                    const int key = pkey[p];
+                    ClassPlan &cp = b.classes[cls_of[key]];
+                    const int32_t pos = C.hist[(size_t)key * kBuckets + pbk[p]]++;
+                    cp.order[pos] = p;
+                    sord[cp.order_off + pos] = p;
+                }
+                continue;
             }
-            if (bad) {
-                ferr.put(g, "graph " + std::to_string(g) + ": bad edge endpoint or self-loop");
-                break;
-            }
-            if (b.labelled) {
-                if (G.elabel) memcpy(el + M.edge_off, G.elabel, 4 * (size_t)G.m);
-                else memset(el + M.edge_off, 0, 4 * (size_t)G.m);
+            const int64_t gi = u - npc;
+            const GraphChunk &C = gcs[gi];
+            int64_t lab = C.nv, eo = C.ne, aw = C.adjw;
+            const int g1 = (int)std::min<int64_t>(ng, (gi + 1) * gch);
+            for (int g = (int)(gi * gch); g < g1; ++g) {
+                const fastged_graph &G = pl->graphs[g];
+                GraphMeta &M = b.meta[g];
+                M.lab_off = lab;
+                M.edge_off = eo;
+                M.adj_off = aw;
+                M.plane_off = aw * B;
+                lab += M.n;
+                eo += M.m;
+                aw += (int64_t)M.n * M.W;
+                smeta[g] = M;
+                if (G.n) memcpy(vl + M.lab_off, G.vlabel, 4 * (size_t)G.n);
+                int32_t *dst = ed + 2 * M.edge_off;
+                const unsigned n = (unsigned)G.n;
+                bool bad = false;
+                for (int k = 0; k < G.m; ++k) {
+                    const int32_t x = G.edges[2 * k], y = G.edges[2 * k + 1];
+                    bad |= ((unsigned)x >= n) | ((unsigned)y >= n) | (x == y);
+                    dst[2 * k] = x;
+                    dst[2 * k + 1] = y;
+                }
+                if (bad) {
+                    ferr.put(g, "graph " + std::to_string(g) + ": bad edge endpoint or self-loop");
+                    break;
+                }
+                if (b.labelled) {
+                    if (G.elabel) memcpy(el + M.edge_off, G.elabel, 4 * (size_t)G.m);
+                    else memset(el + M.edge_off, 0, 4 * (size_t)G.m);
+                }
             }
         }
     });
     if (ferr.idx != INT64_MAX) return ferr.report();
-    memcpy(S + b.off_pairs, pl->pairs, 8 * (size_t)np);
-    {
-        int32_t *ord = (int32_t *)(S + b.off_order);
-        int64_t q = 0;
-        for (auto &cp : b.classes) {
-            cp.order_off = q;
-            memcpy(ord + q, cp.order.data(), 4 * cp.order.size());
-            q += (int64_t)cp.order.size();
+    if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
+        b.perm.assign((size_t)mtot, 0);
+        const int ng0 = (int)ro.copy_of.size();
+        for (int p = 0; p < np; ++p) {
+            const int cc = pl->pairs[2 * p] - ng0;
+            if (cc < 0) continue;   // no copy: the source graph fails validation above
+            std::copy(ro.perm[cc].begin(), ro.perm[cc].end(), b.perm.begin() + b.map_off[p]);
         }
     }
-    memcpy(S + b.off_mapoff, b.map_off.data(), 8 * (size_t)np);
+    memcpy(S + b.off_pairs, pl->pairs, 8 * (size_t)np);
     if (kpp) memcpy(S + b.off_kpp, kpp, 4 * (size_t)np);
 
     return FASTGED_OK;
