@@ -363,6 +363,47 @@ def test_invalid_inputs():
             fg.run(single([(g, h)], big_cost, 4))
 
 
+def test_invalid_entries_across_a_large_batch_report_the_lowest_index():
+    """Graphs and pairs are validated in parallel chunks: with several invalid entries spread
+    over a 12,000-pair batch, the error names the lowest invalid graph (graph checks come
+    first, then pair checks, then edge endpoints), and the handle stays usable."""
+    w = W.config2(12000)
+    cases = []
+    # pairs: graph index out of range at 9000 and 7001, per-pair K out of range at 8000
+    pairs = w.pairs.copy()
+    pairs[9000, 1] = 10 ** 6
+    pairs[7001, 0] = -1
+    cases.append((pairs, None, None, "pair 7001: graph index out of range"))
+    kpp = np.full(w.n_pairs, 50, np.int32)
+    kpp[11000], kpp[8000] = 0, 101
+    cases.append((w.pairs, kpp, None, "pair 8000: per-pair K out of range"))
+    # edge labels out of range in graphs 18000 and 17000
+    mm0 = F.Marshalled(w.graphs, w.pairs)
+    el = mm0.el.copy()
+    el[int(mm0.m[:18000].sum())] = 99
+    el[int(mm0.m[:17000].sum())] = -3
+    cases.append((w.pairs, None, ("el", el), "graph 17000: edge label out of range"))
+    # a bad endpoint in graph 20001 and a self-loop in graph 15000
+    ed = mm0.ed.copy()
+    ed[2 * int(mm0.m[:20001].sum()) + 1] = 9999
+    e0 = 2 * int(mm0.m[:15000].sum())
+    ed[e0] = ed[e0 + 1]
+    cases.append((w.pairs, None, ("ed", ed), "graph 15000: bad edge endpoint or self-loop"))
+    with F.FastGED(w.cost) as fg:
+        for pairs, kpp, patch, msg in cases:
+            mm = F.Marshalled(w.graphs, pairs.copy())
+            if patch is not None:
+                getattr(mm, patch[0])[:] = patch[1]
+            cost, maps, nev = F._outputs(mm)
+            K = 100
+            with pytest.raises(F.FastGEDError) as ei:
+                F.fastged_batch_ex(fg.h, mm, K, F.make_options(k_per_pair=kpp), cost, maps, nev)
+            assert ei.value.code == F.FASTGED_ERR_INVALID_ARG
+            assert msg in str(ei.value)
+        ws = W.subset(w, range(200))
+        assert_parity(ws, fg.run(ws), idx=list(range(0, 200, 20)))
+
+
 @pytest.mark.parametrize("cfg", ["config1", "config2", "config3"])
 def test_variant_b_complete_every_last_level_successor(cfg):
     n = {"config1": 200, "config2": 150, "config3": 6}[cfg]
