@@ -430,7 +430,8 @@ class Server:
                                              int(K), int(tag))
 
     def poll(self, max_results: int = 4096, map_cap: int = 1 << 20, timeout_ms: int = 10):
-        """[(tag, status, cost, map, n_evals, latency_ms, queue_ms)] of finished queries."""
+        """[(tag, status, cost, map, n_evals, latency_ms, queue_ms)] of finished queries (the
+        map is empty for a query that failed)."""
         out = (ServeResult * max_results)()
         buf = np.zeros(map_cap, np.int32)
         n = self.lib.fastged_serve_poll(self.s, out, max_results, buf.ctypes.data, map_cap,
@@ -439,7 +440,9 @@ class Server:
             _check(self.lib, n)
         res = []
         for r in out[:n]:
-            mp = buf[r.map_offset:r.map_offset + r.n1].copy()
+            # a failed query has no map in the buffer
+            mp = (buf[r.map_offset:r.map_offset + r.n1].copy() if r.status == FASTGED_OK
+                  else np.zeros(0, np.int32))
             res.append((r.tag, r.status, r.cost, mp, r.n_evals, r.latency_ms, r.queue_ms))
         return res
 

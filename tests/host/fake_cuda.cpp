@@ -1,12 +1,22 @@
 // Test infrastructure: host-only fakes of the CUDA runtime calls and of the kernel-side
-// entry points that the host runtime (fastged_runtime.cu) references, so that its host logic
-// (validation, size classes, pair order, staging layout, memory caps, error paths) can be
-// exercised on a machine without a GPU. Nothing here launches or imitates a kernel: launches
-// succeed without doing anything, and the tests only read what the host side produced.
+// entry points that the host runtime (fastged_runtime.cu, serve.cu) references, so that its
+// host logic (validation, size classes, pair order, staging layout, memory caps, the serving
+// dispatcher, error paths) can be exercised on a machine without a GPU. Nothing here launches
+// or imitates a kernel: launches succeed without doing anything, device-to-host copies deliver
+// zeros (an all-clear status word and zero results), and host functions enqueued on a stream
+// run on one executor thread after a configurable delay, the time a batch would take.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
 
 #include "fastged_internal.h"
 #include "fastged_runtime.h"
@@ -16,6 +26,50 @@ static int g_fail_pinned = 0;                       // next cudaMallocHost calls
 
 extern "C" void fake_set_free_bytes(unsigned long long b) { g_free_bytes = (size_t)b; }
 extern "C" void fake_fail_pinned_alloc(int n) { g_fail_pinned = n; }
+
+namespace {
+// Host functions of every fake stream, run in enqueue order by one thread, each no earlier
+// than `delay_us` after it was enqueued; a stream is idle when none of its host functions is
+// queued or running. Created on first use and never destroyed (its thread is detached).
+struct HostFnQueue {
+    struct Item {
+        cudaStream_t s;
+        cudaHostFn_t fn;
+        void *arg;
+        std::chrono::steady_clock::time_point due;
+    };
+    std::mutex mu;
+    std::condition_variable cv, idle_cv;
+    std::deque<Item> q;
+    std::map<cudaStream_t, int> busy;   // host functions queued or running, per stream
+    std::atomic<int> delay_us{0};
+
+    HostFnQueue() { std::thread([this] { run(); }).detach(); }
+    void run()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return !q.empty(); });
+            const Item it = q.front();   // only this thread removes items
+            lk.unlock();
+            std::this_thread::sleep_until(it.due);
+            it.fn(it.arg);
+            lk.lock();
+            q.pop_front();
+            if (--busy[it.s] == 0) busy.erase(it.s);
+            idle_cv.notify_all();
+        }
+    }
+};
+HostFnQueue &host_fns()
+{
+    static HostFnQueue *h = new HostFnQueue();
+    return *h;
+}
+std::atomic<intptr_t> g_next_stream{1};
+}  // namespace
+
+extern "C" void fake_set_host_fn_delay_us(int us) { host_fns().delay_us.store(us); }
 
 extern "C" {
 cudaError_t cudaMallocHost(void **p, size_t n)
@@ -49,9 +103,26 @@ cudaError_t cudaMemGetInfo(size_t *f, size_t *t)
     *t = (size_t)280 << 30;
     return cudaSuccess;
 }
-cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int)
+cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int)
 {
-    *v = 0;
+    // a GB300: 152 SMs, 227 KB of shared memory per block, 228 KB per SM
+    *v = a == cudaDevAttrMultiProcessorCount              ? 152
+         : a == cudaDevAttrMaxSharedMemoryPerBlockOptin    ? 232448
+         : a == cudaDevAttrMaxSharedMemoryPerMultiprocessor ? 233472
+                                                            : 0;
+    return cudaSuccess;
+}
+cudaError_t cudaSetDevice(int) { return cudaSuccess; }
+cudaError_t cudaLaunchHostFunc(cudaStream_t s, cudaHostFn_t fn, void *arg)
+{
+    HostFnQueue &h = host_fns();
+    {
+        std::lock_guard<std::mutex> g(h.mu);
+        h.q.push_back({s, fn, arg,
+                       std::chrono::steady_clock::now() + std::chrono::microseconds(h.delay_us.load())});
+        ++h.busy[s];
+    }
+    h.cv.notify_all();
     return cudaSuccess;
 }
 cudaError_t cudaGetDevice(int *d)
@@ -76,14 +147,32 @@ cudaError_t cudaGraphDestroy(cudaGraph_t) { return cudaSuccess; }
 cudaError_t cudaGraphExecDestroy(cudaGraphExec_t) { return cudaSuccess; }
 cudaError_t cudaGraphInstantiate(cudaGraphExec_t *g, cudaGraph_t, unsigned long long) { *g = nullptr; return cudaSuccess; }
 cudaError_t cudaGraphLaunch(cudaGraphExec_t, cudaStream_t) { return cudaSuccess; }
-cudaError_t cudaMemcpy(void *, const void *, size_t, cudaMemcpyKind) { return cudaSuccess; }
-cudaError_t cudaMemcpyAsync(void *, const void *, size_t, cudaMemcpyKind, cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaMemcpy(void *dst, const void *, size_t n, cudaMemcpyKind k)
+{
+    if (k == cudaMemcpyDeviceToHost) memset(dst, 0, n);
+    return cudaSuccess;
+}
+cudaError_t cudaMemcpyAsync(void *dst, const void *, size_t n, cudaMemcpyKind k, cudaStream_t)
+{
+    if (k == cudaMemcpyDeviceToHost) memset(dst, 0, n);
+    return cudaSuccess;
+}
 cudaError_t cudaMemsetAsync(void *, int, size_t, cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaStreamBeginCapture(cudaStream_t, cudaStreamCaptureMode) { return cudaSuccess; }
-cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned int) { *s = nullptr; return cudaSuccess; }
+cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned int)
+{
+    *s = reinterpret_cast<cudaStream_t>(16 * g_next_stream.fetch_add(1));
+    return cudaSuccess;
+}
 cudaError_t cudaStreamDestroy(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t *g) { *g = nullptr; return cudaSuccess; }
-cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaStreamSynchronize(cudaStream_t s)
+{
+    HostFnQueue &h = host_fns();
+    std::unique_lock<std::mutex> lk(h.mu);
+    h.idle_cv.wait(lk, [&] { return h.busy.find(s) == h.busy.end(); });
+    return cudaSuccess;
+}
 cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { return cudaSuccess; }
 }
 
@@ -91,7 +180,14 @@ cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { retur
 // the real library has them (two-word classes with narrow maps, wide-map classes of four or
 // more words)
 namespace fastged {
-cudaError_t launch_pack(const PackParams &, int, cudaStream_t) { return cudaSuccess; }
+static std::atomic<int> g_max_pack_graphs{0};   // most graphs one batch packed
+cudaError_t launch_pack(const PackParams &, int n_graphs, cudaStream_t)
+{
+    int m = g_max_pack_graphs.load();
+    while (n_graphs > m && !g_max_pack_graphs.compare_exchange_weak(m, n_graphs)) {
+    }
+    return cudaSuccess;
+}
 cudaError_t launch_kbest(int, bool, bool, bool, int, const KParams &, int, int, size_t, cudaStream_t)
 {
     return cudaSuccess;
@@ -118,3 +214,9 @@ bool kbest_has_cluster_variant(int W, bool wide, bool w32)
 size_t team_shared_static_bytes() { return 2048; }
 size_t team_shared_cluster_bytes() { return 4096; }
 }  // namespace fastged
+
+// the most graphs one batch has packed since the last reset
+extern "C" int fake_max_pack_graphs(int reset)
+{
+    return reset ? fastged::g_max_pack_graphs.exchange(0) : fastged::g_max_pack_graphs.load();
+}

@@ -1,7 +1,7 @@
 """Host logic of the batch flattening, on the CPU.
 
 The host runtime (paper_2605_00830_gb300/csrc/fastged_runtime.cu) holds no device code; here it
-is built with g++ against fakes of the CUDA calls it makes (tests/host/fake_cuda.cpp), and what
+is built with g++ against fakes of the CUDA calls it makes (tests/host_probe.py), and what
 its flattening produces for a batch -- validation errors, size classes, the heaviest-first
 pair order, the graph table, the map offsets, the staging bytes, the cap on resident teams --
 is checked against plain Python restatements of the same rules. The batches span many of the
@@ -9,8 +9,6 @@ chunks the flattening works in, so the parallel passes and their combination are
 """
 import ctypes
 import math
-import os
-import subprocess
 
 import numpy as np
 import pytest
@@ -19,14 +17,7 @@ from oracle import oracle as O
 from paper_2605_00830_gb300 import fastged as F
 from paper_2605_00830_gb300 import workloads as W
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-HOST = os.path.join(HERE, "host")
-CSRC = os.path.join(ROOT, "paper_2605_00830_gb300", "csrc")
-INCLUDE = os.path.join(ROOT, "include")
-RUNTIME = os.path.join(CSRC, "fastged_runtime.cu")
-SOURCES = [os.path.join(HOST, "fake_cuda.cpp"), os.path.join(HOST, "flatten_probe.cpp")]
-LIB = os.path.join(HOST, "_build", "libflatten_probe.so")
+from host_probe import load
 
 META_DTYPE = np.dtype([("n", "<i4"), ("m", "<i4"), ("W", "<i4"), ("pad", "<i4"),
                        ("adj_off", "<i8"), ("plane_off", "<i8"), ("lab_off", "<i8"),
@@ -39,41 +30,9 @@ CLASS_FIELDS = ("W wide w32 pk cluster n1max n2max m1max kmax n_order order_off 
                 "slice_bytes scratch_off smem_bytes").split()
 
 
-def _build():
-    deps = [RUNTIME] + SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
-                                  if f.endswith((".h", ".cuh"))]
-    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    if os.path.exists(LIB) and all(os.path.getmtime(d) <= os.path.getmtime(LIB) for d in deps):
-        return
-    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
-    if not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
-        pytest.skip("CUDA headers not found")
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    # -Bsymbolic: the runtime's calls bind to the fakes in this library even when a real
-    # CUDA runtime is loaded globally in the process (torch)
-    cmd = (["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-Wl,-Bsymbolic",
-            "-I", cuda_inc, "-I", INCLUDE, "-I", CSRC, "-x", "c++", RUNTIME, "-x", "c++"]
-           + SOURCES + ["-o", tmp, "-lpthread", "-ldl"])
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
-    os.replace(tmp, LIB)
-
-
 @pytest.fixture(scope="module")
 def lib():
-    _build()
-    L = ctypes.CDLL(LIB)
-    L.probe_flatten.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
-    L.probe_error.restype = ctypes.c_char_p
-    L.probe_staging.restype = ctypes.c_void_p
-    L.fake_set_free_bytes.argtypes = [ctypes.c_ulonglong]
-    L.fastged_inject_fault.argtypes = [ctypes.c_int, ctypes.c_int]
-    L.probe_batch.argtypes = [ctypes.c_void_p]
-    L.probe_class.argtypes = [ctypes.c_int, ctypes.c_void_p]
-    L.probe_class_order.argtypes = [ctypes.c_int, ctypes.c_void_p]
-    for name in ("probe_meta", "probe_map_off", "probe_perm"):
-        getattr(L, name).argtypes = [ctypes.c_void_p]
+    L = load()
     yield L
     L.fake_set_free_bytes(250 << 30)
 
