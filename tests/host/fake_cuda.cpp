@@ -71,6 +71,36 @@ std::atomic<intptr_t> g_next_stream{1};
 
 extern "C" void fake_set_host_fn_delay_us(int us) { host_fns().delay_us.store(us); }
 
+// The team shape of the last K-Best launch, the elapsed time an event pair reports for each
+// shape (set by the test; 0 ms for shapes not set), and how many K-Best launches were made.
+static std::mutex g_shape_mu;
+static std::map<std::pair<int, int>, float> g_shape_ms;
+static std::pair<int, int> g_last_shape{0, 1};
+static std::atomic<long long> g_kbest_launches{0};
+static void note_launch(int block, int cluster)
+{
+    std::lock_guard<std::mutex> g(g_shape_mu);
+    g_last_shape = {block, cluster};
+    ++g_kbest_launches;
+}
+extern "C" void fake_set_shape_ms(int block, int cluster, float ms)
+{
+    std::lock_guard<std::mutex> g(g_shape_mu);
+    if (block == 0) g_shape_ms.clear();
+    else g_shape_ms[{block, cluster}] = ms;
+}
+extern "C" long long fake_kbest_launches() { return g_kbest_launches.load(); }
+
+// Events report "not ready" until this time: a batch that takes longer than a handle's
+// timeout.
+static std::atomic<long long> g_events_ready_at_us{0};
+static long long now_us()
+{
+    return std::chrono::duration_cast<std::chrono::microseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+extern "C" void fake_events_busy_for_ms(int ms) { g_events_ready_at_us.store(now_us() + 1000LL * ms); }
+
 extern "C" {
 cudaError_t cudaMallocHost(void **p, size_t n)
 {
@@ -138,8 +168,17 @@ const char *cudaGetErrorString(cudaError_t e)
 cudaError_t cudaEventCreate(cudaEvent_t *e) { *e = nullptr; return cudaSuccess; }
 cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned int) { *e = nullptr; return cudaSuccess; }
 cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
-cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t) { *ms = 0.f; return cudaSuccess; }
-cudaError_t cudaEventQuery(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t)
+{
+    std::lock_guard<std::mutex> g(g_shape_mu);
+    auto it = g_shape_ms.find(g_last_shape);
+    *ms = it == g_shape_ms.end() ? 0.f : it->second;
+    return cudaSuccess;
+}
+cudaError_t cudaEventQuery(cudaEvent_t)
+{
+    return now_us() < g_events_ready_at_us.load() ? cudaErrorNotReady : cudaSuccess;
+}
 cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaEventRecordWithFlags(cudaEvent_t, cudaStream_t, unsigned int) { return cudaSuccess; }
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
@@ -188,12 +227,16 @@ cudaError_t launch_pack(const PackParams &, int n_graphs, cudaStream_t)
     }
     return cudaSuccess;
 }
-cudaError_t launch_kbest(int, bool, bool, bool, int, const KParams &, int, int, size_t, cudaStream_t)
+cudaError_t launch_kbest(int, bool, bool, bool, int, const KParams &, int, int block, size_t,
+                         cudaStream_t)
 {
+    note_launch(block, 1);
     return cudaSuccess;
 }
-cudaError_t launch_kbest_cluster(int, int, const KParams &, int, int, size_t, int, cudaStream_t)
+cudaError_t launch_kbest_cluster(int, int, const KParams &, int, int block, size_t, int cluster,
+                                 cudaStream_t)
 {
+    note_launch(block, cluster);
     return cudaSuccess;
 }
 cudaError_t kbest_occupancy(int, bool, bool, bool, int, int, size_t, int *out)

@@ -56,6 +56,21 @@ def load():
     L.fake_fail_pinned_alloc.argtypes = [ctypes.c_int]
     L.fake_set_host_fn_delay_us.argtypes = [ctypes.c_int]
     L.fake_max_pack_graphs.argtypes = [ctypes.c_int]
+    L.fake_set_shape_ms.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_float]
+    L.fake_kbest_launches.restype = ctypes.c_longlong
+    L.fake_events_busy_for_ms.argtypes = [ctypes.c_int]
+    L.fastged_create.argtypes = [ctypes.POINTER(F.CostModel), ctypes.POINTER(vp)]
+    L.fastged_destroy.argtypes = [vp]
+    L.fastged_destroy.restype = None
+    L.fastged_batch_ex.argtypes = [vp, ctypes.POINTER(F.PairList), i32, ctypes.POINTER(F.Options),
+                                   vp, vp, vp]
+    L.fastged_set_timeout.argtypes = [vp, i32]
+    L.fastged_plan_create.argtypes = [vp, ctypes.POINTER(F.PairList), i32,
+                                      ctypes.POINTER(F.Options), ctypes.POINTER(vp)]
+    L.fastged_plan_info.argtypes = [vp, ctypes.POINTER(F.PlanStats)]
+    L.fastged_plan_destroy.argtypes = [vp]
+    L.fastged_plan_destroy.restype = None
+    L.fastged_autotune_clear.restype = None
     L.fastged_inject_fault.argtypes = [i32, i32]
     L.fastged_last_error.argtypes = [vp]
     L.fastged_last_error.restype = ctypes.c_char_p
