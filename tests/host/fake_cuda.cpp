@@ -184,7 +184,12 @@ cudaError_t cudaEventRecordWithFlags(cudaEvent_t, cudaStream_t, unsigned int) { 
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaGraphDestroy(cudaGraph_t) { return cudaSuccess; }
 cudaError_t cudaGraphExecDestroy(cudaGraphExec_t) { return cudaSuccess; }
-cudaError_t cudaGraphInstantiate(cudaGraphExec_t *g, cudaGraph_t, unsigned long long) { *g = nullptr; return cudaSuccess; }
+static char g_fake_graph[16];   // graph and executable handles: one non-null token
+cudaError_t cudaGraphInstantiate(cudaGraphExec_t *g, cudaGraph_t, unsigned long long)
+{
+    *g = reinterpret_cast<cudaGraphExec_t>(g_fake_graph);
+    return cudaSuccess;
+}
 cudaError_t cudaGraphLaunch(cudaGraphExec_t, cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaMemcpy(void *dst, const void *, size_t n, cudaMemcpyKind k)
 {
@@ -204,7 +209,11 @@ cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned int)
     return cudaSuccess;
 }
 cudaError_t cudaStreamDestroy(cudaStream_t) { return cudaSuccess; }
-cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t *g) { *g = nullptr; return cudaSuccess; }
+cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t *g)
+{
+    *g = reinterpret_cast<cudaGraph_t>(g_fake_graph);
+    return cudaSuccess;
+}
 cudaError_t cudaStreamSynchronize(cudaStream_t s)
 {
     HostFnQueue &h = host_fns();
