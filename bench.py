@@ -9,11 +9,13 @@ packing, every K-Best level of every pair, leaf completion and argmin.
   value      pairs/s with the batch resident in HBM (device-resident plan replayed as a
              CUDA graph), CUDA events on the launching stream, L2 flushed between steps
   e2e        the same metric through fastged_batch_ex with host inputs and outputs
-             (flattening, host-to-device copy, kernels, device-to-host copy)
+             (flattening, host-to-device copy, kernels, device-to-host copy), on every rank,
+             max over ranks
   roofline   the K-Best kernel's integer ops per launch / its event-timed duration,
              against the measured LOP3/IADD rate of this GPU (the path is ALU bound)
   plain_form the same arithmetic launched once per pair on one stream (a bounded sample)
-  cpu_baseline  the CPU oracle on a bounded sample, on every host core
+  cpu_baseline  the CPU oracle on a bounded sample, on every host core (and on one core);
+             one-GPU runs only
 
 --impl reference times the CPU oracle (the only reference this method has) on the same
 metric and workload, one bounded sample per step.
@@ -27,7 +29,6 @@ import json
 import os
 import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -156,16 +157,23 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.lines = []
+        self.reader = None
 
     def start(self):
+        import threading
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return
+        # a thread drains the pipe so that nvidia-smi never blocks on a full buffer
+        self.reader = threading.Thread(target=lambda: self.lines.extend(self.p.stdout),
+                                       daemon=True)
+        self.reader.start()
 
     def stop(self):
         if self.p is None:
@@ -176,10 +184,8 @@ class ClockSampler:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-        self.f.flush()
-        self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
-        os.unlink(self.f.name)
+        self.reader.join(timeout=5)
+        rows = [r.split(",") for r in self.lines if r.strip()]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -396,24 +402,29 @@ def ours(args):
                          "peak_source": "measured in-run: LOP3/IADD probe kernels (min of the two)",
                          "popc_peak": peak["popc"] / 1e12},
             "clocks": clk}
-    if rank == 0 and not args.no_extras:
-        # e2e through the public API with host buffers
+    if not args.no_extras:
+        # e2e through the public API with host buffers, on every rank (its own batch): the
+        # barrier and the max over ranks bracket it like the device-timed region
         cst, mp, nv = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
                        np.zeros(mm.n_pairs, np.int64))
         opt = F.make_options()
         F.fastged_batch_ex(g.h, mm, w.K, opt, cst, mp, nv)
-        e2e_t = 0.0
         n_e2e = max(1, min(args.steps, 5))
+        if ws > 1:
+            torch.distributed.barrier()
+        e2e_t = 0.0
         for _ in range(n_e2e):
             flush.zero_()
             torch.cuda.synchronize()
             t = time.perf_counter()
             F.fastged_batch_ex(g.h, mm, w.K, opt, cst, mp, nv)
             e2e_t += time.perf_counter() - t
+        e2e_t = max_over_ranks(e2e_t)
         assert np.array_equal(cst, c_out)
-        line["e2e"] = {"value": mm.n_pairs * n_e2e / e2e_t, "unit": UNIT,
+        line["e2e"] = {"value": mm.n_pairs * ws * n_e2e / e2e_t, "unit": UNIT,
                        "h2d_bytes_per_step": info["input_bytes"],
                        "d2h_bytes_per_step": info["output_bytes"], "steps": n_e2e}
+    if rank == 0 and not args.no_extras:
         # plain per-pair form on a bounded sample
         from paper_2605_00830_gb300 import workloads as W
         ws_ = W.subset(w, range(min(args.plain_sample, w.n_pairs)))
@@ -436,19 +447,20 @@ def ours(args):
         line["serve"] = serving_leg(args.serve_window)
         # the same stream at a load the GPU sustains (the 5,000 req/s stream saturates it)
         line["serve_sustained"] = serving_leg(args.serve_window, rate=1000.0)
+    if rank == 0 and ws == 1 and not args.no_extras:
         # CPU oracle on a bounded sample, all host cores
         threads = os.cpu_count() or 1
         idx = list(range(min(args.cpu_sample, w.n_pairs)))
         dt, _ = run_cpu_oracle(w, idx, threads)
         line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
-                                "sample": f"first {len(idx)} of the 20,000 pairs"}
+                                "sample": f"first {len(idx)} of the {w.n_pairs:,} pairs"}
         # and on one host core (a smaller sample)
         idx1 = list(range(min(max(args.cpu_sample // 16, 50), w.n_pairs)))
         dt1, _ = run_cpu_oracle(w, idx1, 1)
         line["cpu_baseline_1core"] = {"value": len(idx1) / dt1, "unit": UNIT, "cores": 1,
                                       "kind": "oracle",
-                                      "sample": f"first {len(idx1)} of the 20,000 pairs"}
+                                      "sample": f"first {len(idx1)} of the {w.n_pairs:,} pairs"}
     F.fastged_plan_destroy(plan)
     g.close()
     if rank == 0:
