@@ -220,7 +220,7 @@ typedef struct {
     uint64_t tag;              /* the caller's tag from fastged_serve_submit                */
     int32_t status;            /* FASTGED_OK or the error of the batch the query was in     */
     int32_t cost;              /* GED upper bound                                           */
-    int32_t n1;                /* entries of the vertex map                                 */
+    int32_t n1;                /* entries of the vertex map (0 if status is not FASTGED_OK) */
     int32_t pad;
     int64_t map_offset;        /* first entry of the map in the poll's map buffer           */
     int64_t n_evals;           /* successors scored plus leaves completed                   */
@@ -245,9 +245,10 @@ int fastged_serve_submit(fastged_server *s, const fastged_graph *g1, const fastg
                          int32_t K, uint64_t tag);
 
 /* Moves up to max_results finished queries into out[], their vertex maps into map_buf
- * (capacity map_cap entries; each result's map_offset points into it), waiting up to
- * timeout_ms for the first one. Returns the number of results (0 on timeout) or a negative
- * status (FASTGED_ERR_INVALID_ARG if even the first map does not fit). */
+ * (capacity map_cap entries; each result's map_offset points into it, n1 entries long; a
+ * failed query has n1 = 0 and no map), waiting up to timeout_ms for the first one. Returns
+ * the number of results (0 on timeout) or a negative status (FASTGED_ERR_INVALID_ARG if even
+ * the first map does not fit). */
 int fastged_serve_poll(fastged_server *s, fastged_serve_result *out, int32_t max_results,
                        int32_t *map_buf, int64_t map_cap, int32_t timeout_ms);
 

@@ -140,7 +140,7 @@ static void collect_lane(fastged_server *s, Lane &l)
         memset(&res.r, 0, sizeof(res.r));
         res.r.tag = q->tag;
         res.r.status = rc;
-        res.r.n1 = q->n[0];
+        res.r.n1 = rc == FASTGED_OK ? q->n[0] : 0;   // a failed query has no map
         res.r.latency_ms = ms_between(q->t_submit, now);
         res.r.queue_ms = ms_between(q->t_submit, l.t_launch);
         if (rc == FASTGED_OK) {
@@ -219,7 +219,7 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
             memset(&res.r, 0, sizeof(res.r));
             res.r.tag = q->tag;
             res.r.status = rc;
-            res.r.n1 = q->n[0];
+            res.r.n1 = 0;   // no map
             res.r.latency_ms = ms_between(q->t_submit, now);
             res.r.queue_ms = ms_between(q->t_submit, l.t_launch);
             s->done_q.push_back(std::move(res));

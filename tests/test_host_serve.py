@@ -165,7 +165,16 @@ def test_failed_launch_is_reported_for_its_queries(lib):
     lib.fastged_inject_fault(F.FASTGED_INJECT_LAUNCH, 1)   # the next batch fails to launch
     _submit_all(srv, mm, w, kk, range(w.n_pairs))
     srv.stop()                                              # flush the partial batches
-    got = _collect(srv, w.n_pairs)
+    # the raw C results: a failed query reports no map entries (n1 = 0)
+    out = (F.ServeResult * w.n_pairs)()
+    buf = np.zeros(1 << 16, np.int32)
+    n = lib.fastged_serve_poll(srv.s, out, w.n_pairs, buf.ctypes.data, buf.size, 100)
+    assert n == w.n_pairs
+    got = {}
+    for r in out[:n]:
+        a = int(w.pairs[r.tag][0])
+        assert r.n1 == (w.graphs[a].n if r.status == F.FASTGED_OK else 0)
+        got[r.tag] = (r.tag, r.status, r.cost, buf[r.map_offset:r.map_offset + r.n1])
     st = srv.stats()
     srv.close()
     assert sorted(got) == list(range(w.n_pairs))
