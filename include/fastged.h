@@ -54,7 +54,7 @@ extern "C" {
 #define FASTGED_ERR_BUSY        -5   /* serving: admission refused, request queue is full  */
 #define FASTGED_ERR_STOPPED     -6   /* serving: the server is stopped                      */
 
-/* limits of this build */
+/* limits of the library */
 #define FASTGED_MAX_N      1024      /* vertices per graph                                  */
 #define FASTGED_MAX_K      1048576   /* beam width (2^20)                                   */
 #define FASTGED_MAX_ELABEL 255       /* edge labels are 0..255                              */
