@@ -228,13 +228,14 @@ def serving_leg(window_s: float, rate: float = 5000.0):
     w = W.config5(duration_s=window_s, rate=rate, seed=5)
     mm = F.marshal(w)
     srv = F.Server(w.cost, F.serve_config())
-    lat, done, rejected = [], [0], [0]
+    lat, tags, done, rejected = [], [], [0], [0]
     stop = [False]
 
     def poller():
         while not stop[0] or done[0] < w.n_pairs - rejected[0]:
             for r in srv.poll(timeout_ms=20):
                 lat.append(r[5])
+                tags.append(int(r[0]))
                 done[0] += 1
             if stop[0] and done[0] >= w.n_pairs - rejected[0]:
                 break
@@ -254,13 +255,22 @@ def serving_leg(window_s: float, rate: float = 5000.0):
     t_end = time.perf_counter()
     st = srv.stats()
     srv.close()
+    shape = w.meta["shape"][np.array(tags, dtype=np.int64)] if tags else np.zeros(0, np.int32)
     lat = np.array(lat) if lat else np.zeros(1)
+    # latency per query shape: the small molecule-like queries and the large BA pairs apart
+    by_shape = {}
+    for code, name in ((0, "molecule"), (1, "dense"), (2, "ba")):
+        x = lat[:len(shape)][shape == code]
+        if x.size:
+            by_shape[name] = {"n": int(x.size), "p50_ms": float(np.percentile(x, 50)),
+                              "p99_ms": float(np.percentile(x, 99))}
     return {"workload": "Poisson stream, serving mix (70/25/5 % molecule-like / dense ER / BA), "
                         "K in {32,128,512}, setting-1 costs",
             "offered_rps": rate, "window_s": window_s, "requests": int(w.n_pairs),
             "completed": int(done[0]), "rejected": int(rejected[0]),
             "pairs_per_s": done[0] / (t_end - t0), "wall_s": t_end - t0,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "by_shape": by_shape,
             "batches": int(st["batches"]), "mean_batch": st["batched_pairs"] / max(1, st["batches"])}
 
 

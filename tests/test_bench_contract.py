@@ -143,7 +143,10 @@ def test_bench_line_has_every_contract_key(monkeypatch, capsys, fake_smi):
     assert d["clocks"]["sm_mhz"] == 2070.0 and d["clocks"]["reasons"] == ["sw_power_cap"]
     assert d["plain_form"]["sample_pairs"] == 40
     for leg in ("serve", "serve_sustained"):
-        assert {"p50_ms", "p99_ms", "completed", "offered_rps"} <= set(d[leg])
+        assert {"p50_ms", "p99_ms", "completed", "offered_rps", "by_shape"} <= set(d[leg])
+        shapes = d[leg]["by_shape"]
+        assert sum(v["n"] for v in shapes.values()) == d[leg]["completed"]
+        assert "molecule" in shapes and shapes["molecule"]["p50_ms"] == pytest.approx(3.0)
 
 
 def test_reference_arm_line(monkeypatch, capsys):
