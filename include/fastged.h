@@ -53,6 +53,7 @@ extern "C" {
 #define FASTGED_ERR_TIMEOUT     -4   /* a bounded wait ran out (serving / fault injection)  */
 #define FASTGED_ERR_BUSY        -5   /* serving: admission refused, request queue is full  */
 #define FASTGED_ERR_STOPPED     -6   /* serving: the server is stopped                      */
+#define FASTGED_ERR_CANCELLED   -7   /* serving: the query was cancelled before it ran      */
 
 /* limits of the library */
 #define FASTGED_MAX_N      1024      /* vertices per graph                                  */
@@ -252,7 +253,15 @@ int fastged_serve_submit(fastged_server *s, const fastged_graph *g1, const fastg
 int fastged_serve_poll(fastged_server *s, fastged_serve_result *out, int32_t max_results,
                        int32_t *map_buf, int64_t map_cap, int32_t timeout_ms);
 
-/* Counters of the server so far. */
+/* Cancels every query with this tag that is still queued (not yet in a batch): each comes
+ * back through fastged_serve_poll with status FASTGED_ERR_CANCELLED and no map, so every
+ * submitted query still yields exactly one result. Queries already in a batch run to the end.
+ * Returns how many queries were cancelled (0 if none was queued), or FASTGED_ERR_INVALID_ARG
+ * for a null server. Thread-safe. */
+int fastged_serve_cancel(fastged_server *s, uint64_t tag);
+
+/* Counters of the server so far (completed counts every result handed to the completion
+ * queue: succeeded, failed or cancelled). */
 int fastged_serve_get_stats(fastged_server *s, fastged_serve_stats *out);
 
 /* Stops accepting queries, runs every queued one and waits for all batches; results stay

@@ -402,6 +402,39 @@ extern "C" int fastged_serve_submit(fastged_server *s, const fastged_graph *g1,
     return FASTGED_OK;
 }
 
+extern "C" int fastged_serve_cancel(fastged_server *s, uint64_t tag)
+{
+    clear_error();
+    if (!s) return set_error(FASTGED_ERR_INVALID_ARG, "null server");
+    int n = 0;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        const Clock::time_point now = Clock::now();
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+            Request *q = *it;
+            if (q->tag != tag) {
+                ++it;
+                continue;
+            }
+            Result res;
+            memset(&res.r, 0, sizeof(res.r));
+            res.r.tag = q->tag;
+            res.r.status = FASTGED_ERR_CANCELLED;
+            res.r.latency_ms = res.r.queue_ms = ms_between(q->t_submit, now);
+            s->done_q.push_back(std::move(res));
+            s->st.completed++;
+            delete q;
+            it = s->pending.erase(it);
+            ++n;
+        }
+    }
+    if (n > 0) {
+        s->done_cv.notify_all();
+        s->cv.notify_all();
+    }
+    return n;
+}
+
 extern "C" int fastged_serve_poll(fastged_server *s, fastged_serve_result *out, int32_t max_results,
                                   int32_t *map_buf, int64_t map_cap, int32_t timeout_ms)
 {

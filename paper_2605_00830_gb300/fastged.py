@@ -25,6 +25,7 @@ FASTGED_ERR_CUDA = -3
 FASTGED_ERR_TIMEOUT = -4
 FASTGED_ERR_BUSY = -5
 FASTGED_ERR_STOPPED = -6
+FASTGED_ERR_CANCELLED = -7
 FASTGED_FORM_BATCHED = 0
 FASTGED_FORM_PLAIN = 1
 FASTGED_INJECT_ALLOC = 0
@@ -38,7 +39,8 @@ EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_
             "fastged_plan_read", "fastged_plan_info", "fastged_plan_kernel_ms",
             "fastged_plan_destroy", "fastged_measure_int_peak", "fastged_batch_noalloc",
             "fastged_serve_start", "fastged_serve_submit", "fastged_serve_poll",
-            "fastged_serve_get_stats", "fastged_serve_stop", "fastged_serve_destroy",
+            "fastged_serve_get_stats", "fastged_serve_cancel", "fastged_serve_stop",
+            "fastged_serve_destroy",
             "fastged_autotune_entries", "fastged_autotune_clear", "fastged_edit_path",
             "fastged_apply_edit_ops", "fastged_cross", "fastged_set_timeout",
             "fastged_inject_fault"]
@@ -160,6 +162,7 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     lib.fastged_serve_submit.argtypes = [vp, vp, vp, i32, ctypes.c_uint64]
     lib.fastged_serve_poll.argtypes = [vp, ctypes.POINTER(ServeResult), i32, vp, i64, i32]
     lib.fastged_serve_get_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    lib.fastged_serve_cancel.argtypes = [vp, ctypes.c_uint64]
     lib.fastged_serve_stop.argtypes = [vp]
     lib.fastged_serve_stop.restype = None
     lib.fastged_serve_destroy.argtypes = [vp]
@@ -445,6 +448,13 @@ class Server:
                   else np.zeros(0, np.int32))
             res.append((r.tag, r.status, r.cost, mp, r.n_evals, r.latency_ms, r.queue_ms))
         return res
+
+    def cancel(self, tag: int) -> int:
+        """Cancel the still-queued queries with this tag; returns how many were cancelled."""
+        n = self.lib.fastged_serve_cancel(self.s, int(tag))
+        if n < 0:
+            _check(self.lib, n)
+        return n
 
     def stats(self) -> dict:
         st = ServeStats()

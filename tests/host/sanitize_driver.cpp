@@ -3,7 +3,8 @@
 // fakes of fake_cuda.cpp). Through the public C API it runs, on seeded random graphs of every
 // size class: batches from two handles on two threads at once (one of them contends for the
 // shared host thread pool), invalid batches, the degree order, an autotuned plan replayed as
-// a graph, and the server fed by three submitting threads while the main thread polls. It
+// a graph, and the server fed by three submitting threads while the main thread cancels a few
+// queries and polls. It
 // prints one summary line and exits 0 only if every call returned what it should.
 #include <algorithm>
 #include <atomic>
@@ -207,6 +208,9 @@ int main()
                     }
                 }
             });
+        // cancel a few queries while the others are submitted and served (each is either still
+        // queued, and comes back cancelled, or already in a batch, and runs)
+        for (int k : {10, 150, 250}) expect(fastged_serve_cancel(s, (uint64_t)k) >= 0, "cancel");
         std::vector<fastged_serve_result> out(64);
         std::vector<int32_t> maps(1 << 16);
         std::vector<int> seen(3 * per, 0);
@@ -217,7 +221,11 @@ int main()
                                              (int64_t)maps.size(), 20);
             expect(n >= 0, "poll");
             for (int i = 0; i < n; ++i) {
-                expect(out[i].status == FASTGED_OK, "served status");
+                const uint64_t t = out[i].tag;
+                const bool may_cancel = t == 10 || t == 150 || t == 250;
+                expect(out[i].status == FASTGED_OK ||
+                           (may_cancel && out[i].status == FASTGED_ERR_CANCELLED && out[i].n1 == 0),
+                       "served status");
                 expect(out[i].tag < (uint64_t)(3 * per) && seen[out[i].tag]++ == 0, "served once");
                 ++served;
             }

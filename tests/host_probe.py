@@ -80,6 +80,7 @@ def load():
     L.fastged_serve_poll.argtypes = [vp, ctypes.POINTER(F.ServeResult), i32, vp, ctypes.c_int64,
                                      i32]
     L.fastged_serve_get_stats.argtypes = [vp, ctypes.POINTER(F.ServeStats)]
+    L.fastged_serve_cancel.argtypes = [vp, ctypes.c_uint64]
     for name in ("fastged_serve_stop", "fastged_serve_destroy"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None

@@ -5,8 +5,9 @@ tests/host_probe.py). Batches do no device work there: a batch's completion call
 fake stream after a set delay and its results are zeros, so what is checked is the dispatcher:
 every submitted query comes back exactly once with its tag and its map length, batches respect
 their size limit, the queue pushes back when full, admission waits for memory while other
-batches run, a failed launch is reported for every query of that batch, and stop drains the
-queue and then refuses new queries.
+batches run, a failed launch is reported for every query of that batch, a cancelled query
+comes back cancelled while the others run, and stop drains the queue and then refuses new
+queries.
 """
 import ctypes
 import threading
@@ -198,6 +199,44 @@ def test_stop_drains_then_refuses(lib):
     got = _collect(srv, w.n_pairs)
     srv.close()
     assert sorted(got) == list(range(w.n_pairs))
+
+
+def test_cancel_queued_queries(lib):
+    # one lane whose batch takes 200 ms: the first query occupies it, the rest stay queued
+    lib.fake_set_host_fn_delay_us(200000)
+    w, kk = _mix(40, seed=9)
+    w = W.subset(w, range(21))
+    kk = kk[:21]
+    mm = F.Marshalled(w.graphs, w.pairs)
+    cfg = F.serve_config(lanes=1, max_batch_pairs=64, min_batch_pairs=1000,
+                         max_wait_us=10000000)
+    srv = HostServer(lib, w.cost, cfg)
+    _submit_all(srv, mm, w, kk, [0])
+    time.sleep(0.02)                           # the dispatcher launches it on the idle lane
+    _submit_all(srv, mm, w, kk, range(1, 21))
+    # a tag used twice: both queued copies go
+    assert srv.submit(mm, w.pairs[5][0], w.pairs[5][1], int(kk[5]), 5) == F.FASTGED_OK
+    assert srv.cancel(3) == 1 and srv.cancel(5) == 2 and srv.cancel(7) == 1
+    assert srv.cancel(0) == 0                  # already running
+    assert srv.cancel(999) == 0                # never submitted
+    assert lib.fastged_serve_cancel(None, 1) == F.FASTGED_ERR_INVALID_ARG
+    srv.stop()
+    out = (F.ServeResult * 64)()
+    buf = np.zeros(1 << 16, np.int32)
+    n = lib.fastged_serve_poll(srv.s, out, 64, buf.ctypes.data, buf.size, 100)
+    st = srv.stats()
+    srv.close()
+    status = {}
+    for r in out[:n]:
+        status.setdefault(int(r.tag), []).append(r.status)
+        if r.status == F.FASTGED_ERR_CANCELLED:
+            assert r.n1 == 0
+    assert n == 22
+    assert status[3] == status[7] == [F.FASTGED_ERR_CANCELLED]
+    assert status[5] == [F.FASTGED_ERR_CANCELLED] * 2
+    assert all(v == [F.FASTGED_OK] for t, v in status.items() if t not in (3, 5, 7))
+    assert st["submitted"] == st["completed"] == 22 and st["failed"] == 0
+    assert st["batched_pairs"] == 22 - 4
 
 
 def test_invalid_submissions(lib):
