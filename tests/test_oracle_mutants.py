@@ -39,6 +39,8 @@ MUTANTS = {
     "square_edge_sub_always": ("if (e1 && e2) cost += (e1 != e2) ? c[C_ESUB] : 0;",
                                "if (e1 && e2) cost += c[C_ESUB];"),
     "full_cost_ins_del_swapped": ("if (pre[u] < 0) cost += c[C_VINS];", "if (pre[u] < 0) cost += c[C_VDEL];"),
+    "variant_b_cuts_to_k": ("if (!(variant == 1 && i == n1 - 1) && newL > (size_t)K)",
+                            "if (newL > (size_t)K)"),
 }
 
 
@@ -66,6 +68,10 @@ def _pins_pass(lib) -> bool:
                 ped, lm = O.kbest_leaves(g1, g2, case["cost"], exp["K"], lib=lib)
                 if list(ped) != exp["leaf_ped"] or lm.tolist() != exp["leaf_map"]:
                     return False
+        for exp in case.get("kbest_variant1", []):
+            cost, mp, nev = O.kbest(g1, g2, case["cost"], exp["K"], variant=1, lib=lib)
+            if (cost, list(mp), nev) != (exp["cost"], exp["map"], exp["n_evals"]):
+                return False
     for seed in range(12):
         st = W.Stream(seed, 93)
         g1 = W.random_small(st, 1, 5, 0.5, 3, 2)
@@ -79,7 +85,31 @@ def _pins_pass(lib) -> bool:
         cost, mp, _ = O.kbest(g1, g2, c, Kx, lib=lib)
         if cost != ged or O.full_cost(g1, g2, c, mp, lib=lib) != cost:
             return False
+    # variant B: the best child of the beam kept before the last level
+    for seed in range(8):
+        g1, g2 = _rand_pair_b(seed)
+        c = tuple(int(x) for x in W.Stream(seed, 94).randint(1, 6, 6))
+        for K in (1, 2):
+            got = O.kbest(g1, g2, c, K, variant=1, lib=lib)[0]
+            _, maps = O.kbest_leaves(_prefix(g1, g1.n - 1), g2, c, K, lib=lib)
+            best = min(O.full_cost(g1, g2, c, list(m) + [j], lib=lib) for m in maps
+                       for j in [u for u in range(g2.n) if u not in set(int(x) for x in m)] + [-1])
+            if got != best:
+                return False
     return True
+
+
+def _rand_pair_b(seed):
+    st = W.Stream(seed, 95)
+    return W.random_small(st, 2, 5, 0.5, 3, 2), W.random_small(st, 1, 4, 0.5, 3, 2)
+
+
+def _prefix(g, k):
+    e = np.asarray(g.edges, dtype=np.int32).reshape(-1, 2)
+    keep = (e[:, 0] < k) & (e[:, 1] < k)
+    el = None if g.elabel is None else np.asarray(g.elabel, dtype=np.int32)[keep]
+    return W.Graph(n=k, vlabel=np.asarray(g.vlabel, dtype=np.int32)[:k], edges=e[keep],
+                   elabel=el)
 
 
 def test_unmutated_oracle_passes():

@@ -205,6 +205,41 @@ def test_kbest_result_is_the_best_completed_leaf():
     assert n_opt > 0
 
 
+def prefix_graph(g, k):
+    """g restricted to its first k vertices (the edges among them, with their labels)."""
+    e = np.asarray(g.edges, dtype=np.int32).reshape(-1, 2)
+    keep = (e[:, 0] < k) & (e[:, 1] < k)
+    el = None if g.elabel is None else np.asarray(g.elabel, dtype=np.int32)[keep]
+    return W.Graph(n=k, vlabel=np.asarray(g.vlabel, dtype=np.int32)[:k], edges=e[keep],
+                   elabel=el)
+
+
+def variant_b_by_definition(g1, g2, cost, K):
+    """Variant B completes every successor of the last level: every child (each free g2
+    vertex, or the deletion) of the beam kept after the first n1 - 1 levels. That beam is the
+    final kept list of the search on g1's first n1 - 1 vertices, which no later vertex of g1
+    influences, so it comes from a variant-A run on that prefix; each child is a complete map,
+    scored by the independent full-path cost."""
+    _, maps = O.kbest_leaves(prefix_graph(g1, g1.n - 1), g2, cost, K)
+    best = None
+    for m in maps:
+        used = set(int(x) for x in m if x >= 0)
+        for j in [u for u in range(g2.n) if u not in used] + [-1]:
+            c = O.full_cost(g1, g2, cost, list(m) + [j])
+            best = c if best is None else min(best, c)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_variant_b_is_the_best_child_of_the_penultimate_beam(seed):
+    g1, g2 = _rand_pair(seed, 1, 6, ne=2 if seed % 2 else 0)
+    cost = _rand_cost(seed)
+    for K in (1, 2, 3, 5):
+        got, mp, _ = O.kbest(g1, g2, cost, K, variant=1)
+        assert got == variant_b_by_definition(g1, g2, cost, K)
+        assert O.full_cost(g1, g2, cost, mp) == got
+
+
 def test_kbest_k1_evals_closed_form():
     """With K = 1 the search follows one path: level i scores (n2 - #substitutions so far)
     + 1 successors, and one leaf is completed."""
