@@ -240,6 +240,45 @@ def test_variant_b_is_the_best_child_of_the_penultimate_beam(seed):
         assert O.full_cost(g1, g2, cost, mp) == got
 
 
+def ped_by_definition(g1k, g2, cost, m):
+    """Partial edit distance of a map of g1's first k vertices: the full-path cost of the
+    prefix map less what the leaf completion adds (every unused g2 vertex and every g2 edge
+    with an unused end are insertions)."""
+    used = set(int(x) for x in m if x >= 0)
+    e2 = np.asarray(g2.edges).reshape(-1, 2)
+    pending = cost[2] * (g2.n - len(used)) + cost[5] * sum(
+        1 for a, b in e2 if int(a) not in used or int(b) not in used)
+    return O.full_cost(g1k, g2, cost, list(m)) - pending
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_each_level_keeps_the_k_best_children(seed):
+    """Algorithm 1 level by level: the list kept after level k is the K smallest children of
+    the list kept after level k - 1 (every free target vertex in increasing order, then the
+    deletion), ordered by (PED, parent slot, child), each PED recomputed from the definition.
+    The kept lists come from runs on g1's first k vertices, which later vertices do not
+    influence."""
+    g1, g2 = _rand_pair(seed, 1, 6, ne=2 if seed % 3 == 0 else 0)
+    cost = _rand_cost(seed)
+    for K in (1, 2, 3, 7):
+        prev_ped, prev_maps = O.kbest_leaves(prefix_graph(g1, 0), g2, cost, K)
+        for k in range(1, g1.n + 1):
+            g1k = prefix_graph(g1, k)
+            children = []
+            for slot, m in enumerate(prev_maps):
+                used = set(int(x) for x in m if x >= 0)
+                for j in [u for u in range(g2.n) if u not in used] + [-1]:
+                    child = list(m) + [j]
+                    key_j = j if j >= 0 else g2.n
+                    children.append((ped_by_definition(g1k, g2, cost, child), slot, key_j, child))
+            children.sort(key=lambda t: t[:3])
+            kept = children[:K]
+            ped, maps = O.kbest_leaves(g1k, g2, cost, K)
+            assert list(ped) == [c[0] for c in kept]
+            assert maps.tolist() == [c[3] for c in kept]
+            prev_ped, prev_maps = ped, maps
+
+
 def test_kbest_k1_evals_closed_form():
     """With K = 1 the search follows one path: level i scores (n2 - #substitutions so far)
     + 1 successors, and one leaf is completed."""
