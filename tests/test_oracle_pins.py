@@ -257,11 +257,12 @@ def test_each_level_keeps_the_k_best_children(seed):
     the list kept after level k - 1 (every free target vertex in increasing order, then the
     deletion), ordered by (PED, parent slot, child), each PED recomputed from the definition.
     The kept lists come from runs on g1's first k vertices, which later vertices do not
-    influence."""
+    influence. The evaluation count is every child scored plus every final leaf completed."""
     g1, g2 = _rand_pair(seed, 1, 6, ne=2 if seed % 3 == 0 else 0)
     cost = _rand_cost(seed)
     for K in (1, 2, 3, 7):
         prev_ped, prev_maps = O.kbest_leaves(prefix_graph(g1, 0), g2, cost, K)
+        scored = 0
         for k in range(1, g1.n + 1):
             g1k = prefix_graph(g1, k)
             children = []
@@ -271,12 +272,15 @@ def test_each_level_keeps_the_k_best_children(seed):
                     child = list(m) + [j]
                     key_j = j if j >= 0 else g2.n
                     children.append((ped_by_definition(g1k, g2, cost, child), slot, key_j, child))
+            scored += len(children)
             children.sort(key=lambda t: t[:3])
             kept = children[:K]
             ped, maps = O.kbest_leaves(g1k, g2, cost, K)
             assert list(ped) == [c[0] for c in kept]
             assert maps.tolist() == [c[3] for c in kept]
             prev_ped, prev_maps = ped, maps
+        # n_evals: every child scored at every level, plus every final leaf completed
+        assert O.kbest(g1, g2, cost, K)[2] == scored + len(prev_maps)
 
 
 def test_kbest_k1_evals_closed_form():
