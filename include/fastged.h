@@ -271,6 +271,11 @@ void fastged_serve_stop(fastged_server *s);
 /* Stops the server if needed and releases it (unpolled results are discarded). */
 void fastged_serve_destroy(fastged_server *s);
 
+/* Host threads: batches are validated and staged on a process-wide thread pool whose size
+ * the environment variable FASTGED_HOST_THREADS sets when the pool is first used (threads
+ * of one batch, the calling thread included; 1 = the caller alone; default: up to 16). The
+ * staged bytes and every result are the same for any size. */
+
 /* Tuning table of the process (size-class shape -> team shape). If the environment variable
  * FASTGED_AUTOTUNE_FILE names a file, the table is read from it on first use and every new
  * entry is appended to it. fastged_autotune_entries returns the number of entries;

@@ -188,10 +188,16 @@ public:
 private:
     static constexpr int kPollUs = 200;
 
+    // FASTGED_HOST_THREADS (read once, at first use) sets the threads of a parallel_for,
+    // the caller included: 1 runs everything in the caller; by default up to 16
     HostPool()
     {
         const unsigned hw = std::thread::hardware_concurrency();
-        const int nw = (int)std::min(15u, hw > 1 ? hw - 1 : 0u);
+        int nw = (int)std::min(15u, hw > 1 ? hw - 1 : 0u);
+        if (const char *e = getenv("FASTGED_HOST_THREADS")) {
+            const long t = strtol(e, nullptr, 10);
+            if (t >= 1) nw = (int)std::min(t - 1, 63L);
+        }
         for (int k = 0; k < nw; ++k) workers_.emplace_back([this] { loop(); });
     }
     ~HostPool()

@@ -9,6 +9,9 @@ chunks the flattening works in, so the parallel passes and their combination are
 """
 import ctypes
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -356,3 +359,37 @@ def test_pinned_allocation_failure(lib):
     assert f.rc == F.FASTGED_ERR_OOM and "injected" in f.err
     f = Flat(lib, w, K=16)
     assert f.rc == 0, f.err
+
+
+_DIGEST = r"""
+import hashlib, sys
+sys.path[:0] = [{root!r}, {tests!r}]
+from host_probe import load
+import test_host_flatten as T
+L = load()
+f = T.Flat(L, T._mix(), K=64, cost=(2, 4, 4, 1, 2, 2), vertex_order=1)
+assert f.rc == 0, f.err
+h = hashlib.sha256(f.staging)
+for o in f.orders:
+    h.update(o.tobytes())
+for a in (f.meta, f.map_off, f.perm):
+    h.update(a.tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_staged_bytes_do_not_depend_on_the_thread_count(lib):
+    """The flattening's chunks are sized by the number of host threads; what it stages, its
+    classes, their orders, the graph table, the map offsets and the branching permutation
+    must be the same for any number (FASTGED_HOST_THREADS; one process per count, since the
+    pool is sized once)."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = _DIGEST.format(root=os.path.dirname(here), tests=here)
+    digests = set()
+    for t in ("1", "3", "16"):
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           timeout=600, env=dict(os.environ, FASTGED_HOST_THREADS=t))
+        assert r.returncode == 0, r.stderr[-2000:]
+        digests.add(r.stdout.strip().splitlines()[-1])
+    assert len(digests) == 1
+
