@@ -279,7 +279,9 @@ void fastged_serve_destroy(fastged_server *s);
 /* Tuning table of the process (size-class shape -> team shape). If the environment variable
  * FASTGED_AUTOTUNE_FILE names a file, the table is read from it on first use and every new
  * entry is appended to it. fastged_autotune_entries returns the number of entries;
- * fastged_autotune_clear forgets them all (the file is left alone). */
+ * fastged_autotune_clear forgets them all (the file is left alone). FASTGED_CLUSTER = 1, 2,
+ * 4, 8 or 16 forces the CTAs per team of the classes that may use thread-block clusters (few
+ * pairs of four or more words, or two-word pairs with very wide beams), over the table. */
 int fastged_autotune_entries(void);
 void fastged_autotune_clear(void);
 
