@@ -213,7 +213,7 @@ typedef struct {
     int32_t min_batch_pairs;   /* launch once this many queries of a bucket wait (64)      */
     int32_t max_pending;       /* queued queries at most; beyond: FASTGED_ERR_BUSY (2^20)  */
     int32_t max_wait_us;       /* longest wait of the oldest query before launch (200)     */
-    int32_t pad;
+    int32_t max_retries;       /* times a query of a failed batch is queued again (0)      */
     int64_t hbm_reserve_bytes; /* device memory kept free by admission (1 GiB)             */
 } fastged_serve_config;
 

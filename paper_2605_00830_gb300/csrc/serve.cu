@@ -36,6 +36,7 @@ struct Request {
     uint64_t tag = 0;
     int32_t K = 1;
     int bucket = 0;
+    int retries = 0;   // times the query went back to the queue after its batch failed
     int32_t n[2] = {0, 0}, m[2] = {0, 0};
     std::vector<int32_t> vl[2], ed[2], el[2];
     bool labelled[2] = {false, false};
@@ -117,6 +118,22 @@ struct fastged_server {
     fastged_serve_stats st{};
 };
 
+// Queries of a failed batch that may still be retried go back to the front of the queue in
+// their order; returns whether q was taken back (caller holds mu).
+static bool requeue_for_retry(fastged_server *s, Request *q, std::vector<Request *> &again)
+{
+    if (q->retries >= s->cfg.max_retries) return false;
+    ++q->retries;
+    again.push_back(q);
+    return true;
+}
+
+static void push_front_in_order(fastged_server *s, const std::vector<Request *> &again)
+{
+    for (auto it = again.rbegin(); it != again.rend(); ++it) s->pending.push_front(*it);
+    if (!again.empty()) s->cv.notify_all();
+}
+
 static void CUDART_CB lane_done_cb(void *arg)
 {
     Lane *l = (Lane *)arg;
@@ -134,8 +151,10 @@ static void collect_lane(fastged_server *s, Lane &l)
     const int rc = batch_results(l.h, l.out_cost.data(), l.out_map.data(), l.out_nev.data());
     const Clock::time_point now = Clock::now();
     int64_t off = 0;
+    std::vector<Request *> again;
     for (int p = 0; p < np; ++p) {
         Request *q = l.reqs[p];
+        if (rc != FASTGED_OK && requeue_for_retry(s, q, again)) continue;
         Result res;
         memset(&res.r, 0, sizeof(res.r));
         res.r.tag = q->tag;
@@ -151,8 +170,10 @@ static void collect_lane(fastged_server *s, Lane &l)
         off += q->n[0];
         s->done_q.push_back(std::move(res));
         s->st.completed++;
+        if (rc != FASTGED_OK) s->st.failed++;
         delete q;
     }
+    push_front_in_order(s, again);
     l.reqs.clear();
     l.busy = false;
     l.done = false;
@@ -212,9 +233,12 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
     }
     lk.lock();
     if (rc != FASTGED_OK) {
-        // nothing is in flight on this lane: report the failure for every request
+        // nothing is in flight on this lane: queue the requests again while they may be
+        // retried, report the failure for the others
         const Clock::time_point now = Clock::now();
+        std::vector<Request *> again;
         for (Request *q : l.reqs) {
+            if (requeue_for_retry(s, q, again)) continue;
             Result res;
             memset(&res.r, 0, sizeof(res.r));
             res.r.tag = q->tag;
@@ -227,6 +251,7 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
             s->st.failed++;
             delete q;
         }
+        push_front_in_order(s, again);
         l.reqs.clear();
         l.busy = false;
         s->done_cv.notify_all();
@@ -331,7 +356,7 @@ extern "C" int fastged_serve_start(const fastged_cost_model *cost, const fastged
     if (!cost || !out) return set_error(FASTGED_ERR_INVALID_ARG, "null argument");
     fastged_serve_config c = cfg ? *cfg : serve_defaults();
     if (c.lanes < 1 || c.lanes > 16 || c.max_batch_pairs < 1 || c.min_batch_pairs < 1 ||
-        c.max_pending < 1 || c.max_wait_us < 0 || c.hbm_reserve_bytes < 0)
+        c.max_pending < 1 || c.max_wait_us < 0 || c.hbm_reserve_bytes < 0 || c.max_retries < 0)
         return set_error(FASTGED_ERR_INVALID_ARG, "serve config out of range");
     fastged_server *s = new fastged_server();
     s->cost = *cost;

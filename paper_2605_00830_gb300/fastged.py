@@ -99,7 +99,7 @@ class DeviceBatch(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
                 ("min_batch_pairs", ctypes.c_int32), ("max_pending", ctypes.c_int32),
-                ("max_wait_us", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("max_wait_us", ctypes.c_int32), ("max_retries", ctypes.c_int32),
                 ("hbm_reserve_bytes", ctypes.c_int64)]
 
 
@@ -409,9 +409,9 @@ class FastGED:
 
 
 def serve_config(lanes=6, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
-                 max_wait_us=200, hbm_reserve_bytes=1 << 30) -> ServeConfig:
-    return ServeConfig(lanes, max_batch_pairs, min_batch_pairs, max_pending, max_wait_us, 0,
-                       hbm_reserve_bytes)
+                 max_wait_us=200, hbm_reserve_bytes=1 << 30, max_retries=0) -> ServeConfig:
+    return ServeConfig(lanes, max_batch_pairs, min_batch_pairs, max_pending, max_wait_us,
+                       max_retries, hbm_reserve_bytes)
 
 
 class Server:

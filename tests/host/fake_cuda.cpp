@@ -229,8 +229,13 @@ cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { retur
 // more words)
 namespace fastged {
 static std::atomic<int> g_max_pack_graphs{0};   // most graphs one batch packed
+static std::atomic<int> g_fail_launches{0};     // next packing launches that fail
 cudaError_t launch_pack(const PackParams &, int n_graphs, cudaStream_t)
 {
+    int f = g_fail_launches.load();
+    while (f > 0 && !g_fail_launches.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f > 0) return cudaErrorLaunchFailure;
     int m = g_max_pack_graphs.load();
     while (n_graphs > m && !g_max_pack_graphs.compare_exchange_weak(m, n_graphs)) {
     }
@@ -272,3 +277,6 @@ extern "C" int fake_max_pack_graphs(int reset)
 {
     return reset ? fastged::g_max_pack_graphs.exchange(0) : fastged::g_max_pack_graphs.load();
 }
+
+// the next n packing launches fail (a batch's launch error)
+extern "C" void fake_fail_launches(int n) { fastged::g_fail_launches.store(n); }

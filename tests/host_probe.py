@@ -56,6 +56,7 @@ def load():
     L.fake_fail_pinned_alloc.argtypes = [ctypes.c_int]
     L.fake_set_host_fn_delay_us.argtypes = [ctypes.c_int]
     L.fake_max_pack_graphs.argtypes = [ctypes.c_int]
+    L.fake_fail_launches.argtypes = [ctypes.c_int]
     L.fake_set_shape_ms.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_float]
     L.fake_kbest_launches.restype = ctypes.c_longlong
     L.fake_events_busy_for_ms.argtypes = [ctypes.c_int]

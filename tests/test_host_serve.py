@@ -5,7 +5,8 @@ tests/host_probe.py). Batches do no device work there: a batch's completion call
 fake stream after a set delay and its results are zeros, so what is checked is the dispatcher:
 every submitted query comes back exactly once with its tag and its map length, batches respect
 their size limit, the queue pushes back when full, admission waits for memory while other
-batches run, a failed launch is reported for every query of that batch, a cancelled query
+batches run, a failed launch is reported for every query of that batch (or the batch is
+retried, up to max_retries times), a cancelled query
 comes back cancelled while the others run, and stop drains the queue and then refuses new
 queries.
 """
@@ -199,6 +200,47 @@ def test_stop_drains_then_refuses(lib):
     got = _collect(srv, w.n_pairs)
     srv.close()
     assert sorted(got) == list(range(w.n_pairs))
+
+
+@pytest.mark.parametrize("fails,retries,ok", [(1, 1, True), (2, 1, False), (1, 0, False),
+                                               (3, 3, True)])
+def test_failed_batch_is_retried(lib, fails, retries, ok):
+    """A query whose batch fails goes back to the queue up to max_retries times; only then is
+    its failure reported."""
+    lib.fake_set_host_fn_delay_us(0)
+    w, kk = _mix(4, seed=10)
+    mm = F.Marshalled(w.graphs, w.pairs)
+    srv = HostServer(lib, w.cost, F.serve_config(lanes=1, max_retries=retries))
+    lib.fake_fail_launches(fails)
+    try:
+        _submit_all(srv, mm, w, kk, [0])
+        got = _collect(srv, 1, timeout_s=30)
+        st = srv.stats()
+    finally:
+        lib.fake_fail_launches(0)
+        srv.close()
+    assert list(got) == [0]
+    assert got[0][1] == (F.FASTGED_OK if ok else F.FASTGED_ERR_CUDA)
+    assert st["failed"] == (0 if ok else 1) and st["completed"] == 1
+    assert st["batches"] == min(fails, retries + 1) + (1 if ok else 0)
+
+
+def test_retries_recover_a_failed_batch_in_a_stream(lib):
+    lib.fake_set_host_fn_delay_us(200)
+    w, kk = _mix(60, seed=11)
+    mm = F.Marshalled(w.graphs, w.pairs)
+    cfg = F.serve_config(lanes=2, max_batch_pairs=16, min_batch_pairs=8, max_wait_us=500,
+                         max_retries=1)
+    srv = HostServer(lib, w.cost, cfg)
+    lib.fastged_inject_fault(F.FASTGED_INJECT_LAUNCH, 2)   # the second batch fails once
+    _submit_all(srv, mm, w, kk, range(w.n_pairs))
+    got = _collect(srv, w.n_pairs)
+    st = srv.stats()
+    srv.close()
+    assert sorted(got) == list(range(w.n_pairs))
+    assert all(r[1] == F.FASTGED_OK for r in got.values())
+    assert st["failed"] == 0 and st["completed"] == w.n_pairs
+    assert st["batched_pairs"] > w.n_pairs          # the failed batch's queries ran twice
 
 
 def test_cancel_queued_queries(lib):
