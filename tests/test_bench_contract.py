@@ -149,6 +149,62 @@ def test_bench_line_has_every_contract_key(monkeypatch, capsys, fake_smi):
         assert "molecule" in shapes and shapes["molecule"]["p50_ms"] == pytest.approx(3.0)
 
 
+class _SetAttr:
+    """monkeypatch's setattr, for the spawned ranks below (nothing is undone there)."""
+
+    def setattr(self, obj, name, value):
+        setattr(obj, name, value)
+
+
+def _write_fake_smi():
+    d = os.path.join(ROOT, "tests", "_build", "fake_smi")
+    os.makedirs(d, exist_ok=True)
+    exe = os.path.join(d, "nvidia-smi")
+    with open(exe, "w") as f:
+        f.write(f"#!/bin/sh\nwhile true; do echo '{SMI_ROW}'; sleep 0.05; done\n")
+    os.chmod(exe, os.stat(exe).st_mode | stat.S_IXUSR)
+    return d
+
+
+def _bench_rank(rank, world, port, out_dir):
+    import contextlib
+    import io
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    os.environ["PATH"] = _write_fake_smi() + os.pathsep + os.environ["PATH"]
+    sys.path.insert(0, ROOT)
+    _stand_ins(_SetAttr())
+    import bench
+    sys.argv = ["bench.py", "--gpus", str(world), "--steps", "3", "--warmup", "3",
+                "--pairs", "200", "--plain-sample", "20", "--serve-window", "0.1"]
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        rc = bench.main()
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(f"rc={rc}\n" + buf.getvalue())
+
+
+def test_bench_under_two_ranks(tmp_path):
+    """The torchrun path with two gloo ranks: rank 0 alone prints, value and e2e are the whole
+    job's (both ranks' pairs over the slowest rank's time), and the oracle legs are left out."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = 31500 + (os.getpid() % 2000)
+    mp.spawn(_bench_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    out0 = open(tmp_path / "r0.txt").read().splitlines()
+    out1 = open(tmp_path / "r1.txt").read().splitlines()
+    assert out0[0] == "rc=0" and out1[0] == "rc=0"
+    assert not [l for l in out1 if l.startswith("{")]
+    lines = [l for l in out0 if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["scaling"] == "weak"
+    assert d["value"] == pytest.approx(2 * 200 / 4e-3)
+    assert d["ms_per_step"] == pytest.approx(4.0)
+    assert d["e2e"]["value"] > 0 and "serve" in d and "plain_form" in d
+    assert "cpu_baseline" not in d and "cpu_baseline_1core" not in d
+    assert d["config"]["parallelism"] == "replicas2"
+
+
 def test_reference_arm_line(monkeypatch, capsys):
     d = _run_bench(monkeypatch, capsys, ["--impl", "reference", "--steps", "1", "--warmup", "0",
                                           "--pairs", "200", "--cpu-sample", "40"])
