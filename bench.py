@@ -277,16 +277,39 @@ def serving_leg(window_s: float, rate: float = 5000.0):
             "batches": int(st["batches"]), "mean_batch": st["batched_pairs"] / max(1, st["batches"])}
 
 
+# The oracle scores each successor by walking the source vertices mapped so far: about
+# n1 * min(K, ...) * (n2 + 1) * n1 / 2 steps per pair, at roughly this many steps per second on
+# one core. The estimate only sizes the bounded samples, so a factor of two either way does
+# no harm.
+ORACLE_STEPS_PER_S = 2.5e8
+
+
+def oracle_pair_seconds(w, p) -> float:
+    """A rough single-core time of the oracle on pair p (for sizing its bounded samples)."""
+    g1, g2 = w.graphs[int(w.pairs[p][0])], w.graphs[int(w.pairs[p][1])]
+    K = int(w.k_per_pair[p]) if w.k_per_pair is not None else w.K
+    beam = min(K, 1 + g1.n * g2.n)
+    return g1.n * beam * (g2.n + 1) * max(g1.n, 1) / 2 / ORACLE_STEPS_PER_S
+
+
 def run_cpu_oracle(w, idx, threads, max_s=None):
-    """The oracle on pairs idx (in chunks of a few pairs per thread, stopping after the chunk
-    that passes max_s seconds when given); returns (seconds, results of the pairs run)."""
+    """The oracle on pairs idx; with max_s, in chunks sized from the estimated time of a pair,
+    stopping after the chunk that passes max_s seconds. Returns (seconds, results), or
+    (None, reason) when a single pair would already take longer than 2 * max_s."""
     from oracle import oracle as O
-    chunk = max(64 * threads, 256) if max_s is not None else max(len(idx), 1)
+    if max_s is None:
+        t = time.perf_counter()
+        res = O.kbest_workload(w, idx, threads=threads)
+        return time.perf_counter() - t, res
+    est = max(oracle_pair_seconds(w, idx[0]), 1e-6) if idx else 1e-6
+    if est > 2 * max_s:
+        return None, f"skipped: one pair of this batch takes about {est:.0f} s in the oracle"
+    chunk = int(min(max(threads * max_s / 4 / est, threads), max(64 * threads, 256)))
     res = []
     t = time.perf_counter()
     for k in range(0, len(idx), chunk):
         res += O.kbest_workload(w, idx[k:k + chunk], threads=threads)
-        if max_s is not None and time.perf_counter() - t >= max_s:
+        if time.perf_counter() - t >= max_s:
             break
     return time.perf_counter() - t, res
 
@@ -298,6 +321,10 @@ def reference_arm(args):
     w = workload(0, args.pairs)
     threads = os.cpu_count() or 1
     sample = list(range(min(args.cpu_sample, w.n_pairs)))
+    probe_dt, why = run_cpu_oracle(w, sample[:1], 1, args.cpu_seconds)
+    if probe_dt is None:
+        print(json.dumps({"impl": "reference", "unavailable": why}), flush=True)
+        return 0
     for _ in range(args.warmup):
         run_cpu_oracle(w, sample[:200], threads, args.cpu_seconds)
     tot = 0.0
@@ -478,17 +505,17 @@ def ours(args):
         # CPU oracle on a bounded sample (at most cpu_sample pairs and about cpu_seconds of
         # wall time), all host cores
         threads = os.cpu_count() or 1
-        idx = list(range(min(args.cpu_sample, w.n_pairs)))
-        dt, res = run_cpu_oracle(w, idx, threads, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": len(res) / dt, "unit": UNIT, "cores": threads,
-                                "kind": "oracle",
-                                "sample": f"first {len(res)} of the {w.n_pairs:,} pairs"}
-        # and on one host core (a smaller sample)
-        idx1 = list(range(min(max(args.cpu_sample // 16, 50), w.n_pairs)))
-        dt1, res1 = run_cpu_oracle(w, idx1, 1, args.cpu_seconds)
-        line["cpu_baseline_1core"] = {"value": len(res1) / dt1, "unit": UNIT, "cores": 1,
-                                      "kind": "oracle",
-                                      "sample": f"first {len(res1)} of the {w.n_pairs:,} pairs"}
+        for key, cores, n in (("cpu_baseline", threads, args.cpu_sample),
+                              ("cpu_baseline_1core", 1, max(args.cpu_sample // 16, 50))):
+            idx = list(range(min(n, w.n_pairs)))
+            dt, res = run_cpu_oracle(w, idx, cores, args.cpu_seconds)
+            if dt is None:
+                line[key] = {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": res}
+            else:
+                line[key] = {"value": len(res) / dt, "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"first {len(res)} of the {w.n_pairs:,} pairs"}
     F.fastged_plan_destroy(plan)
     g.close()
     if rank == 0:

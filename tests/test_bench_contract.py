@@ -205,6 +205,31 @@ def test_bench_under_two_ranks(tmp_path):
     assert d["config"]["parallelism"] == "replicas2"
 
 
+@pytest.mark.parametrize("workload,pairs", [("dense", 6), ("large", 2)])
+def test_other_workloads_keep_the_oracle_legs_bounded(monkeypatch, capsys, fake_smi,
+                                                      workload, pairs):
+    """On the slower batches the oracle legs stop at their time bound, or are skipped (with
+    the reason) when one pair alone would take far longer."""
+    _stand_ins(monkeypatch)
+    d = _run_bench(monkeypatch, capsys, ["--workload", workload, "--pairs", str(pairs),
+                                          "--steps", "3", "--warmup", "3", "--plain-sample", "2",
+                                          "--serve-window", "0.05", "--cpu-seconds", "1"])
+    for key in ("cpu_baseline", "cpu_baseline_1core"):
+        leg = d[key]
+        if workload == "large":
+            assert leg["value"] is None and leg["sample"].startswith("skipped")
+        else:
+            assert leg["value"] > 0 and leg["sample"].startswith("first ")
+    r = _run_bench(monkeypatch, capsys, ["--impl", "reference", "--workload", workload,
+                                          "--pairs", str(pairs), "--steps", "1", "--warmup", "0",
+                                          "--cpu-seconds", "1"])
+    if workload == "large":
+        assert r == {"impl": "reference", "unavailable": r["unavailable"]}
+        assert "skipped" in r["unavailable"]
+    else:
+        assert r["value"] > 0
+
+
 def test_reference_arm_line(monkeypatch, capsys):
     d = _run_bench(monkeypatch, capsys, ["--impl", "reference", "--steps", "1", "--warmup", "0",
                                           "--pairs", "200", "--cpu-sample", "40"])
