@@ -117,8 +117,15 @@ cudaError_t cudaFreeHost(void *p)
     free(p);
     return cudaSuccess;
 }
+static int g_fail_device = 0;                      // next cudaMalloc calls that fail
+extern "C" void fake_fail_device_alloc(int n) { g_fail_device = n; }
 cudaError_t cudaMalloc(void **p, size_t n)
 {
+    if (g_fail_device > 0) {
+        --g_fail_device;
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     *p = malloc(n ? n : 1);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }

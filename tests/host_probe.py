@@ -54,6 +54,7 @@ def load():
         getattr(L, name).argtypes = [vp]
     L.fake_set_free_bytes.argtypes = [ctypes.c_ulonglong]
     L.fake_fail_pinned_alloc.argtypes = [ctypes.c_int]
+    L.fake_fail_device_alloc.argtypes = [ctypes.c_int]
     L.fake_set_host_fn_delay_us.argtypes = [ctypes.c_int]
     L.fake_max_pack_graphs.argtypes = [ctypes.c_int]
     L.fake_fail_launches.argtypes = [ctypes.c_int]

@@ -146,3 +146,30 @@ def test_timeout_returns_early_and_the_handle_recovers(lib):
     assert time.time() - t0 < 1.0
     lib.fake_events_busy_for_ms(0)
     lib.fastged_destroy(h)
+
+
+def test_failed_device_allocation_leaves_the_handle_usable(lib):
+    """A batch that needs more device memory than the handle holds, when cudaMalloc fails:
+    FASTGED_ERR_OOM, no outputs written, and the next call allocates afresh and succeeds."""
+    small, big = W.config2(50), W.config2(3000)
+    h = _handle(lib, small.cost)
+    o = F.make_options()
+
+    def run(w):
+        mm = F.Marshalled(w.graphs, w.pairs)
+        cost, maps, nev = F._outputs(mm)
+        cost[:] = -5
+        rc = lib.fastged_batch_ex(h, ctypes.byref(mm.pl), w.K, ctypes.byref(o),
+                                  cost.ctypes.data, maps.ctypes.data, nev.ctypes.data)
+        return rc, cost
+
+    assert run(small)[0] == F.FASTGED_OK
+    lib.fake_fail_device_alloc(1)
+    rc, cost = run(big)
+    assert rc == F.FASTGED_ERR_OOM and b"cudaMalloc" in lib.fastged_last_error(None)
+    assert (cost == -5).all()
+    rc, cost = run(big)
+    assert rc == F.FASTGED_OK and (cost == 0).all()
+    assert run(small)[0] == F.FASTGED_OK
+    lib.fastged_destroy(h)
+
