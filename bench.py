@@ -78,11 +78,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pairs", type=int, default=0, help="0 = the workload's full size")
-    ap.add_argument("--workload", choices=["molecule", "dense", "large", "widebeam"],
+    ap.add_argument("--workload", choices=["molecule", "dense", "large", "widebeam", "sizesweep"],
                     default="molecule",
                     help="molecule: the 20,000-pair batch the metric is quoted on (default); "
                          "dense / large: the 4,096-pair dense ER and 64-pair BA batches; "
-                         "widebeam: 16 molecule-sized pairs at K = 100,000")
+                         "widebeam: 16 molecule-sized pairs at K = 100,000; "
+                         "sizesweep: one pair of G(n, 0.4) graphs at K = 5,000 (see --n)")
+    ap.add_argument("--n", type=int, default=950,
+                    help="vertices per graph of the sizesweep workload")
     ap.add_argument("--k", type=int, default=0,
                     help="beam width K for every pair (0 = the workload's own K)")
     ap.add_argument("--block", type=int, default=0,
@@ -115,6 +118,9 @@ WORKLOADS = {
               "large sparse BA batch: 64 pairs, 500-1,000 vertices, K=1024, unit costs"),
     "widebeam": ("config_wide_beam", 16, 6,
                  "wide-beam batch: 16 pairs, 18-22 vertices, K=100,000, setting-1 costs"),
+    "sizesweep": ("config_size_sweep", 1, 7,
+                  "graph-size scaling: pairs of G(n, 0.4) graphs with n vertices, 4 vertex "
+                  "labels, K=5,000, setting-1 costs"),
 }
 _ARGS = None
 
@@ -123,7 +129,8 @@ def workload(rank: int, n_pairs: int):
     from paper_2605_00830_gb300 import workloads as W
     fn, full, seed0, _ = WORKLOADS[_ARGS.workload]
     seed = seed0 if rank == 0 else seed0 + 7919 * rank
-    w = getattr(W, fn)(n_pairs or full, seed=seed)
+    extra = {"n": getattr(_ARGS, "n", 950)} if fn == "config_size_sweep" else {}
+    w = getattr(W, fn)(n_pairs or full, seed=seed, **extra)
     if getattr(_ARGS, "k", 0):
         w.K = _ARGS.k
     return w

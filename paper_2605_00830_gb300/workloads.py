@@ -331,6 +331,20 @@ def config_wide_beam(n_pairs: int = 16, seed: int = 6, K: int = 100000) -> Workl
     return Workload(f"molecule_n18-22_K{K}", graphs, pairs, SETTING1_COSTS, K)
 
 
+def config_size_sweep(n_pairs: int = 1, seed: int = 7, n: int = 950, K: int = 5000,
+                      density: float = 0.4) -> Workload:
+    """Scaling with graph size (the paper's Fig. 4d setting): pairs of random G(n, 0.4)
+    graphs with n vertices each, 4 uniform vertex labels, unlabelled edges, the paper's
+    setting-1 costs, K = 5,000."""
+    graphs = []
+    for p in range(n_pairs):
+        for role in (0, 1):
+            st = Stream(seed, 7, n, p, role)
+            graphs.append(erdos_renyi(st, n, density, 4))
+    pairs = np.arange(2 * n_pairs, dtype=np.int32).reshape(-1, 2)
+    return Workload(f"er_n{n}_d{density}_K{K}", graphs, pairs, SETTING1_COSTS, K)
+
+
 def config5(duration_s: float = 60.0, rate: float = 5000.0, seed: int = 5,
             max_requests: Optional[int] = None) -> Workload:
     """Serving stream: Poisson arrivals at `rate` req/s for `duration_s`; 70 % molecule-like

@@ -205,7 +205,7 @@ def test_bench_under_two_ranks(tmp_path):
     assert d["config"]["parallelism"] == "replicas2"
 
 
-@pytest.mark.parametrize("workload,pairs", [("dense", 6), ("large", 2)])
+@pytest.mark.parametrize("workload,pairs", [("dense", 6), ("large", 2), ("sizesweep", 1)])
 def test_other_workloads_keep_the_oracle_legs_bounded(monkeypatch, capsys, fake_smi,
                                                       workload, pairs):
     """On the slower batches the oracle legs stop at their time bound, or are skipped (with
@@ -216,14 +216,14 @@ def test_other_workloads_keep_the_oracle_legs_bounded(monkeypatch, capsys, fake_
                                           "--serve-window", "0.05", "--cpu-seconds", "1"])
     for key in ("cpu_baseline", "cpu_baseline_1core"):
         leg = d[key]
-        if workload == "large":
+        if workload in ("large", "sizesweep"):
             assert leg["value"] is None and leg["sample"].startswith("skipped")
         else:
             assert leg["value"] > 0 and leg["sample"].startswith("first ")
     r = _run_bench(monkeypatch, capsys, ["--impl", "reference", "--workload", workload,
                                           "--pairs", str(pairs), "--steps", "1", "--warmup", "0",
                                           "--cpu-seconds", "1"])
-    if workload == "large":
+    if workload in ("large", "sizesweep"):
         assert r == {"impl": "reference", "unavailable": r["unavailable"]}
         assert "skipped" in r["unavailable"]
     else:
