@@ -104,9 +104,9 @@ def test_every_query_completes_once(lib):
 
 
 def test_batches_stop_at_the_size_limit(lib):
-    # one lane whose batches take 20 ms: while the first runs, the rest of 300 queries of one
+    # one lane whose batches take 100 ms: while the first runs, the rest of 300 queries of one
     # size bucket queue up, so every later batch is cut at max_batch_pairs
-    lib.fake_set_host_fn_delay_us(20000)
+    lib.fake_set_host_fn_delay_us(100000)
     w = W.config2(1200, seed=8)
     keep = [p for p in range(w.n_pairs) if w.graphs[int(w.pairs[p][1])].n <= 32][:300]
     w = W.subset(w, keep)
@@ -254,7 +254,9 @@ def test_cancel_queued_queries(lib):
                          max_wait_us=10000000)
     srv = HostServer(lib, w.cost, cfg)
     _submit_all(srv, mm, w, kk, [0])
-    time.sleep(0.02)                           # the dispatcher launches it on the idle lane
+    t0 = time.time()                           # the dispatcher launches it on the idle lane
+    while srv.stats()["batches"] < 1 and time.time() - t0 < 10:
+        time.sleep(0.001)
     _submit_all(srv, mm, w, kk, range(1, 21))
     # a tag used twice: both queued copies go
     assert srv.submit(mm, w.pairs[5][0], w.pairs[5][1], int(kk[5]), 5) == F.FASTGED_OK
