@@ -1,7 +1,8 @@
 """ctypes front end for the plain C oracle (fastged_oracle.c).
 
-TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU baseline are
-the only callers. Nothing on the product path imports this module. The oracle shares no
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check, the benchmark's CPU baseline and the
+oracle's own accuracy report (accuracy_report.py) are the only callers. Nothing on the product
+path imports this module. The oracle shares no
 code with the CUDA path; its only common input is the graph description produced by the
 seeded workload generators (which hold none of the method's arithmetic).
 
