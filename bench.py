@@ -90,6 +90,11 @@ def parse_args():
                     help="beam width K for every pair (0 = the workload's own K)")
     ap.add_argument("--block", type=int, default=0,
                     help="threads per team for every size class (0 = autotuned)")
+    ap.add_argument("--team", choices=["auto", "cta"], default="auto",
+                    help="auto: one warp per pair where the pairs are small enough (default); "
+                         "cta: every pair solved by a CTA (or a cluster of CTAs)")
+    ap.add_argument("--hist-window", type=int, default=0,
+                    help="selection histogram window (0 = the kernels' default)")
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--cpu-sample", type=int, default=4000,
                     help="most pairs the CPU oracle legs run")
@@ -377,8 +382,10 @@ def ours(args):
     g = F.FastGED(w.cost)
     # the autotuner times each size class's team shapes once, outside the timed region
     # (--block fixes the team size instead, so that a profiler sees only the timed launches)
-    popt = (F.make_options(block_threads=args.block) if args.block else
-            F.make_options(autotune=1))
+    team = F.FASTGED_TEAM_CTA if args.team == "cta" else F.FASTGED_TEAM_AUTO
+    popt = (F.make_options(block_threads=args.block, team=team, hist_window=args.hist_window)
+            if args.block else
+            F.make_options(autotune=1, team=team, hist_window=args.hist_window))
     plan = F.fastged_plan_create(g.h, mm, w.K, popt)
     # a dedicated stream: the legacy default stream has handle 0, which the C ABI reads as
     # "the plan's own stream"
@@ -468,7 +475,7 @@ def ours(args):
         # barrier and the max over ranks bracket it like the device-timed region
         cst, mp, nv = (np.zeros(mm.n_pairs, np.int32), np.zeros(int(mm.map_off[-1]), np.int32),
                        np.zeros(mm.n_pairs, np.int64))
-        opt = F.make_options()
+        opt = F.make_options(team=team, hist_window=args.hist_window)
         F.fastged_batch_ex(g.h, mm, w.K, opt, cst, mp, nv)
         n_e2e = max(1, min(args.steps, 5))
         if ws > 1:
@@ -491,7 +498,8 @@ def ours(args):
         ws_ = W.subset(w, range(min(args.plain_sample, w.n_pairs)))
         mms = F.marshal(ws_)
         pplan = F.fastged_plan_create(g.h, mms, w.K, F.make_options(form=F.FASTGED_FORM_PLAIN,
-                                                                     use_cuda_graph=0))
+                                                                     use_cuda_graph=0,
+                                                                     team=team))
         F.fastged_plan_run(pplan, stream.cuda_stream)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -114,7 +114,14 @@ typedef struct {
                              /* FASTGED_ORDER_DEGREE (1: descending degree, ties by index;    */
                              /* an extension, not part of the paper). Maps are returned in   */
                              /* source index order either way                                 */
+    int32_t team;            /* FASTGED_TEAM_AUTO (0): pairs with at most 64 vertices in g1   */
+                             /* and g2 and K <= 128 are solved by one warp each, the others   */
+                             /* by a CTA (or a cluster of CTAs) each; FASTGED_TEAM_CTA (1):   */
+                             /* every pair by a CTA or cluster. Results do not depend on it   */
 } fastged_options;
+
+#define FASTGED_TEAM_AUTO 0
+#define FASTGED_TEAM_CTA  1
 
 #define FASTGED_ORDER_INDEX 0
 #define FASTGED_ORDER_DEGREE 1

@@ -65,6 +65,43 @@ struct Layout {
     int64_t cta_off, cta_bytes;
 };
 
+// One-warp teams (kbest_warp_kernel): every warp of a CTA solves its own pair in its own
+// block of shared memory; the two vertex-map buffers are in that block too, or in the warp's
+// block of global scratch (gmap). Offsets are in bytes from the start of the block.
+enum WarpRegion : int {
+    WR_TGT = 0,   // g2 records: adjacency word, label planes, cost-row entry (n2 + 1 of them)
+    WR_LAB2,      // g2 vertex labels, int32[n2]
+    WR_NOFF,      // g1 prior-neighbour list offsets, int32[n1 + 1]
+    WR_NBR,       // g1 prior-neighbour lists, int32[m1]: k | edge label << 16
+    WR_IMG0, WR_IMG1,     // Img bitset of every kept node, Word[K], two beam buffers
+    WR_PED0, WR_PED1,     // PED of every kept node, int32[K]
+    WR_E20, WR_E21,       // g2 edges with both ends in Img, uint16[K]
+    WR_ENT,       // successor entries of a level in enumeration order, uint16[K * (n2 + 1)]
+    WR_NODEOFF,   // first entry of every node, uint16[K + 1]
+    WR_KLIST,     // kept successors, uint32[K]: PED offset << 16 | entry index
+    WR_SEL,       // selected children in key order, int32[K]: parent slot << 8 | j
+    WR_SELPED,    // their PEDs, int32[K]
+    WR_MAP0, WR_MAP1,     // vertex maps of the kept nodes, uint8[K][mrow]
+    WR_COUNT
+};
+
+// bytes of one target record of the one-warp kernel: one bitset word for the adjacency, npl
+// label planes and the 32-bit cost-row entry, padded to 16 bytes (vector loads)
+constexpr int warp_rec_bytes(bool w32, int npl)
+{
+    return ((w32 ? 4 : 8) * (1 + npl) + 4 + 15) / 16 * 16;
+}
+
+struct WarpLayout {
+    int32_t off[WR_COUNT];
+    int32_t warp_bytes;   // shared memory per warp
+    int32_t gmap;         // 1: WR_MAP0 / WR_MAP1 are offsets into the warp's global block
+    int32_t gmap_bytes;   // bytes of that global block (0 when the maps are in shared memory)
+    int32_t mrow;         // bytes per stored vertex map (a multiple of 16)
+    int32_t ent_dummy;    // entry index past every level's successors (kmax * (n2max + 1)):
+                          // where lanes without a successor at a step store
+};
+
 struct KParams {
     // batch inputs
     const GraphMeta *gmeta;
@@ -90,6 +127,7 @@ struct KParams {
     // scratch
     uint8_t *gscratch;
     Layout lay;
+    WarpLayout wl;               // one-warp teams only
     // per-phase cycle counters; profiling builds only (nullptr otherwise)
     unsigned long long *phase_cycles;
 };

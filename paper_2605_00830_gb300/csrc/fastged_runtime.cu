@@ -10,6 +10,9 @@
 // and by the width of a stored vertex-map entry (8 or 16 bits). Each class gets a region
 // plan: the per-team working set is split into regions placed in shared memory in order
 // of access frequency; what does not fit goes to a per-team slice of global scratch.
+// Pairs of single-word classes with small graphs and beams (n1, n2 <= 64, K <= 128) form
+// their own classes solved by one warp per pair (several warps per CTA, each with its own
+// block of shared memory).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +48,9 @@ cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int c
 size_t team_shared_cluster_bytes();
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
+cudaError_t launch_kbest_warp(bool w32, int bk, const KParams &p, int grid, int block,
+                              size_t smem, cudaStream_t st);
+cudaError_t kbest_warp_occupancy(bool w32, int bk, int block, size_t smem, int *out);
 }  // namespace fastged
 
 using namespace fastged;
@@ -472,6 +478,52 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
     L.slice_bytes = (int64_t)align_up(g_used, 256);
 }
 
+size_t fastged::plan_warp_layout(ClassPlan &cp, int B, bool gmap)
+{
+    WarpLayout &wl = cp.wl;
+    const int npl = label_instance(B);
+    const size_t rec = (size_t)warp_rec_bytes(cp.w32, npl);
+    const size_t wb = cp.w32 ? 4 : 8;
+    const size_t km = (size_t)cp.kmax, n2 = (size_t)cp.n2max, n1 = (size_t)cp.n1max;
+    wl.mrow = (int32_t)align_up(std::max<size_t>(n1, 1), 16);
+    size_t sz[WR_COUNT];
+    sz[WR_TGT] = (n2 + 1) * rec;
+    sz[WR_LAB2] = std::max<size_t>(n2, 1) * 4;
+    sz[WR_NOFF] = (n1 + 1) * 4;
+    sz[WR_NBR] = (size_t)std::max(cp.m1max, 1) * 4;
+    sz[WR_IMG0] = sz[WR_IMG1] = km * wb;
+    sz[WR_PED0] = sz[WR_PED1] = km * 4;
+    sz[WR_E20] = sz[WR_E21] = km * 2;
+    sz[WR_ENT] = (km * (n2 + 1) + 1) * 2;   // + the slot idle lanes store to
+    wl.ent_dummy = (int32_t)(km * (n2 + 1));
+    sz[WR_NODEOFF] = (km + 1) * 2;
+    sz[WR_KLIST] = km * 4;
+    sz[WR_SEL] = km * 4;
+    sz[WR_SELPED] = km * 4;
+    sz[WR_MAP0] = sz[WR_MAP1] = km * (size_t)wl.mrow;
+    size_t sh = 0, gl = 0;
+    for (int r = 0; r < WR_COUNT; ++r) {
+        const size_t a = align_up(sz[r], 16);
+        if (gmap && (r == WR_MAP0 || r == WR_MAP1)) {
+            wl.off[r] = (int32_t)gl;
+            gl += a;
+        } else {
+            wl.off[r] = (int32_t)sh;
+            sh += a;
+        }
+    }
+    wl.warp_bytes = (int32_t)sh;
+    wl.gmap = gmap ? 1 : 0;
+    wl.gmap_bytes = gmap ? (int32_t)align_up(gl, 256) : 0;
+    cp.lay.B = B;
+    cp.lay.kmax = cp.kmax;
+    cp.lay.n1max = cp.n1max;
+    cp.lay.n2max = cp.n2max;
+    cp.lay.word_bytes = (int32_t)wb;
+    cp.lay.pk = 1;
+    return sh;
+}
+
 static size_t layout_total(const ClassPlan &cp, int B, int block)
 {
     ClassPlan t = cp;
@@ -485,6 +537,7 @@ static size_t layout_total(const ClassPlan &cp, int B, int block)
 struct TuneChoice {
     int block = 0;
     int cluster = 1;
+    int gmap = -1;   // one-warp classes: 1 = vertex maps in global scratch, 0 = shared memory
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune;
@@ -502,10 +555,9 @@ static int pow2_ceil(int x)
 static std::string class_key(const ClassPlan &cp, int B, int npairs, int sm_count)
 {
     char buf[128];
-    snprintf(buf, sizeof(buf), "w%d%s%s%s_b%d_k%d_n%d_%s", cp.W, cp.wide ? "x" : "",
-             cp.w32 ? "h" : "", cp.pk ? "p" : "", label_instance(B), pow2_ceil(cp.kmax),
-             pow2_ceil(cp.n2max),
-             npairs < sm_count ? "few" : "many");
+    snprintf(buf, sizeof(buf), "%sw%d%s%s%s_b%d_k%d_n%d_%s", cp.warp ? "warp_" : "", cp.W,
+             cp.wide ? "x" : "", cp.w32 ? "h" : "", cp.pk ? "p" : "", label_instance(B),
+             pow2_ceil(cp.kmax), pow2_ceil(cp.n2max), npairs < sm_count ? "few" : "many");
     return buf;
 }
 
@@ -517,12 +569,15 @@ static void tune_load_locked()
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char key[128];
-    int block = 0, cluster = 1;
-    while (fscanf(f, "%127s %d %d", key, &block, &cluster) == 3) {
+    // one entry per line: key, threads per CTA, CTAs per team, map placement, time in ms
+    char line[256], key[128];
+    while (fgets(line, sizeof(line), f)) {
+        int block = 0, cluster = 1, gmap = -1;
+        if (sscanf(line, "%127s %d %d %d", key, &block, &cluster, &gmap) != 4) continue;
         TuneChoice c;
         c.block = block;
         c.cluster = cluster;
+        c.gmap = gmap;
         g_tune[key] = c;
     }
     fclose(f);
@@ -551,7 +606,7 @@ static void tune_store(const std::string &key, const TuneChoice &c, double ms)
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %.4f\n", key.c_str(), c.block, c.cluster, ms);
+    fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), c.block, c.cluster, c.gmap, ms);
     fclose(f);
 }
 
@@ -581,8 +636,47 @@ static bool cluster_eligible(const ClassPlan &cp, int npairs, int sm_count)
 // Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
 // Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
 // CTAs per pair.
+// One-warp classes: warps per CTA (threads / 32, at most 8) and where the vertex maps live.
+// Without a tuning entry the maps stay in shared memory when that still leaves room for 16
+// warps per SM, and CTAs hold 4 warps.
+static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
+{
+    const int npairs = (int)std::max<size_t>(cp.order.size(), 1);
+    TuneChoice tc;
+    const bool tuned = tune_lookup(class_key(cp, B, npairs, h->sm_count), &tc);
+    int block = forced_block ? forced_block : (tuned && tc.block ? tc.block : 128);
+    bool gmap;
+    if (tuned && tc.gmap >= 0) {
+        gmap = tc.gmap != 0;
+    } else {
+        const size_t shared_maps = plan_warp_layout(cp, B, false);
+        gmap = (size_t)h->smem_per_sm / std::max<size_t>(shared_maps, 1) < 16;
+    }
+    const size_t wbytes = plan_warp_layout(cp, B, gmap);
+    // at most 8 warps per CTA (the kernel's launch bound is 256 threads)
+    int wpc = std::min(8, std::max(1, block / 32));
+    while (wpc > 1 && (size_t)wpc * wbytes > (size_t)h->smem_optin) wpc >>= 1;
+    if ((size_t)wpc * wbytes > (size_t)h->smem_optin)
+        return set_error(FASTGED_ERR_CUDA, "a one-warp team does not fit shared memory");
+    block = wpc * 32;
+    int occ = 0;
+    cudaError_t e = kbest_warp_occupancy(cp.w32, label_instance(B), block, (size_t)wpc * wbytes,
+                                         &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ < 1) return set_error(FASTGED_ERR_CUDA, "one-warp teams do not fit on an SM");
+    cp.block = block;
+    cp.smem = (size_t)wpc * wbytes;
+    cp.all_smem = !gmap;
+    cp.lay.smem_bytes = (int64_t)cp.smem;
+    cp.lay.slice_bytes = gmap ? (int64_t)wpc * cp.wl.gmap_bytes : 0;
+    const int64_t need = ((int64_t)cp.order.size() + wpc - 1) / wpc;
+    cp.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * occ, need));
+    return FASTGED_OK;
+}
+
 static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
 {
+    if (cp.warp) return tune_warp_class(h, cp, B, forced_block);
     const size_t stat = team_shared_static_bytes() + 1024;   // + per-block reservation
     const size_t per_sm = (size_t)h->smem_per_sm;
     const size_t max_dyn = (size_t)h->smem_optin - team_shared_static_bytes();
@@ -719,6 +813,8 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         return set_error(FASTGED_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
     if (opt.vertex_order != FASTGED_ORDER_INDEX && opt.vertex_order != FASTGED_ORDER_DEGREE)
         return set_error(FASTGED_ERR_INVALID_ARG, "vertex_order must be 0 or 1");
+    if (opt.team != FASTGED_TEAM_AUTO && opt.team != FASTGED_TEAM_CTA)
+        return set_error(FASTGED_ERR_INVALID_ARG, "team must be 0 or 1");
     b.perm.clear();
     Reordered ro;
     if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
@@ -815,7 +911,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     constexpr int kKeys = 32, kBuckets = 64 * 16;
     struct KeyClass {
         int first = INT_MAX;   // first pair of this class key
-        int8_t W = 1, wide = 0, w32 = 0, pk = 0;
+        int8_t W = 1, wide = 0, w32 = 0, pk = 0, warp = 0;
         int n1max = 0, n2max = 0, m1max = 0, kmax = 1;
         int bmin = kBuckets, bmax = -1;
     };
@@ -852,7 +948,11 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             const bool pk = packable(ped_bound, kp, g2.n);
             if (W == 1 && !pk) W = 2;
             const bool wide = g2.n >= 255, w32 = W == 1 && g2.n <= 32;
-            const int key =
+            // one warp per pair: single-word, packable pairs with small source graphs and
+            // beams, variant A
+            const bool warp = opt.team == FASTGED_TEAM_AUTO && opt.variant == 0 && W == 1 &&
+                              g1.n <= kWarpMaxN && kp <= kWarpMaxK;
+            const int key = warp ? 22 + (w32 ? 1 : 0) :
                 (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
                 (pk ? 1 : 0);
             const double wt = (double)g1.n *
@@ -871,6 +971,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
                 kc.wide = (int8_t)wide;
                 kc.w32 = (int8_t)w32;
                 kc.pk = (int8_t)pk;
+                kc.warp = (int8_t)warp;
             }
             kc.n1max = std::max(kc.n1max, g1.n);
             kc.m1max = std::max(kc.m1max, g1.m);
@@ -898,6 +999,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
                     y.wide = x.wide;
                     y.w32 = x.w32;
                     y.pk = x.pk;
+                    y.warp = x.warp;
                 }
                 y.n1max = std::max(y.n1max, x.n1max);
                 y.m1max = std::max(y.m1max, x.m1max);
@@ -921,6 +1023,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
             cp.wide = y.wide || y.W >= 8;
             cp.w32 = y.w32;
             cp.pk = y.pk;
+            cp.warp = y.warp;
             cp.n1max = y.n1max;
             cp.m1max = y.m1max;
             cp.n2max = y.n2max;
@@ -1108,7 +1211,7 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     p.n_order = (int32_t)cp.order.size();
     p.kpp = b.has_kpp ? (const int32_t *)(in + b.off_kpp) : nullptr;
     p.K = b.K;
-    p.hwin = b.opt.hist_window ? b.opt.hist_window : kHistMax;
+    p.hwin = b.opt.hist_window ? b.opt.hist_window : (cp.warp ? kWarpHist : kHistMax);
     p.variant = b.opt.variant;
     p.cost.vsub = h->cost.v_sub;
     p.cost.vdel = h->cost.v_del;
@@ -1124,6 +1227,7 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     p.out_nevals = (int64_t *)(wk + b.woff_nev);
     p.gscratch = wk + b.woff_scratch + cp.scratch_off;
     p.lay = cp.lay;
+    p.wl = cp.wl;
 #ifdef FASTGED_PHASE_TIMERS
     if (!g_phase_dev && cudaMalloc(&g_phase_dev, 128) == cudaSuccess) cudaMemset(g_phase_dev, 0, 128);
     p.phase_cycles = g_phase_dev;
@@ -1174,7 +1278,10 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             p.order += pos[pr];
             p.n_order = 1;
             p.queue_head = qbase + pr;
-            if (cp.cluster > 1)
+            if (cp.warp)
+                CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, 1, 32, (size_t)cp.wl.warp_bytes,
+                                     st));
+            else if (cp.cluster > 1)
                 CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.cluster, cp.block, cp.smem,
                                         cp.cluster, st));
             else
@@ -1185,7 +1292,9 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
     } else if (nc == 1) {
         const ClassPlan &cp = b.classes[0];
         KParams p = make_params(h, b, 0, in, wk);
-        if (cp.cluster > 1)
+        if (cp.warp)
+            CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, cp.grid, cp.block, cp.smem, st));
+        else if (cp.cluster > 1)
             CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
                                     cp.cluster, st));
         else
@@ -1198,7 +1307,10 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
             const ClassPlan &cp = b.classes[k];
             CK(cudaStreamWaitEvent(h->class_stream[k], h->ev[kMaxClasses], 0));
             KParams p = make_params(h, b, k, in, wk);
-            if (cp.cluster > 1)
+            if (cp.warp)
+                CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
+                                     h->class_stream[k]));
+            else if (cp.cluster > 1)
                 CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
                                         cp.cluster, h->class_stream[k]));
             else
@@ -1347,7 +1459,15 @@ static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_
             if (it != g_tune.end()) continue;
         }
         std::vector<TuneChoice> cands;
-        if (cluster_eligible(cp, npairs, h->sm_count)) {
+        if (cp.warp) {
+            for (int gm : {0, 1})
+                for (int bt : {64, 128, 256}) {
+                    TuneChoice c;
+                    c.block = bt;
+                    c.gmap = gm;
+                    cands.push_back(c);
+                }
+        } else if (cluster_eligible(cp, npairs, h->sm_count)) {
             for (int cl : {1, 4, 8, 16}) {
                 TuneChoice c;
                 c.block = cl == 1 ? 256 : 512;

@@ -38,6 +38,8 @@ struct ClassPlan {
     bool pk = false;              // successors packed into one 32-bit entry (see packable)
     bool all_smem = false;        // every region of a team fits in shared memory
     int cluster = 1;              // CTAs per team (> 1: a thread-block cluster per pair)
+    bool warp = false;            // one warp per pair (kbest_warp_kernel; W == 1, small K)
+    WarpLayout wl{};              // layout of one warp's working set (warp classes)
     int n1max = 0, n2max = 0, m1max = 0, kmax = 1;
     std::vector<int32_t> order;   // pair indices, heaviest first
     int64_t order_off = 0;        // offset of this class's order in the device order array
@@ -74,6 +76,15 @@ int set_error(int code, const char *msg);
 // splits a team's working set into shared-memory and global-scratch regions (budget bytes of
 // shared memory, filled in order of access frequency)
 void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
+// lays out one warp's working set for a one-warp class; gmap puts the vertex maps in global
+// scratch. Returns the shared-memory bytes per warp.
+size_t plan_warp_layout(ClassPlan &cp, int B, bool gmap);
+// one-warp teams: largest K and largest graphs (vertices of g1 and g2) they take
+constexpr int kWarpMaxK = 128;
+constexpr int kWarpMaxN = 64;
+// default histogram window of the one-warp kernel (its PED offsets are counted by bit ballots,
+// one per bit of the bucket index)
+constexpr int kWarpHist = 16;
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);
 // One-shot host-side fault injection (fastged_inject_fault): true when the armed fault of

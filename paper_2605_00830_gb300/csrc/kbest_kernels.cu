@@ -2,15 +2,17 @@
 // kernel instances.
 //
 //   pack_kernel   S0: edge lists -> adjacency bitsets and edge-label bit-planes
-//   launch_kbest / kbest_occupancy / launch_kbest_cluster / kbest_cluster_occupancy:
+//   launch_kbest / kbest_occupancy / launch_kbest_cluster / kbest_cluster_occupancy /
+//   launch_kbest_warp / kbest_warp_occupancy:
 //                 pick the instance (words per bitset, map entry width, all-shared-memory or
-//                 not, label planes) of the S1-S5 kernels in kbest_impl.cuh, which are
-//                 compiled in kbest_b0.cu, kbest_b2.cu and kbest_b8.cu.
+//                 not, label planes) of the S1-S5 kernels in kbest_impl.cuh (one-CTA and
+//                 cluster teams) and kbest_warp.cuh (one-warp teams), which are compiled in
+//                 kbest_b0.cu, kbest_b2.cu and kbest_b8.cu.
 //
 // Method: Algorithm 1 of Dabah & Herten (branching Sec. 4.1.1, evaluation Sec. 4.1.2 and
 // Algorithm 2, selection Sec. 4.2, leaf insertions Sec. 4.4); kbest_impl.cuh states how the
 // implied edge costs are computed from bitsets.
-#include "kbest_impl.cuh"
+#include "kbest_warp.cuh"
 
 namespace fastged {
 
@@ -58,7 +60,10 @@ bool kbest_has_smem_variant(int W, bool wide, bool w32) { return w32 || (W <= 4 
                                                        int *);                                 \
     extern template cudaError_t launch_kbest_cluster_bk<BK>(int, const KParams &, int, int,     \
                                                             size_t, int, cudaStream_t);        \
-    extern template cudaError_t kbest_cluster_occupancy_bk<BK>(int, int, size_t, int, int *);
+    extern template cudaError_t kbest_cluster_occupancy_bk<BK>(int, int, size_t, int, int *);  \
+    extern template cudaError_t launch_kbest_warp_bk<BK>(bool, const KParams &, int, int,       \
+                                                         size_t, cudaStream_t);                \
+    extern template cudaError_t kbest_warp_occupancy_bk<BK>(bool, int, size_t, int *);
 FASTGED_EXTERN_BK(0)
 FASTGED_EXTERN_BK(2)
 FASTGED_EXTERN_BK(8)
@@ -105,6 +110,22 @@ cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int c
     if (bk == 0) return kbest_cluster_occupancy_bk<0>(W, block, smem, cluster, out);
     if (bk == 2) return kbest_cluster_occupancy_bk<2>(W, block, smem, cluster, out);
     return kbest_cluster_occupancy_bk<8>(W, block, smem, cluster, out);
+}
+
+// one-warp teams (kbest_warp.cuh): w32 = one 32-bit bitset word, else one 64-bit word
+cudaError_t launch_kbest_warp(bool w32, int bk, const KParams &p, int grid, int block,
+                              size_t smem, cudaStream_t st)
+{
+    if (bk == 0) return launch_kbest_warp_bk<0>(w32, p, grid, block, smem, st);
+    if (bk == 2) return launch_kbest_warp_bk<2>(w32, p, grid, block, smem, st);
+    return launch_kbest_warp_bk<8>(w32, p, grid, block, smem, st);
+}
+
+cudaError_t kbest_warp_occupancy(bool w32, int bk, int block, size_t smem, int *out)
+{
+    if (bk == 0) return kbest_warp_occupancy_bk<0>(w32, block, smem, out);
+    if (bk == 2) return kbest_warp_occupancy_bk<2>(w32, block, smem, out);
+    return kbest_warp_occupancy_bk<8>(w32, block, smem, out);
 }
 
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st)

@@ -1,0 +1,673 @@
+// kbest_warp.cuh -- sm_103a K-Best kernel with one warp per pair, for pairs whose target graph
+// fits one bitset word (n2 <= 64), whose source has at most 64 vertices and whose beam is
+// small (the molecule-like batches). Instantiated per edge-label plane count in kbest_b0.cu,
+// kbest_b2.cu and kbest_b8.cu next to the team kernels of kbest_impl.cuh.
+//
+// Method: Algorithm 1 of Dabah & Herten (branching Sec. 4.1.1, evaluation Sec. 4.1.2 and
+// Algorithm 2, selection Sec. 4.2, leaf insertions Sec. 4.4), with the bitset form of the
+// implied edge costs stated at the top of kbest_impl.cuh. Results are identical to the team
+// kernels' (same key order, same tie-breaking); only the mapping onto the hardware differs:
+//
+//   * a warp owns a pair, so a level needs no block barrier and no cross-warp table;
+//   * evaluation runs lane <-> parent node: each lane keeps its node's vectors (Img, P, label
+//     planes of P, base PED) in registers and walks the node's free target vertices in
+//     increasing order, so no successor-id list is built; every step of that walk scores one
+//     successor per lane against the staged target record of its vertex, without branches;
+//   * the PED histogram of the selection is counted in the same loop in per-lane 4-bit
+//     counters (16 buckets, widened to 16 bits every 15 steps and summed over the warp once
+//     per level), anchored at the PED of the best parent, a lower bound of every child (costs
+//     are non-negative and slot 0 holds the least PED of the kept list);
+//   * each successor leaves one 16-bit entry (PED offset clamped to 8 bits, j) in enumeration
+//     order (node by node, j increasing, the deletion last); the kept ones are compacted in
+//     that order and then placed at their rank by a counting sort over the buckets;
+//   * when the K-th PED falls past the histogram window, the level is scored again with exact
+//     16-bit PED offsets (every PED of a pair routed here is below 2^16), the K-th offset is
+//     found by bisection, the kept entries are ranked by (PED, enumeration order) and their
+//     target vertices recovered from the node's free set.
+#pragma once
+#include "kbest_impl.cuh"
+
+namespace fastged {
+
+// PED histogram buckets of the one-warp kernel: offsets 0..kWarpBuckets-2 from the anchor,
+// and one bucket for everything past them
+constexpr int kWarpBuckets = 16;
+// kept successors a warp places at once: the largest K of a one-warp class, in 32s
+constexpr int kWarpChunks = 4;
+
+// Target record of g2 vertex u (u < n2), or of the deletion column u = n2 (no neighbours, no
+// labels): adjacency word, NPL edge-label planes, and the vertex-cost entry C[i][u] of the
+// current level.
+template <typename Word, int NPL>
+struct __align__(16) TgtRec {
+    Word a2;
+    Word l[NPL];
+    int32_t crow;
+};
+template <typename Word>
+struct __align__(16) TgtRec<Word, 0> {
+    Word a2;
+    int32_t crow;
+};
+
+static_assert(sizeof(TgtRec<uint32_t, 0>) == warp_rec_bytes(true, 0), "record size");
+static_assert(sizeof(TgtRec<uint32_t, 2>) == warp_rec_bytes(true, 2), "record size");
+static_assert(sizeof(TgtRec<uint32_t, kMaxB>) == warp_rec_bytes(true, kMaxB), "record size");
+static_assert(sizeof(TgtRec<uint64_t, 0>) == warp_rec_bytes(false, 0), "record size");
+static_assert(sizeof(TgtRec<uint64_t, 2>) == warp_rec_bytes(false, 2), "record size");
+static_assert(sizeof(TgtRec<uint64_t, kMaxB>) == warp_rec_bytes(false, kMaxB), "record size");
+
+template <typename Word, int NPL>
+__device__ __forceinline__ Word rec_plane(const TgtRec<Word, NPL> &r, int b) { return r.l[b]; }
+template <typename Word>
+__device__ __forceinline__ Word rec_plane(const TgtRec<Word, 0> &, int) { return (Word)0; }
+template <typename Word, int NPL>
+__device__ __forceinline__ void rec_set_plane(TgtRec<Word, NPL> &r, int b, Word v) { r.l[b] = v; }
+template <typename Word>
+__device__ __forceinline__ void rec_set_plane(TgtRec<Word, 0> &, int, Word) {}
+
+#ifdef FASTGED_PHASE_TIMERS
+// profiling builds only: cycles lane 0 of every warp spends in each phase
+#define WPHASE(k)                                            \
+    do {                                                     \
+        if ((threadIdx.x & 31) == 0) {                       \
+            const long long t_ = clock64();                  \
+            ph[k] += t_ - ph_last;                           \
+            ph_last = t_;                                    \
+        }                                                    \
+    } while (0)
+#else
+#define WPHASE(k) do { } while (0)
+#endif
+
+__device__ __forceinline__ int ffsw(uint32_t x) { return __ffs((int)x) - 1; }
+__device__ __forceinline__ int ffsw(uint64_t x) { return __ffsll((long long)x) - 1; }
+
+// Working set of one warp (see WarpRegion).
+template <typename Word, int NPL>
+struct WarpRegs {
+    TgtRec<Word, NPL> *tgt;
+    int32_t *lab2, *noff, *nbr;
+    Word *imgc, *imgn;          // current / next beam buffers, swapped after every level
+    int32_t *pedc, *pedn;
+    uint16_t *e2c, *e2n;
+    uint8_t *mapc, *mapn;
+    uint16_t *ent, *nodeoff;
+    uint32_t *klist;
+    int32_t *sel, *selped;
+    int ent_dummy;              // an entry slot past every level's entries (stores of idle lanes)
+};
+
+// Scores every successor of level i (lane <-> parent node). Entries go to ent in enumeration
+// order and nodeoff receives each node's first entry. EXACT = false: entry = (min(PED - A,
+// 255) << 8) | j, and on return lane b < kWarpBuckets holds the number of successors whose
+// offset min(PED - A, H - 1) is b; EXACT = true: entry = PED - A (exact, below 2^16).
+// FOLD: insertion and deletion of an edge cost the same, so the two implied-edge terms are
+// one popcount. Returns the number of successors of the level.
+template <typename Word, int BK, bool FOLD, bool EXACT>
+__device__ __forceinline__ int eval_level(const KParams &p,
+                                          const WarpRegs<Word, (BK == 8 ? kMaxB : BK)> &R,
+                                          int L, int n0, int deg, int n2, int mrow, int A, int H,
+                                          int &hist)
+{
+    constexpr int WB = 8 * (int)sizeof(Word);
+    constexpr int NPL = BK == 8 ? kMaxB : BK;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
+    const int c_eins = p.cost.eins, c_edel = p.cost.edel, c_esub = p.cost.esub;
+    const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
+    const uint8_t *mapc = R.mapc;
+    const TgtRec<Word, NPL> *tgt = R.tgt;
+    uint16_t *dummy = R.ent + R.ent_dummy;
+    // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 15 steps into
+    // acc[m] = buckets (m, m + 4) and acc[4 + m] = (8 + m, 12 + m), 16 bits each
+    uint32_t clo = 0, chi = 0, acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0;
+    int since = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            acc[m] += (clo >> (4 * m)) & 0x000F000Fu;
+            acc[4 + m] += (chi >> (4 * m)) & 0x000F000Fu;
+        }
+        clo = chi = 0;
+        since = 0;
+    };
+    int tot = 0;
+    for (int g0 = 0; g0 < L; g0 += 32) {
+        const int s = g0 + lane;
+        const bool act = s < L;
+        // S2: P = images of the substituted g1 neighbours of v_i, their edge labels as planes
+        // at the image positions, dcnt = deleted neighbours (the neighbour list is the same
+        // for every lane: v_i's prior neighbours)
+        Word P = (Word)0;
+        Word PL[NPL > 0 ? NPL : 1];
+#pragma unroll
+        for (int b = 0; b < (NPL > 0 ? NPL : 1); ++b) PL[b] = (Word)0;
+        int dcnt = 0;
+        const uint8_t *ms = mapc + (int64_t)(act ? s : 0) * mrow;
+        for (int t0 = 0; t0 < deg; t0 += 4) {
+            int e[4];
+            uint8_t phi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr[n0 + t0 + u] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) phi[u] = (e[u] >= 0 && act) ? ms[e[u] & 0xffff] : (uint8_t)0xff;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool sub = phi[u] != 0xff;
+                dcnt += (e[u] >= 0 && !sub) ? 1 : 0;
+                const Word pb = sub ? (Word)1 << phi[u] : (Word)0;
+                P |= pb;
+#pragma unroll
+                for (int b = 0; b < NPL; ++b)
+                    if (b < B && ((e[u] >> (16 + b)) & 1)) PL[b] |= pb;
+            }
+        }
+        const Word im = act ? R.imgc[s] : ~(Word)0;
+        const int base = act ? R.pedc[s] + c_edel * dcnt - A : 0;
+        const int cnt = act ? n2 - popcw((Word)(im & nmask)) + 1 : 0;   // free vertices + deletion
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int off = tot + incl - cnt;
+        if (act) R.nodeoff[s] = (uint16_t)off;
+        const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
+        Word x = act ? (Word)(~im & nmask) : (Word)0;
+        uint16_t *ep = R.ent + off;
+        for (int t = 0; t < maxc; ++t) {
+            const bool val = t < cnt;
+            // next free vertex in increasing order; once none is left, the deletion (j = n2)
+            const int f = ffsw(x);
+            const int j = x ? f : n2;
+            x &= x - (Word)1;
+            const TgtRec<Word, NPL> r = tgt[j];
+            const Word ai = r.a2 & im;
+            int d = base + r.crow;
+            if (FOLD) {
+                d += c_eins * popcw((Word)(ai ^ P));
+            } else {
+                d += c_eins * popcw((Word)(ai & ~P)) + c_edel * popcw((Word)(P & ~r.a2));
+            }
+            if (NPL > 0) {
+                Word ld = (Word)0;
+#pragma unroll
+                for (int b = 0; b < NPL; ++b)
+                    if (b < B) ld |= PL[b] ^ rec_plane(r, b);
+                d += c_esub * popcw((Word)(r.a2 & P & ld));
+            }
+            uint16_t *dst = val ? ep + t : dummy;
+            if (EXACT) {
+                *dst = (uint16_t)d;
+            } else {
+                *dst = (uint16_t)((min(d, 255) << 8) | j);
+                const int dd = min(d, H - 1);
+                const uint32_t inc = val ? 1u << ((dd & 7) << 2) : 0u;
+                clo += dd < 8 ? inc : 0u;
+                chi += dd < 8 ? 0u : inc;
+                if (++since == 15) flush();
+            }
+        }
+        tot += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) R.nodeoff[L] = (uint16_t)tot;
+    if (!EXACT) {
+        flush();
+        // warp totals (at most 128 x 65 successors: 16-bit fields cannot overflow), then lane
+        // b takes bucket b
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(FULL, acc[m], o);
+        }
+        const int b = lane & 15;
+        const int wsel = ((b >> 3) << 2) | (b & 3);
+        uint32_t wv = acc[0];
+#pragma unroll
+        for (int m = 1; m < 8; ++m) wv = wsel == m ? acc[m] : wv;
+        hist = (int)((wv >> (((b >> 2) & 1) << 4)) & 0xffffu);
+    }
+    __syncwarp();
+    return tot;
+}
+
+// Slot of the node that owns entry k (nodeoff is strictly increasing: every node has at
+// least its deletion successor).
+__device__ __forceinline__ int node_of(const uint16_t *nodeoff, int L, int k)
+{
+    int lo = 0, hi = L;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)nodeoff[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Word, int BK, bool FOLD>
+__device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, uint8_t *gw,
+                                                const int pair)
+{
+    constexpr int NPL = BK == 8 ? kMaxB : BK;
+    constexpr int WB = 8 * (int)sizeof(Word);
+    using Rec = TgtRec<Word, NPL>;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const WarpLayout &wl = p.wl;
+    WarpRegs<Word, NPL> R;
+    R.tgt = (Rec *)(ws + wl.off[WR_TGT]);
+    R.lab2 = (int32_t *)(ws + wl.off[WR_LAB2]);
+    R.noff = (int32_t *)(ws + wl.off[WR_NOFF]);
+    R.nbr = (int32_t *)(ws + wl.off[WR_NBR]);
+    R.imgc = (Word *)(ws + wl.off[WR_IMG0]);
+    R.imgn = (Word *)(ws + wl.off[WR_IMG1]);
+    R.pedc = (int32_t *)(ws + wl.off[WR_PED0]);
+    R.pedn = (int32_t *)(ws + wl.off[WR_PED1]);
+    R.e2c = (uint16_t *)(ws + wl.off[WR_E20]);
+    R.e2n = (uint16_t *)(ws + wl.off[WR_E21]);
+    R.ent = (uint16_t *)(ws + wl.off[WR_ENT]);
+    R.nodeoff = (uint16_t *)(ws + wl.off[WR_NODEOFF]);
+    R.klist = (uint32_t *)(ws + wl.off[WR_KLIST]);
+    R.sel = (int32_t *)(ws + wl.off[WR_SEL]);
+    R.selped = (int32_t *)(ws + wl.off[WR_SELPED]);
+    R.ent_dummy = wl.ent_dummy;
+    uint8_t *mb = wl.gmap ? gw : ws;
+    R.mapc = mb + wl.off[WR_MAP0];
+    R.mapn = mb + wl.off[WR_MAP1];
+
+    const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
+    const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
+    const int n1 = m1.n, n2 = m2.n, W1 = m1.W;
+    const int K = p.kpp ? p.kpp[pair] : p.K;
+    const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
+    const int mrow = wl.mrow;
+    const CostModel c = p.cost;
+    // buckets 0..H-2 hold one PED offset each, H-1 the rest
+    const int H = min(p.hwin, kWarpBuckets);
+    constexpr uint8_t DEL = 0xff;
+    // m &= ballot(bit b of an offset) ^ lb[b] keeps the lanes whose bit b equals bit b of
+    // this lane's index
+    unsigned lb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lb[k] = ((lane >> k) & 1) ? 0u : 0xffffffffu;
+#ifdef FASTGED_PHASE_TIMERS
+    long long ph[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long ph_last = clock64();
+#endif
+
+    // ---- stage the target graph (records of u = 0..n2, the last one the deletion) and the
+    // source graph's prior-neighbour lists
+    {
+        const uint64_t *adj2 = p.adj + m2.adj_off;
+        const uint64_t *pl2 = p.planes + m2.plane_off;
+        const int W2 = m2.W;
+        for (int u = lane; u <= n2; u += 32) {
+            Rec r;
+            r.a2 = u < n2 ? (Word)adj2[(int64_t)u * W2] : (Word)0;
+#pragma unroll
+            for (int b = 0; b < NPL; ++b)
+                rec_set_plane(r, b, (u < n2 && b < B) ? (Word)pl2[((int64_t)b * n2 + u) * W2] : (Word)0);
+            r.crow = 0;
+            R.tgt[u] = r;
+            if (u < n2) R.lab2[u] = p.vlab[m2.lab_off + u];
+        }
+        // prior neighbours v_k (k < v) of every g1 vertex v, with their edge labels
+        for (int v = lane; v < n1; v += 32) {
+            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+            int d = 0;
+            for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
+            R.noff[v + 1] = d;
+        }
+        __syncwarp();
+        int carry = 0;
+        for (int v0 = 0; v0 < n1; v0 += 32) {
+            const int v = v0 + lane;
+            const int d = v < n1 ? R.noff[v + 1] : 0;
+            int incl = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            __syncwarp();
+            if (v < n1) R.noff[v + 1] = carry + incl;
+            carry += __shfl_sync(FULL, incl, 31);
+        }
+        if (lane == 0) R.noff[0] = 0;
+        __syncwarp();
+        const int64_t pstep = (int64_t)n1 * W1;
+        for (int v = lane; v < n1; v += 32) {
+            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+            const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
+            int o = R.noff[v];
+            for (int w = 0; w < W1; ++w) {
+                uint64_t bits = row[w] & low_mask(v, w);
+                while (bits) {
+                    const int t = __ffsll((long long)bits) - 1;
+                    bits &= bits - 1ull;
+                    int lab = 0;
+                    for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
+                    R.nbr[o++] = (w * 64 + t) | (lab << 16);
+                }
+            }
+        }
+        // root: empty map, Img empty, PED 0
+        if (lane == 0) {
+            R.imgc[0] = (Word)0;
+            R.pedc[0] = 0;
+            R.e2c[0] = 0;
+        }
+        __syncwarp();
+    }
+
+    long long nevals = 0;
+    int L = 1;
+    WPHASE(0);
+    for (int i = 0; i < n1; ++i) {
+        // S1: this level's vertex-cost row C[i][u] (the deletion column holds c_vdel)
+        {
+            const int a1 = p.vlab[m1.lab_off + i];
+            for (int u = lane; u <= n2; u += 32)
+                R.tgt[u].crow = u < n2 ? ((R.lab2[u] != a1) ? c.vsub : 0) : c.vdel;
+        }
+        __syncwarp();
+        WPHASE(7);
+        const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
+        const int A = R.pedc[0];   // least PED of the kept list: a lower bound of every child
+        int hist = 0;
+        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist);
+        nevals += tot;
+        WPHASE(1);
+        const int newL = min(K, tot);
+        // S4: bucket b = PED - A for b < H - 1, bucket H - 1 = everything past the window
+        const int cb = lane < H ? hist : 0;
+        int incl = cb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int bexcl = incl - cb;
+        const int thr = __ffs(__ballot_sync(FULL, lane < H && incl >= newL)) - 1;
+        if (thr < H - 1) {
+            // kept: every successor below bucket thr and the first q of bucket thr, compacted
+            // in enumeration order (the loop stops once all are found)
+            const int q = newL - __shfl_sync(FULL, bexcl, thr);
+            const int lim = (thr + 1) << 8;   // entry < lim <=> PED offset <= thr
+            int keep_before = 0, eq_before = 0;
+            for (int kb = 0; kb < tot && keep_before < newL; kb += 128) {
+                int e[4];
+                unsigned le[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kb + 32 * u + lane;
+                    e[u] = k < tot ? (int)R.ent[k] : 0xffff;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(FULL, e[u] < lim);
+                if ((le[0] | le[1] | le[2] | le[3]) == 0u) continue;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (le[u] == 0u) continue;
+                    const int d = e[u] >> 8;
+                    const bool is_eq = d == thr;
+                    const unsigned eqb = __ballot_sync(FULL, is_eq);
+                    const bool keep = (d < thr) || (is_eq && eq_before + __popc(eqb & lanemask_lt()) < q);
+                    const unsigned kbm = __ballot_sync(FULL, keep);
+                    if (keep)
+                        R.klist[keep_before + __popc(kbm & lanemask_lt())] =
+                            ((uint32_t)d << 16) | (uint32_t)(kb + 32 * u + lane);
+                    keep_before += __popc(kbm);
+                    eq_before += __popc(eqb);
+                }
+            }
+            __syncwarp();
+            WPHASE(3);
+            // place every kept successor at its rank: (smaller offsets) + (equal offsets
+            // earlier in enumeration order). All chunks of the kept list are handled at once;
+            // lane b carries the kept successors of bucket b in the chunks before each one.
+            uint32_t kv[kWarpChunks];
+            int dk[kWarpChunks], pos[kWarpChunks];
+            bool vk[kWarpChunks];
+            int run = 0;
+#pragma unroll
+            for (int ch = 0; ch < kWarpChunks; ++ch) {
+                const int x = 32 * ch + lane;
+                vk[ch] = x < newL;
+                kv[ch] = vk[ch] ? R.klist[x] : 0u;
+                dk[ch] = (int)(kv[ch] >> 16);
+            }
+#pragma unroll
+            for (int ch = 0; ch < kWarpChunks; ++ch) {
+                const unsigned V = __ballot_sync(FULL, vk[ch]);
+                // same: lanes whose offset equals this lane's; m: lanes whose offset is this
+                // lane's index
+                unsigned same = V, m = V;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const unsigned bb = __ballot_sync(FULL, (dk[ch] >> b) & 1);
+                    same &= ((dk[ch] >> b) & 1) ? bb : ~bb;
+                    m &= bb ^ lb[b];
+                }
+                pos[ch] = __shfl_sync(FULL, bexcl, dk[ch]) + __shfl_sync(FULL, run, dk[ch]) +
+                          __popc(same & lanemask_lt());
+                run += __popc(m);
+            }
+#pragma unroll
+            for (int ch = 0; ch < kWarpChunks; ++ch) {
+                if (vk[ch]) {
+                    const int k = (int)(kv[ch] & 0xffffu);
+                    const int s = node_of(R.nodeoff, L, k);
+                    R.sel[pos[ch]] = (s << 8) | (int)(R.ent[k] & 0xffu);
+                    R.selped[pos[ch]] = A + dk[ch];
+                }
+            }
+            WPHASE(4);
+        } else {
+            // exact fallback: score the level again with exact PED offsets, find the K-th one
+            // by bisection, compact the kept entries in enumeration order and rank them by
+            // (PED, enumeration order)
+            int dummy = 0;
+            eval_level<Word, BK, FOLD, true>(p, R, L, n0, deg, n2, mrow, A, H, dummy);
+            auto count_le = [&](int t) -> int {
+                int cnt = 0;
+                for (int k = lane; k < tot; k += 32) cnt += ((int)R.ent[k] <= t);
+                return warp_sum(cnt);
+            };
+            int lo = H - 1, hi = 0;
+            for (int k = lane; k < tot; k += 32) hi = max(hi, (int)R.ent[k]);
+            hi = (int)__reduce_max_sync(FULL, (unsigned)hi);
+            if (lo > hi) lo = hi;
+            while (lo < hi) {   // count(<= lo - 1) < newL <= count(<= hi)
+                const int mid = lo + (hi - lo) / 2;
+                if (count_le(mid) >= newL) hi = mid;
+                else lo = mid + 1;
+            }
+            const int T = lo;
+            const int q = newL - (T > 0 ? count_le(T - 1) : 0);
+            int keep_before = 0, eq_before = 0;
+            for (int kb = 0; kb < tot; kb += 32) {
+                const int k = kb + lane;
+                const int d = k < tot ? (int)R.ent[k] : 0x10000;
+                const bool is_eq = d == T;
+                const unsigned eqb = __ballot_sync(FULL, is_eq);
+                const bool keep = (d < T) || (is_eq && eq_before + __popc(eqb & lanemask_lt()) < q);
+                const unsigned kbm = __ballot_sync(FULL, keep);
+                if (keep)
+                    R.klist[keep_before + __popc(kbm & lanemask_lt())] = ((uint32_t)d << 16) | (uint32_t)k;
+                keep_before += __popc(kbm);
+                eq_before += __popc(eqb);
+            }
+            __syncwarp();
+            // rank of every kept key (keys are distinct: the entry index is in the low half)
+            for (int x = lane; x < newL; x += 32) {
+                const uint32_t kx = R.klist[x];
+                int rank = 0;
+                for (int y = 0; y < newL; ++y) rank += R.klist[y] < kx;
+                R.selped[rank] = (int)kx;
+            }
+            __syncwarp();
+            for (int r = lane; r < newL; r += 32) {
+                const uint32_t kx = (uint32_t)R.selped[r];
+                const int d = (int)(kx >> 16), k = (int)(kx & 0xffffu);
+                const int s = node_of(R.nodeoff, L, k);
+                const int t = k - (int)R.nodeoff[s];
+                const int cnt = (int)R.nodeoff[s + 1] - (int)R.nodeoff[s];
+                int j = n2;
+                if (t < cnt - 1) {   // the t-th free target vertex of node s
+                    const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
+                    Word x = ~R.imgc[s] & nmask;
+                    for (int z = 0; z < t; ++z) x &= x - (Word)1;
+                    j = ffsw(x);
+                }
+                R.sel[r] = (s << 8) | j;
+                R.selped[r] = A + d;
+            }
+            WPHASE(5);
+        }
+        __syncwarp();
+        // kept children in key order (slot = rank): parent map + entry i, Img, PED, and the
+        // g2 edges inside Img (for the leaf completion)
+        {
+            const int nvec = (i + 15) >> 4;
+            const uint8_t *__restrict__ mapc = R.mapc;
+            uint8_t *__restrict__ mapn = R.mapn;
+#pragma unroll 2
+            for (int r = lane; r < newL; r += 32) {
+                const int v = R.sel[r];
+                const int s = v >> 8, j = v & 0xff;
+                const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
+                uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
+                for (int t = 0; t < nvec; ++t) dst[t] = src[t];
+                mapn[(int64_t)r * mrow + i] = j < n2 ? (uint8_t)j : DEL;
+                const Word im = R.imgc[s];
+                int e2 = R.e2c[s];
+                Word imn = im;
+                if (j < n2) {
+                    e2 += popcw((Word)(R.tgt[j].a2 & im));
+                    imn |= (Word)1 << j;
+                }
+                R.imgn[r] = imn;
+                R.e2n[r] = (uint16_t)e2;
+                R.pedn[r] = R.selped[r];
+            }
+        }
+        __syncwarp();
+        { Word *t = R.imgc; R.imgc = R.imgn; R.imgn = t; }
+        { int32_t *t = R.pedc; R.pedc = R.pedn; R.pedn = t; }
+        { uint16_t *t = R.e2c; R.e2c = R.e2n; R.e2n = t; }
+        { uint8_t *t = R.mapc; R.mapc = R.mapn; R.mapn = t; }
+        L = newL;
+        WPHASE(6);
+    }
+
+    // ---- S5: complete every kept leaf (insert the free g2 vertices and their edges), least
+    // (total, slot)
+    unsigned long long best = ~0ull;
+    for (int s = lane; s < L; s += 32) {
+        const int nimg = popcw(R.imgc[s]);
+        const long long total = (long long)R.pedc[s] + (long long)c.vins * (n2 - nimg) +
+                                (long long)c.eins * (m2.m - (int)R.e2c[s]);
+        const unsigned long long key = ((unsigned long long)total << 32) | (unsigned)s;
+        best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(FULL, best, o);
+        best = y < best ? y : best;
+    }
+    if (lane == 0) {
+        p.out_cost[pair] = (int32_t)(best >> 32);
+        if (p.out_nevals) p.out_nevals[pair] = nevals + L;
+    }
+    const int bs = (int)(best & 0xffffffffull);
+    const uint8_t *mbest = R.mapc + (int64_t)bs * mrow;
+    int32_t *om = p.out_map + p.map_off[pair];
+    for (int k = lane; k < n1; k += 32) {
+        const uint8_t v = mbest[k];
+        om[k] = v == DEL ? -1 : (int32_t)v;
+    }
+    __syncwarp();
+    WPHASE(8);
+#ifdef FASTGED_PHASE_TIMERS
+    if (lane == 0 && p.phase_cycles)
+        for (int k = 0; k < 16; ++k) atomicAdd(&p.phase_cycles[k], (unsigned long long)ph[k]);
+#endif
+}
+
+// Persistent one-warp teams: each warp pops pairs from the class's queue until it is empty.
+template <typename Word, int BK>
+__global__ void __launch_bounds__(256) kbest_warp_kernel(const KParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int wic = (int)(threadIdx.x >> 5);
+    const int gwarp = (int)blockIdx.x * (int)(blockDim.x >> 5) + wic;
+    uint8_t *ws = smem + (int64_t)wic * p.wl.warp_bytes;
+    uint8_t *gw = p.wl.gmap ? p.gscratch + (int64_t)gwarp * p.wl.gmap_bytes : nullptr;
+    const bool fold = p.cost.eins == p.cost.edel;
+    for (;;) {
+        int qi = 0;
+        if ((threadIdx.x & 31) == 0) qi = atomicAdd(p.queue_head, 1);
+        qi = __shfl_sync(0xffffffffu, qi, 0);
+        if (qi >= p.n_order) break;
+        if (fold) solve_pair_warp<Word, BK, true>(p, ws, gw, p.order[qi]);
+        else solve_pair_warp<Word, BK, false>(p, ws, gw, p.order[qi]);
+    }
+}
+
+template <typename Word, int BK>
+static cudaError_t ensure_warp_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kbest_warp_kernel<Word, BK>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kbest_warp_kernel<Word, BK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int BK>
+cudaError_t launch_kbest_warp_bk(bool w32, const KParams &p, int grid, int block, size_t smem,
+                                 cudaStream_t st)
+{
+    if (w32) {
+        cudaError_t e = ensure_warp_attr<uint32_t, BK>();
+        if (e != cudaSuccess) return e;
+        kbest_warp_kernel<uint32_t, BK><<<grid, block, smem, st>>>(p);
+    } else {
+        cudaError_t e = ensure_warp_attr<uint64_t, BK>();
+        if (e != cudaSuccess) return e;
+        kbest_warp_kernel<uint64_t, BK><<<grid, block, smem, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t kbest_warp_occupancy_bk(bool w32, int block, size_t smem, int *out)
+{
+    if (w32) {
+        cudaError_t e = ensure_warp_attr<uint32_t, BK>();
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_warp_kernel<uint32_t, BK>,
+                                                             block, smem);
+    }
+    cudaError_t e = ensure_warp_attr<uint64_t, BK>();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kbest_warp_kernel<uint64_t, BK>,
+                                                         block, smem);
+}
+
+}  // namespace fastged

@@ -33,6 +33,8 @@ FASTGED_INJECT_LAUNCH = 1
 FASTGED_INJECT_ADMISSION = 2
 FASTGED_ORDER_INDEX = 0
 FASTGED_ORDER_DEGREE = 1
+FASTGED_TEAM_AUTO = 0
+FASTGED_TEAM_CTA = 1
 
 EXPORTED = ["fastged_version", "fastged_last_error", "fastged_create", "fastged_destroy",
             "fastged_batch", "fastged_batch_ex", "fastged_plan_create", "fastged_plan_run",
@@ -71,7 +73,8 @@ class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("k_per_pair", ctypes.c_void_p), ("hist_window", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("vertex_order", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
+                ("team", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -253,12 +256,13 @@ def marshal(w) -> Marshalled:
 
 def make_options(form: int = FASTGED_FORM_BATCHED, variant: int = 0, k_per_pair=None,
                  hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1,
-                 autotune: int = 0, vertex_order: int = FASTGED_ORDER_INDEX):
+                 autotune: int = 0, vertex_order: int = FASTGED_ORDER_INDEX,
+                 team: int = FASTGED_TEAM_AUTO):
     kpp = None
     if k_per_pair is not None:
         kpp = np.ascontiguousarray(np.asarray(k_per_pair, dtype=np.int32))
     o = Options(form, variant, kpp.ctypes.data if kpp is not None else None, hist_window,
-                block_threads, use_cuda_graph, autotune, vertex_order)
+                block_threads, use_cuda_graph, autotune, vertex_order, team)
     o._keep = kpp
     return o
 

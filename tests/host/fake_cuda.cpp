@@ -7,6 +7,7 @@
 // run on one executor thread after a configurable delay, the time a batch would take.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -268,6 +269,19 @@ cudaError_t kbest_occupancy(int, bool, bool, bool, int, int, size_t, int *out)
 cudaError_t kbest_cluster_occupancy(int, int, int, size_t, int cluster, int *out)
 {
     *out = 152 / cluster;
+    return cudaSuccess;
+}
+// one-warp launches report their vertex-map placement as cluster 100 + gmap
+cudaError_t launch_kbest_warp(bool, int, const KParams &p, int, int block, size_t, cudaStream_t)
+{
+    note_launch(block, 100 + p.wl.gmap);
+    return cudaSuccess;
+}
+cudaError_t kbest_warp_occupancy(bool, int, int block, size_t smem, int *out)
+{
+    // as many CTAs as fit the SM's 228 KB of shared memory and 64 warps
+    const size_t by_smem = smem ? (233472 - 1024) / (smem + 1024) : 64;
+    *out = (int)std::min<size_t>(by_smem, (size_t)(2048 / block));
     return cudaSuccess;
 }
 bool kbest_has_smem_variant(int, bool, bool) { return true; }

@@ -49,13 +49,13 @@ extern "C" void probe_batch(int64_t *v)
 }
 
 // W wide w32 pk cluster n1max n2max m1max kmax n_order order_off block grid slice_bytes
-// scratch_off smem_bytes
+// scratch_off smem_bytes warp
 extern "C" void probe_class(int k, int64_t *v)
 {
     const ClassPlan &c = g_b.classes[k];
     const int64_t x[] = {c.W, c.wide, c.w32, c.pk, c.cluster, c.n1max, c.n2max, c.m1max,
                          c.kmax, (int64_t)c.order.size(), c.order_off, c.block, c.grid,
-                         c.lay.slice_bytes, (int64_t)c.scratch_off, c.lay.smem_bytes};
+                         c.lay.slice_bytes, (int64_t)c.scratch_off, c.lay.smem_bytes, c.warp};
     memcpy(v, x, sizeof(x));
 }
 

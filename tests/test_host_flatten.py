@@ -30,7 +30,7 @@ BATCH_FIELDS = ("n_graphs n_pairs K B labelled has_kpp n_vlab n_edges adj_words 
                 "off_kpp in_bytes woff_err woff_cost woff_nev woff_map out_bytes woff_queue "
                 "woff_pool woff_scratch work_bytes n_classes perm_size").split()
 CLASS_FIELDS = ("W wide w32 pk cluster n1max n2max m1max kmax n_order order_off block grid "
-                "slice_bytes scratch_off smem_bytes").split()
+                "slice_bytes scratch_off smem_bytes warp").split()
 
 
 @pytest.fixture(scope="module")
@@ -92,8 +92,10 @@ def words_class(n2):
 
 
 def class_key(g1, g2, kp, cost):
-    """(W, wide, w32, pk): bitset words of g2 (a single-word pair that cannot pack its
-    successors into 32 bits moves to two words), 16-bit map entries, 32-bit words, packed."""
+    """(W, wide, w32, pk, warp): bitset words of g2 (a single-word pair that cannot pack its
+    successors into 32 bits moves to two words), 16-bit map entries, 32-bit words, packed,
+    and one warp per pair (single-word pairs whose source has at most 64 vertices and whose
+    K is at most 128, under the default team option and variant A)."""
     vsub, vdel, vins, esub, edel, eins = cost
     ped_bound = g1.n * max(vsub, vdel) + g1.m * max(esub, edel) + g2.m * eins
     jb = int(g2.n).bit_length()
@@ -101,7 +103,8 @@ def class_key(g1, g2, kp, cost):
     W = words_class(g2.n)
     if W == 1 and not pk:
         W = 2
-    return (W, g2.n >= 255, W == 1 and g2.n <= 32, pk)
+    warp = W == 1 and g1.n <= 64 and kp <= 128
+    return (W, g2.n >= 255, W == 1 and g2.n <= 32, pk, warp)
 
 
 def work_bucket(g1, g2, kp):
@@ -141,9 +144,9 @@ def test_classes_and_heaviest_first_order(lib, per_pair_k):
     assert len(f.classes) == len(first) >= 4
     off = 0
     for cl, order, key in zip(f.classes, f.orders, first):
-        Wk, wide, w32, pk = key
-        assert (cl["W"], cl["wide"], cl["w32"], cl["pk"]) == (Wk, int(wide or Wk >= 8), int(w32),
-                                                              int(pk))
+        Wk, wide, w32, pk, warp = key
+        assert (cl["W"], cl["wide"], cl["w32"], cl["pk"], cl["warp"]) == (
+            Wk, int(wide or Wk >= 8), int(w32), int(pk), int(warp))
         items = keys[key]
         expect = [p for _, p, _, _, _ in sorted(items)]
         assert order.tolist() == expect

@@ -43,19 +43,22 @@ def _plan(L, h, mm, K, **opts):
     return p.value, st
 
 
-def _probe_classes(L, w, K):
-    """(block, cluster) of every size class when the batch is planned now."""
+def _probe_classes(L, w, K, team=F.FASTGED_TEAM_CTA, full=False):
+    """(block, cluster) of every size class when the batch is planned now (with full=True,
+    a dict of the class's fields)."""
     c = (ctypes.c_int32 * 6)(*w.cost)
     mm = F.Marshalled(w.graphs, w.pairs)
-    o = F.make_options()
+    o = F.make_options(team=team)
     assert L.probe_flatten(ctypes.addressof(mm.pl), K, ctypes.addressof(o), c) == 0
     v = (ctypes.c_int64 * 31)()
     L.probe_batch(v)
     out = []
+    names = ("W wide w32 pk cluster n1max n2max m1max kmax n_order order_off block grid "
+             "slice_bytes scratch_off smem_bytes warp").split()
     for k in range(v[29]):
-        x = (ctypes.c_int64 * 16)()
+        x = (ctypes.c_int64 * 17)()
         L.probe_class(k, x)
-        out.append((x[11], x[4]))   # block, cluster
+        out.append(dict(zip(names, x)) if full else (x[11], x[4]))   # block, cluster
     return out
 
 
@@ -68,7 +71,7 @@ def test_autotuner_picks_the_fastest_block_size(lib):
     mm = F.Marshalled(w.graphs, w.pairs)
     h = _handle(lib, w.cost)
     n0 = lib.fake_kbest_launches()
-    p, st = _plan(lib, h, mm, w.K, autotune=1)
+    p, st = _plan(lib, h, mm, w.K, autotune=1, team=F.FASTGED_TEAM_CTA)
     assert st.n_classes == 2
     # three shapes per class, each timed twice, one launch per timing run
     assert lib.fake_kbest_launches() - n0 == 2 * 3 * 2
@@ -78,12 +81,12 @@ def test_autotuner_picks_the_fastest_block_size(lib):
     # change, and a batch planned without autotuning uses the recorded shapes
     lib.fake_set_shape_ms(512, 1, 9.0)
     n1 = lib.fake_kbest_launches()
-    p2, st2 = _plan(lib, h, mm, w.K, autotune=1)
+    p2, st2 = _plan(lib, h, mm, w.K, autotune=1, team=F.FASTGED_TEAM_CTA)
     assert lib.fake_kbest_launches() == n1
     assert [st2.block_threads[k] for k in range(2)] == [512, 512]
     assert _probe_classes(lib, w, w.K) == [(512, 1), (512, 1)]
     # a fixed block size skips the table
-    p3, st3 = _plan(lib, h, mm, w.K, autotune=1, block_threads=128)
+    p3, st3 = _plan(lib, h, mm, w.K, autotune=1, block_threads=128, team=F.FASTGED_TEAM_CTA)
     assert [st3.block_threads[k] for k in range(2)] == [128, 128]
     for q in (p, p2, p3):
         lib.fastged_plan_destroy(q)
@@ -94,6 +97,64 @@ def test_autotuner_picks_the_fastest_block_size(lib):
     assert lib.fastged_autotune_entries() == 0
     assert _probe_classes(lib, w, w.K) == [(256, 1), (256, 1)]
     assert _probe_classes(lib, w, 32) == [(128, 1), (128, 1)]
+
+
+def _warp_bytes(n1, n2, m1, K, B, w32, gmap):
+    """Shared memory of one warp of a one-warp class: g2 records (16-byte padded: adjacency
+    word, B label planes, cost entry), labels, neighbour offsets and lists, two beams of
+    Img / PED / inner-edge counts, the 16-bit entries, node offsets, kept list, selection,
+    and the two map buffers unless they are in global scratch."""
+    a = lambda x: (x + 15) // 16 * 16
+    wb = 4 if w32 else 8
+    rec = a(wb * (1 + B) + 4)
+    mrow = a(max(n1, 1))
+    parts = [(n2 + 1) * rec, max(n2, 1) * 4, (n1 + 1) * 4, max(m1, 1) * 4, K * wb, K * wb,
+             K * 4, K * 4, K * 2, K * 2, (K * (n2 + 1) + 1) * 2, (K + 1) * 2, K * 4, K * 4,
+             K * 4]
+    if not gmap:
+        parts += [K * mrow, K * mrow]
+    return sum(a(x) for x in parts)
+
+
+def test_one_warp_classes_and_their_tuning(lib):
+    """Molecule-like pairs (K <= 128) go to one-warp classes: CTAs of 4 warps by default,
+    vertex maps in shared memory while 16 warps still fit an SM, grid capped by the pairs.
+    The autotuner times 64/128/256 threads with the maps in shared or global memory (the
+    fake reports the placement as cluster 100 + gmap) and keeps the fastest; the maps then
+    move to a per-warp block of global scratch."""
+    lib.fastged_autotune_clear()
+    lib.fake_set_shape_ms(0, 0, 0.0)
+    times = {(64, 100): 4.0, (128, 100): 3.0, (256, 100): 5.0,
+             (64, 101): 6.0, (128, 101): 7.0, (256, 101): 2.0}
+    for (block, cl), ms in times.items():
+        lib.fake_set_shape_ms(block, cl, ms)
+    w = W.config2(3000)
+    cls = _probe_classes(lib, w, w.K, team=F.FASTGED_TEAM_AUTO, full=True)
+    assert len(cls) == 2 and all(c["warp"] == 1 for c in cls)
+    assert sorted(c["w32"] for c in cls) == [0, 1]
+    for c in cls:
+        args = (c["n1max"], c["n2max"], c["m1max"], c["kmax"], 2, bool(c["w32"]))
+        gmap = 233472 // _warp_bytes(*args, False) < 16
+        assert c["block"] == 128 and c["smem_bytes"] == 4 * _warp_bytes(*args, gmap)
+        mrow = (c["n1max"] + 15) // 16 * 16
+        assert c["slice_bytes"] == (4 * ((2 * c["kmax"] * mrow + 255) // 256 * 256) if gmap
+                                    else 0)
+        assert 1 <= c["grid"] <= min(152 * (2048 // 128), (c["n_order"] + 3) // 4)
+    mm = F.Marshalled(w.graphs, w.pairs)
+    h = _handle(lib, w.cost)
+    n0 = lib.fake_kbest_launches()
+    p, st = _plan(lib, h, mm, w.K, autotune=1)
+    assert lib.fake_kbest_launches() - n0 == 2 * 6 * 2
+    assert [st.block_threads[k] for k in range(2)] == [256, 256]
+    for c in _probe_classes(lib, w, w.K, team=F.FASTGED_TEAM_AUTO, full=True):
+        assert c["block"] == 256 and c["warp"] == 1
+        assert c["slice_bytes"] > 0 and c["slice_bytes"] % (8 * 256) == 0
+    # K past the one-warp limit: CTA teams again
+    assert all(c["warp"] == 0 for c in _probe_classes(lib, w, 129, team=F.FASTGED_TEAM_AUTO,
+                                                       full=True))
+    lib.fastged_plan_destroy(p)
+    lib.fastged_destroy(h)
+    lib.fastged_autotune_clear()
 
 
 def test_autotuner_picks_the_fastest_cluster_size(lib):
