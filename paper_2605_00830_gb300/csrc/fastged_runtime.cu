@@ -636,7 +636,7 @@ static bool cluster_eligible(const ClassPlan &cp, int npairs, int sm_count)
 // Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
 // Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
 // CTAs per pair.
-// One-warp classes: warps per CTA (threads / 32, at most 8) and where the vertex maps live.
+// One-warp classes: warps per CTA (threads / 32, at most 4) and where the vertex maps live.
 // Without a tuning entry the maps stay in shared memory when that still leaves room for 16
 // warps per SM, and CTAs hold 4 warps.
 static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
@@ -653,8 +653,8 @@ static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_b
         gmap = (size_t)h->smem_per_sm / std::max<size_t>(shared_maps, 1) < 16;
     }
     const size_t wbytes = plan_warp_layout(cp, B, gmap);
-    // at most 8 warps per CTA (the kernel's launch bound is 256 threads)
-    int wpc = std::min(8, std::max(1, block / 32));
+    // at most 4 warps per CTA (the kernel's launch bound is 128 threads)
+    int wpc = std::min(4, std::max(1, block / 32));
     while (wpc > 1 && (size_t)wpc * wbytes > (size_t)h->smem_optin) wpc >>= 1;
     if ((size_t)wpc * wbytes > (size_t)h->smem_optin)
         return set_error(FASTGED_ERR_CUDA, "a one-warp team does not fit shared memory");
@@ -1460,8 +1460,10 @@ static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_
         }
         std::vector<TuneChoice> cands;
         if (cp.warp) {
+            // two or four warps per CTA (one-warp CTAs run into the SM's CTA limit when
+            // several classes share the GPU)
             for (int gm : {0, 1})
-                for (int bt : {64, 128, 256}) {
+                for (int bt : {64, 128}) {
                     TuneChoice c;
                     c.block = bt;
                     c.gmap = gm;

@@ -83,19 +83,36 @@ __device__ __forceinline__ void rec_set_plane(TgtRec<Word, 0> &, int, Word) {}
 __device__ __forceinline__ int ffsw(uint32_t x) { return __ffs((int)x) - 1; }
 __device__ __forceinline__ int ffsw(uint64_t x) { return __ffsll((long long)x) - 1; }
 
-// Working set of one warp (see WarpRegion).
+// Dynamic shared memory of the one-warp kernel (every warp of a CTA has its block in it).
+extern __shared__ __align__(16) uint8_t g_warp_smem[];
+
+// Working set of one warp (see WarpRegion): the warp's block is addressed by 32-bit offsets
+// into shared memory; only the vertex maps (shared or global) need full pointers. The beam
+// buffers alternate: cur selects which of each pair holds the current level.
 template <typename Word, int NPL>
 struct WarpRegs {
-    TgtRec<Word, NPL> *tgt;
-    int32_t *lab2, *noff, *nbr;
-    Word *imgc, *imgn;          // current / next beam buffers, swapped after every level
-    int32_t *pedc, *pedn;
-    uint16_t *e2c, *e2n;
-    uint8_t *mapc, *mapn;
-    uint16_t *ent, *nodeoff;
-    uint32_t *klist;
-    int32_t *sel, *selped;
-    int ent_dummy;              // an entry slot past every level's entries (stores of idle lanes)
+    uint32_t wb;     // start of the warp's block in dynamic shared memory
+    int cur;         // 0: buffers *0 are current, *1 next; 1: the reverse
+    uint8_t *mb;     // base of the vertex-map buffers
+    template <typename T>
+    __device__ __forceinline__ T *at(int32_t off) const { return (T *)(g_warp_smem + wb + (uint32_t)off); }
+    __device__ __forceinline__ TgtRec<Word, NPL> *tgt(const WarpLayout &wl) const { return at<TgtRec<Word, NPL>>(wl.off[WR_TGT]); }
+    __device__ __forceinline__ int32_t *lab2(const WarpLayout &wl) const { return at<int32_t>(wl.off[WR_LAB2]); }
+    __device__ __forceinline__ int32_t *noff(const WarpLayout &wl) const { return at<int32_t>(wl.off[WR_NOFF]); }
+    __device__ __forceinline__ int32_t *nbr(const WarpLayout &wl) const { return at<int32_t>(wl.off[WR_NBR]); }
+    __device__ __forceinline__ Word *imgc(const WarpLayout &wl) const { return at<Word>(cur ? wl.off[WR_IMG1] : wl.off[WR_IMG0]); }
+    __device__ __forceinline__ Word *imgn(const WarpLayout &wl) const { return at<Word>(cur ? wl.off[WR_IMG0] : wl.off[WR_IMG1]); }
+    __device__ __forceinline__ int32_t *pedc(const WarpLayout &wl) const { return at<int32_t>(cur ? wl.off[WR_PED1] : wl.off[WR_PED0]); }
+    __device__ __forceinline__ int32_t *pedn(const WarpLayout &wl) const { return at<int32_t>(cur ? wl.off[WR_PED0] : wl.off[WR_PED1]); }
+    __device__ __forceinline__ uint16_t *e2c(const WarpLayout &wl) const { return at<uint16_t>(cur ? wl.off[WR_E21] : wl.off[WR_E20]); }
+    __device__ __forceinline__ uint16_t *e2n(const WarpLayout &wl) const { return at<uint16_t>(cur ? wl.off[WR_E20] : wl.off[WR_E21]); }
+    __device__ __forceinline__ uint16_t *ent(const WarpLayout &wl) const { return at<uint16_t>(wl.off[WR_ENT]); }
+    __device__ __forceinline__ uint16_t *nodeoff(const WarpLayout &wl) const { return at<uint16_t>(wl.off[WR_NODEOFF]); }
+    __device__ __forceinline__ uint32_t *klist(const WarpLayout &wl) const { return at<uint32_t>(wl.off[WR_KLIST]); }
+    __device__ __forceinline__ int32_t *sel(const WarpLayout &wl) const { return at<int32_t>(wl.off[WR_SEL]); }
+    __device__ __forceinline__ int32_t *selped(const WarpLayout &wl) const { return at<int32_t>(wl.off[WR_SELPED]); }
+    __device__ __forceinline__ uint8_t *mapc(const WarpLayout &wl) const { return mb + (cur ? wl.off[WR_MAP1] : wl.off[WR_MAP0]); }
+    __device__ __forceinline__ uint8_t *mapn(const WarpLayout &wl) const { return mb + (cur ? wl.off[WR_MAP0] : wl.off[WR_MAP1]); }
 };
 
 // Scores every successor of level i (lane <-> parent node). Entries go to ent in enumeration
@@ -114,18 +131,18 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     constexpr int NPL = BK == 8 ? kMaxB : BK;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const WarpLayout &wl = p.wl;
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
     const int c_eins = p.cost.eins, c_edel = p.cost.edel, c_esub = p.cost.esub;
     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
-    const uint8_t *mapc = R.mapc;
-    const TgtRec<Word, NPL> *tgt = R.tgt;
-    uint16_t *dummy = R.ent + R.ent_dummy;
+    const uint8_t *mapc = R.mapc(wl);
+    const TgtRec<Word, NPL> *tgt = R.tgt(wl);
+    uint16_t *dummy = R.ent(wl) + wl.ent_dummy;
     // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 15 steps into
     // acc[m] = buckets (m, m + 4) and acc[4 + m] = (8 + m, 12 + m), 16 bits each
     uint32_t clo = 0, chi = 0, acc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = 0;
-    int since = 0;
     auto flush = [&]() {
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -133,7 +150,6 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             acc[4 + m] += (chi >> (4 * m)) & 0x000F000Fu;
         }
         clo = chi = 0;
-        since = 0;
     };
     int tot = 0;
     for (int g0 = 0; g0 < L; g0 += 32) {
@@ -152,7 +168,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             int e[4];
             uint8_t phi[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr[n0 + t0 + u] : -1;
+            for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr(wl)[n0 + t0 + u] : -1;
 #pragma unroll
             for (int u = 0; u < 4; ++u) phi[u] = (e[u] >= 0 && act) ? ms[e[u] & 0xffff] : (uint8_t)0xff;
 #pragma unroll
@@ -166,8 +182,8 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                     if (b < B && ((e[u] >> (16 + b)) & 1)) PL[b] |= pb;
             }
         }
-        const Word im = act ? R.imgc[s] : ~(Word)0;
-        const int base = act ? R.pedc[s] + c_edel * dcnt - A : 0;
+        const Word im = act ? R.imgc(wl)[s] : ~(Word)0;
+        const int base = act ? R.pedc(wl)[s] + c_edel * dcnt - A : 0;
         const int cnt = act ? n2 - popcw((Word)(im & nmask)) + 1 : 0;   // free vertices + deletion
         int incl = cnt;
 #pragma unroll
@@ -176,11 +192,14 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             if (lane >= o) incl += v;
         }
         const int off = tot + incl - cnt;
-        if (act) R.nodeoff[s] = (uint16_t)off;
+        if (act) R.nodeoff(wl)[s] = (uint16_t)off;
         const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
         Word x = act ? (Word)(~im & nmask) : (Word)0;
-        uint16_t *ep = R.ent + off;
-        for (int t = 0; t < maxc; ++t) {
+        uint16_t *ep = R.ent(wl) + off;
+        // blocks of 15 steps: a 4-bit counter cannot overflow inside one
+        for (int t0 = 0; t0 < maxc; t0 += 15) {
+        const int t1 = min(maxc, t0 + 15);
+        for (int t = t0; t < t1; ++t) {
             const bool val = t < cnt;
             // next free vertex in increasing order; once none is left, the deletion (j = n2)
             const int f = ffsw(x);
@@ -210,14 +229,14 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                 const uint32_t inc = val ? 1u << ((dd & 7) << 2) : 0u;
                 clo += dd < 8 ? inc : 0u;
                 chi += dd < 8 ? 0u : inc;
-                if (++since == 15) flush();
             }
+        }
+        if (!EXACT) flush();
         }
         tot += __shfl_sync(FULL, incl, 31);
     }
-    if (lane == 0) R.nodeoff[L] = (uint16_t)tot;
+    if (lane == 0) R.nodeoff(wl)[L] = (uint16_t)tot;
     if (!EXACT) {
-        flush();
         // warp totals (at most 128 x 65 successors: 16-bit fields cannot overflow), then lane
         // b takes bucket b
 #pragma unroll
@@ -250,7 +269,7 @@ __device__ __forceinline__ int node_of(const uint16_t *nodeoff, int L, int k)
 }
 
 template <typename Word, int BK, bool FOLD>
-__device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, uint8_t *gw,
+__device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, uint8_t *gw,
                                                 const int pair)
 {
     constexpr int NPL = BK == 8 ? kMaxB : BK;
@@ -260,25 +279,9 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
     const int lane = threadIdx.x & 31;
     const WarpLayout &wl = p.wl;
     WarpRegs<Word, NPL> R;
-    R.tgt = (Rec *)(ws + wl.off[WR_TGT]);
-    R.lab2 = (int32_t *)(ws + wl.off[WR_LAB2]);
-    R.noff = (int32_t *)(ws + wl.off[WR_NOFF]);
-    R.nbr = (int32_t *)(ws + wl.off[WR_NBR]);
-    R.imgc = (Word *)(ws + wl.off[WR_IMG0]);
-    R.imgn = (Word *)(ws + wl.off[WR_IMG1]);
-    R.pedc = (int32_t *)(ws + wl.off[WR_PED0]);
-    R.pedn = (int32_t *)(ws + wl.off[WR_PED1]);
-    R.e2c = (uint16_t *)(ws + wl.off[WR_E20]);
-    R.e2n = (uint16_t *)(ws + wl.off[WR_E21]);
-    R.ent = (uint16_t *)(ws + wl.off[WR_ENT]);
-    R.nodeoff = (uint16_t *)(ws + wl.off[WR_NODEOFF]);
-    R.klist = (uint32_t *)(ws + wl.off[WR_KLIST]);
-    R.sel = (int32_t *)(ws + wl.off[WR_SEL]);
-    R.selped = (int32_t *)(ws + wl.off[WR_SELPED]);
-    R.ent_dummy = wl.ent_dummy;
-    uint8_t *mb = wl.gmap ? gw : ws;
-    R.mapc = mb + wl.off[WR_MAP0];
-    R.mapn = mb + wl.off[WR_MAP1];
+    R.wb = wb;
+    R.cur = 0;
+    R.mb = wl.gmap ? gw : g_warp_smem + wb;
 
     const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
     const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
@@ -313,21 +316,21 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
             for (int b = 0; b < NPL; ++b)
                 rec_set_plane(r, b, (u < n2 && b < B) ? (Word)pl2[((int64_t)b * n2 + u) * W2] : (Word)0);
             r.crow = 0;
-            R.tgt[u] = r;
-            if (u < n2) R.lab2[u] = p.vlab[m2.lab_off + u];
+            R.tgt(wl)[u] = r;
+            if (u < n2) R.lab2(wl)[u] = p.vlab[m2.lab_off + u];
         }
         // prior neighbours v_k (k < v) of every g1 vertex v, with their edge labels
         for (int v = lane; v < n1; v += 32) {
             const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
             int d = 0;
             for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
-            R.noff[v + 1] = d;
+            R.noff(wl)[v + 1] = d;
         }
         __syncwarp();
         int carry = 0;
         for (int v0 = 0; v0 < n1; v0 += 32) {
             const int v = v0 + lane;
-            const int d = v < n1 ? R.noff[v + 1] : 0;
+            const int d = v < n1 ? R.noff(wl)[v + 1] : 0;
             int incl = d;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -335,16 +338,16 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
                 if (lane >= o) incl += y;
             }
             __syncwarp();
-            if (v < n1) R.noff[v + 1] = carry + incl;
+            if (v < n1) R.noff(wl)[v + 1] = carry + incl;
             carry += __shfl_sync(FULL, incl, 31);
         }
-        if (lane == 0) R.noff[0] = 0;
+        if (lane == 0) R.noff(wl)[0] = 0;
         __syncwarp();
         const int64_t pstep = (int64_t)n1 * W1;
         for (int v = lane; v < n1; v += 32) {
             const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
             const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
-            int o = R.noff[v];
+            int o = R.noff(wl)[v];
             for (int w = 0; w < W1; ++w) {
                 uint64_t bits = row[w] & low_mask(v, w);
                 while (bits) {
@@ -352,15 +355,15 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
                     bits &= bits - 1ull;
                     int lab = 0;
                     for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
-                    R.nbr[o++] = (w * 64 + t) | (lab << 16);
+                    R.nbr(wl)[o++] = (w * 64 + t) | (lab << 16);
                 }
             }
         }
         // root: empty map, Img empty, PED 0
         if (lane == 0) {
-            R.imgc[0] = (Word)0;
-            R.pedc[0] = 0;
-            R.e2c[0] = 0;
+            R.imgc(wl)[0] = (Word)0;
+            R.pedc(wl)[0] = 0;
+            R.e2c(wl)[0] = 0;
         }
         __syncwarp();
     }
@@ -373,12 +376,12 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
         {
             const int a1 = p.vlab[m1.lab_off + i];
             for (int u = lane; u <= n2; u += 32)
-                R.tgt[u].crow = u < n2 ? ((R.lab2[u] != a1) ? c.vsub : 0) : c.vdel;
+                R.tgt(wl)[u].crow = u < n2 ? ((R.lab2(wl)[u] != a1) ? c.vsub : 0) : c.vdel;
         }
         __syncwarp();
         WPHASE(7);
-        const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
-        const int A = R.pedc[0];   // least PED of the kept list: a lower bound of every child
+        const int n0 = R.noff(wl)[i], deg = R.noff(wl)[i + 1] - n0;
+        const int A = R.pedc(wl)[0];   // least PED of the kept list: a lower bound of every child
         int hist = 0;
         const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist);
         nevals += tot;
@@ -406,24 +409,34 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = kb + 32 * u + lane;
-                    e[u] = k < tot ? (int)R.ent[k] : 0xffff;
+                    e[u] = k < tot ? (int)R.ent(wl)[k] : 0xffff;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(FULL, e[u] < lim);
                 if ((le[0] | le[1] | le[2] | le[3]) == 0u) continue;
+                // the four sub-chunks' ties, then their kept sets, each set of ballots taken
+                // together (the counts of the sub-chunks before are prefix sums)
+                const unsigned lt = lanemask_lt();
+                unsigned eqb[4], kbm[4];
+                bool keep[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) eqb[u] = __ballot_sync(FULL, (e[u] >> 8) == thr);
+                int eqp = eq_before;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (le[u] == 0u) continue;
                     const int d = e[u] >> 8;
-                    const bool is_eq = d == thr;
-                    const unsigned eqb = __ballot_sync(FULL, is_eq);
-                    const bool keep = (d < thr) || (is_eq && eq_before + __popc(eqb & lanemask_lt()) < q);
-                    const unsigned kbm = __ballot_sync(FULL, keep);
-                    if (keep)
-                        R.klist[keep_before + __popc(kbm & lanemask_lt())] =
-                            ((uint32_t)d << 16) | (uint32_t)(kb + 32 * u + lane);
-                    keep_before += __popc(kbm);
-                    eq_before += __popc(eqb);
+                    keep[u] = (d < thr) || (d == thr && eqp + __popc(eqb[u] & lt) < q);
+                    eqp += __popc(eqb[u]);
+                }
+                eq_before = eqp;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) kbm[u] = __ballot_sync(FULL, keep[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (keep[u])
+                        R.klist(wl)[keep_before + __popc(kbm[u] & lt)] =
+                            ((uint32_t)(e[u] >> 8) << 16) | (uint32_t)(kb + 32 * u + lane);
+                    keep_before += __popc(kbm[u]);
                 }
             }
             __syncwarp();
@@ -439,7 +452,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
             for (int ch = 0; ch < kWarpChunks; ++ch) {
                 const int x = 32 * ch + lane;
                 vk[ch] = x < newL;
-                kv[ch] = vk[ch] ? R.klist[x] : 0u;
+                kv[ch] = vk[ch] ? R.klist(wl)[x] : 0u;
                 dk[ch] = (int)(kv[ch] >> 16);
             }
 #pragma unroll
@@ -462,9 +475,9 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
             for (int ch = 0; ch < kWarpChunks; ++ch) {
                 if (vk[ch]) {
                     const int k = (int)(kv[ch] & 0xffffu);
-                    const int s = node_of(R.nodeoff, L, k);
-                    R.sel[pos[ch]] = (s << 8) | (int)(R.ent[k] & 0xffu);
-                    R.selped[pos[ch]] = A + dk[ch];
+                    const int s = node_of(R.nodeoff(wl), L, k);
+                    R.sel(wl)[pos[ch]] = (s << 8) | (int)(R.ent(wl)[k] & 0xffu);
+                    R.selped(wl)[pos[ch]] = A + dk[ch];
                 }
             }
             WPHASE(4);
@@ -476,11 +489,11 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
             eval_level<Word, BK, FOLD, true>(p, R, L, n0, deg, n2, mrow, A, H, dummy);
             auto count_le = [&](int t) -> int {
                 int cnt = 0;
-                for (int k = lane; k < tot; k += 32) cnt += ((int)R.ent[k] <= t);
+                for (int k = lane; k < tot; k += 32) cnt += ((int)R.ent(wl)[k] <= t);
                 return warp_sum(cnt);
             };
             int lo = H - 1, hi = 0;
-            for (int k = lane; k < tot; k += 32) hi = max(hi, (int)R.ent[k]);
+            for (int k = lane; k < tot; k += 32) hi = max(hi, (int)R.ent(wl)[k]);
             hi = (int)__reduce_max_sync(FULL, (unsigned)hi);
             if (lo > hi) lo = hi;
             while (lo < hi) {   // count(<= lo - 1) < newL <= count(<= hi)
@@ -493,40 +506,40 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
             int keep_before = 0, eq_before = 0;
             for (int kb = 0; kb < tot; kb += 32) {
                 const int k = kb + lane;
-                const int d = k < tot ? (int)R.ent[k] : 0x10000;
+                const int d = k < tot ? (int)R.ent(wl)[k] : 0x10000;
                 const bool is_eq = d == T;
                 const unsigned eqb = __ballot_sync(FULL, is_eq);
                 const bool keep = (d < T) || (is_eq && eq_before + __popc(eqb & lanemask_lt()) < q);
                 const unsigned kbm = __ballot_sync(FULL, keep);
                 if (keep)
-                    R.klist[keep_before + __popc(kbm & lanemask_lt())] = ((uint32_t)d << 16) | (uint32_t)k;
+                    R.klist(wl)[keep_before + __popc(kbm & lanemask_lt())] = ((uint32_t)d << 16) | (uint32_t)k;
                 keep_before += __popc(kbm);
                 eq_before += __popc(eqb);
             }
             __syncwarp();
             // rank of every kept key (keys are distinct: the entry index is in the low half)
             for (int x = lane; x < newL; x += 32) {
-                const uint32_t kx = R.klist[x];
+                const uint32_t kx = R.klist(wl)[x];
                 int rank = 0;
-                for (int y = 0; y < newL; ++y) rank += R.klist[y] < kx;
-                R.selped[rank] = (int)kx;
+                for (int y = 0; y < newL; ++y) rank += R.klist(wl)[y] < kx;
+                R.selped(wl)[rank] = (int)kx;
             }
             __syncwarp();
             for (int r = lane; r < newL; r += 32) {
-                const uint32_t kx = (uint32_t)R.selped[r];
+                const uint32_t kx = (uint32_t)R.selped(wl)[r];
                 const int d = (int)(kx >> 16), k = (int)(kx & 0xffffu);
-                const int s = node_of(R.nodeoff, L, k);
-                const int t = k - (int)R.nodeoff[s];
-                const int cnt = (int)R.nodeoff[s + 1] - (int)R.nodeoff[s];
+                const int s = node_of(R.nodeoff(wl), L, k);
+                const int t = k - (int)R.nodeoff(wl)[s];
+                const int cnt = (int)R.nodeoff(wl)[s + 1] - (int)R.nodeoff(wl)[s];
                 int j = n2;
                 if (t < cnt - 1) {   // the t-th free target vertex of node s
                     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
-                    Word x = ~R.imgc[s] & nmask;
+                    Word x = ~R.imgc(wl)[s] & nmask;
                     for (int z = 0; z < t; ++z) x &= x - (Word)1;
                     j = ffsw(x);
                 }
-                R.sel[r] = (s << 8) | j;
-                R.selped[r] = A + d;
+                R.sel(wl)[r] = (s << 8) | j;
+                R.selped(wl)[r] = A + d;
             }
             WPHASE(5);
         }
@@ -535,33 +548,29 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
         // g2 edges inside Img (for the leaf completion)
         {
             const int nvec = (i + 15) >> 4;
-            const uint8_t *__restrict__ mapc = R.mapc;
-            uint8_t *__restrict__ mapn = R.mapn;
-#pragma unroll 2
+            const uint8_t *__restrict__ mapc = R.mapc(wl);
+            uint8_t *__restrict__ mapn = R.mapn(wl);
             for (int r = lane; r < newL; r += 32) {
-                const int v = R.sel[r];
+                const int v = R.sel(wl)[r];
                 const int s = v >> 8, j = v & 0xff;
                 const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
                 uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
                 for (int t = 0; t < nvec; ++t) dst[t] = src[t];
                 mapn[(int64_t)r * mrow + i] = j < n2 ? (uint8_t)j : DEL;
-                const Word im = R.imgc[s];
-                int e2 = R.e2c[s];
+                const Word im = R.imgc(wl)[s];
+                int e2 = R.e2c(wl)[s];
                 Word imn = im;
                 if (j < n2) {
-                    e2 += popcw((Word)(R.tgt[j].a2 & im));
+                    e2 += popcw((Word)(R.tgt(wl)[j].a2 & im));
                     imn |= (Word)1 << j;
                 }
-                R.imgn[r] = imn;
-                R.e2n[r] = (uint16_t)e2;
-                R.pedn[r] = R.selped[r];
+                R.imgn(wl)[r] = imn;
+                R.e2n(wl)[r] = (uint16_t)e2;
+                R.pedn(wl)[r] = R.selped(wl)[r];
             }
         }
         __syncwarp();
-        { Word *t = R.imgc; R.imgc = R.imgn; R.imgn = t; }
-        { int32_t *t = R.pedc; R.pedc = R.pedn; R.pedn = t; }
-        { uint16_t *t = R.e2c; R.e2c = R.e2n; R.e2n = t; }
-        { uint8_t *t = R.mapc; R.mapc = R.mapn; R.mapn = t; }
+        R.cur ^= 1;
         L = newL;
         WPHASE(6);
     }
@@ -570,9 +579,9 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
     // (total, slot)
     unsigned long long best = ~0ull;
     for (int s = lane; s < L; s += 32) {
-        const int nimg = popcw(R.imgc[s]);
-        const long long total = (long long)R.pedc[s] + (long long)c.vins * (n2 - nimg) +
-                                (long long)c.eins * (m2.m - (int)R.e2c[s]);
+        const int nimg = popcw(R.imgc(wl)[s]);
+        const long long total = (long long)R.pedc(wl)[s] + (long long)c.vins * (n2 - nimg) +
+                                (long long)c.eins * (m2.m - (int)R.e2c(wl)[s]);
         const unsigned long long key = ((unsigned long long)total << 32) | (unsigned)s;
         best = key < best ? key : best;
     }
@@ -586,7 +595,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
         if (p.out_nevals) p.out_nevals[pair] = nevals + L;
     }
     const int bs = (int)(best & 0xffffffffull);
-    const uint8_t *mbest = R.mapc + (int64_t)bs * mrow;
+    const uint8_t *mbest = R.mapc(wl) + (int64_t)bs * mrow;
     int32_t *om = p.out_map + p.map_off[pair];
     for (int k = lane; k < n1; k += 32) {
         const uint8_t v = mbest[k];
@@ -602,12 +611,11 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint8_t *ws, u
 
 // Persistent one-warp teams: each warp pops pairs from the class's queue until it is empty.
 template <typename Word, int BK>
-__global__ void __launch_bounds__(256) kbest_warp_kernel(const KParams p)
+__global__ void __launch_bounds__(128, 5) kbest_warp_kernel(const KParams p)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
     const int wic = (int)(threadIdx.x >> 5);
     const int gwarp = (int)blockIdx.x * (int)(blockDim.x >> 5) + wic;
-    uint8_t *ws = smem + (int64_t)wic * p.wl.warp_bytes;
+    const uint32_t wb = (uint32_t)wic * (uint32_t)p.wl.warp_bytes;
     uint8_t *gw = p.wl.gmap ? p.gscratch + (int64_t)gwarp * p.wl.gmap_bytes : nullptr;
     const bool fold = p.cost.eins == p.cost.edel;
     for (;;) {
@@ -615,8 +623,8 @@ __global__ void __launch_bounds__(256) kbest_warp_kernel(const KParams p)
         if ((threadIdx.x & 31) == 0) qi = atomicAdd(p.queue_head, 1);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= p.n_order) break;
-        if (fold) solve_pair_warp<Word, BK, true>(p, ws, gw, p.order[qi]);
-        else solve_pair_warp<Word, BK, false>(p, ws, gw, p.order[qi]);
+        if (fold) solve_pair_warp<Word, BK, true>(p, wb, gw, p.order[qi]);
+        else solve_pair_warp<Word, BK, false>(p, wb, gw, p.order[qi]);
     }
 }
 

@@ -119,13 +119,12 @@ def _warp_bytes(n1, n2, m1, K, B, w32, gmap):
 def test_one_warp_classes_and_their_tuning(lib):
     """Molecule-like pairs (K <= 128) go to one-warp classes: CTAs of 4 warps by default,
     vertex maps in shared memory while 16 warps still fit an SM, grid capped by the pairs.
-    The autotuner times 64/128/256 threads with the maps in shared or global memory (the
+    The autotuner times 64/128 threads with the maps in shared or global memory (the
     fake reports the placement as cluster 100 + gmap) and keeps the fastest; the maps then
     move to a per-warp block of global scratch."""
     lib.fastged_autotune_clear()
     lib.fake_set_shape_ms(0, 0, 0.0)
-    times = {(64, 100): 4.0, (128, 100): 3.0, (256, 100): 5.0,
-             (64, 101): 6.0, (128, 101): 7.0, (256, 101): 2.0}
+    times = {(64, 100): 3.0, (128, 100): 5.0, (64, 101): 7.0, (128, 101): 2.0}
     for (block, cl), ms in times.items():
         lib.fake_set_shape_ms(block, cl, ms)
     w = W.config2(3000)
@@ -144,11 +143,11 @@ def test_one_warp_classes_and_their_tuning(lib):
     h = _handle(lib, w.cost)
     n0 = lib.fake_kbest_launches()
     p, st = _plan(lib, h, mm, w.K, autotune=1)
-    assert lib.fake_kbest_launches() - n0 == 2 * 6 * 2
-    assert [st.block_threads[k] for k in range(2)] == [256, 256]
+    assert lib.fake_kbest_launches() - n0 == 2 * 4 * 2
+    assert [st.block_threads[k] for k in range(2)] == [128, 128]
     for c in _probe_classes(lib, w, w.K, team=F.FASTGED_TEAM_AUTO, full=True):
-        assert c["block"] == 256 and c["warp"] == 1
-        assert c["slice_bytes"] > 0 and c["slice_bytes"] % (8 * 256) == 0
+        assert c["block"] == 128 and c["warp"] == 1
+        assert c["slice_bytes"] > 0 and c["slice_bytes"] % (4 * 256) == 0
     # K past the one-warp limit: CTA teams again
     assert all(c["warp"] == 0 for c in _probe_classes(lib, w, 129, team=F.FASTGED_TEAM_AUTO,
                                                        full=True))
