@@ -413,16 +413,20 @@ typedef struct {
     int32_t max_m;            /* host: >= every graph's edge count                          */
     int32_t max_elabel;       /* host: >= every edge label (0 for unlabelled graphs)        */
     int32_t pad;
-    int64_t total_vertices;   /* host: sum of graph_n                                       */
+    int64_t total_vertices;   /* host: entries of vlabel, >= sum of graph_n                 */
+    int64_t total_edges;      /* host: edges in edges (and entries of elabel)               */
+    int64_t map_len;          /* host: entries of out_mapping                               */
     const int32_t *graph_n;   /* device [n_graphs] vertices per graph                       */
     const int32_t *graph_m;   /* device [n_graphs] edges per graph                          */
-    const int64_t *vlabel_off;/* device [n_graphs] first label of graph g in vlabel         */
+    const int64_t *vlabel_off;/* device [n_graphs] first label of graph g in vlabel (ranges */
+                              /* may overlap: graphs may share label rows)                  */
     const int64_t *edge_off;  /* device [n_graphs] first edge of graph g in edges / elabel  */
     const int32_t *vlabel;    /* device [total_vertices] vertex labels                      */
     const int32_t *edges;     /* device [2 * total edges] endpoint pairs, as fastged_graph  */
     const int32_t *elabel;    /* device [total edges] edge labels, or NULL                  */
     const int32_t *pairs;     /* device [2 * n_pairs] (source g1, target g2) graph indices  */
     const int64_t *map_off;   /* device [n_pairs] first entry of pair p's map in out_mapping*/
+                              /* (map_off[p] + n of the source graph <= map_len)            */
 } fastged_device_batch;
 
 /* K-Best GED of every pair of a device-resident batch without allocating memory.
@@ -434,15 +438,19 @@ typedef struct {
  *   stream       cudaStream_t the work is enqueued on (NULL = the legacy default stream)
  * Blocks until the results are on the device (it reads back a status word twice).
  * Errors: FASTGED_ERR_INVALID_ARG for out-of-range host bounds, for device data that breaks
- * them (vertex / edge counts, endpoints, self-loops, duplicate edges, labels, pair indices;
- * the outputs are then unspecified), and for a batch whose tables, bit-set pools and one
- * team's working set do not fit FASTGED_NOALLOC_SCRATCH_BYTES; FASTGED_ERR_CUDA otherwise.
+ * them (vertex / edge counts above max_n / max_m, label or edge ranges past total_vertices /
+ * total_edges, more vertices in all than total_vertices, endpoints, self-loops, duplicate
+ * edges, labels, pair indices, maps past map_len; these are checked on the device before any
+ * kernel reads an edge or writes a map, and the outputs are then unspecified), and for a
+ * batch whose tables, bit-set pools and one team's working set do not fit
+ * FASTGED_NOALLOC_SCRATCH_BYTES; FASTGED_ERR_CUDA otherwise.
  * The scratch array is shared by every call in the process: calls whose device work
  * overlaps (on different streams, or from several host threads) race and corrupt each
  * other's results, so issue them one after another. It keeps the last call's contents;
  * each call clears what must start at zero itself. The first call on a device resolves the
- * array's device address (with that device current) and should be made before any stream
- * capture begins. */
+ * array's device address (with that device current), and so does the first call after the
+ * device's context was replaced (e.g. by cudaDeviceReset); the call waits for its stream, so
+ * it cannot be captured into a CUDA graph. */
 int fastged_batch_noalloc(const fastged_cost_model *cost, const fastged_device_batch *batch,
                           int32_t K, int32_t *out_cost, int32_t *out_mapping,
                           int64_t *out_nevals, void *stream);

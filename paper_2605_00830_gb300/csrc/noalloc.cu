@@ -9,8 +9,11 @@
 // of the loaded module, so every GPU that loads the library holds it until the process exits.
 //
 // Host code may not use the array's name as a device address (it is a host-side stand-in).
-// The first call on a device, with that device current, resolves the real address once with
-// cudaGetSymbolAddress; later calls reuse it.
+// The first call on a device, with that device current, resolves the real address with
+// cudaGetSymbolAddress; later calls reuse it while the device's context is the same one (a
+// new context, after cudaDeviceReset for instance, may load the module elsewhere, so the
+// address is resolved again).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +21,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/fastged.h"
 #include "fastged_internal.h"
@@ -34,40 +38,112 @@ size_t team_shared_static_bytes();
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FASTGED_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device (resolved on the first call per device).
+// Device address of g_noalloc_scratch per device, with the id of the context it was resolved
+// in (0: not yet).
 constexpr int kMaxDevices = 64;
-static void *g_scratch_addr[kMaxDevices];
+struct ScratchAddr {
+    unsigned long long ctx = 0;
+    void *addr = nullptr;
+};
+static ScratchAddr g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mu;
 
-// Builds the graph table (every graph gets rows of Wg words), the identity pair order, and
-// validates what the packing kernel relies on: vertex and edge counts, edge endpoints, edge
-// labels and pair indices. Any violation sets bit kErrInvalid of *err.
+// Id of the calling thread's current context (unique over the process's lifetime), from the
+// driver entry points; 0 when it cannot be read (the address is then resolved on every call).
+static unsigned long long current_context_id()
+{
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (GetIdFn)f;
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+        get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Bit-set row of every graph: an exclusive prefix sum of the vertex counts (one block, the
+// graphs in chunks of its size), so graphs whose label ranges overlap still get rows of
+// their own. Negative counts count as 0 here (noalloc_prepare rejects them).
+__global__ void noalloc_rows(const int32_t *graph_n, int n_graphs, int64_t *row)
+{
+    __shared__ int64_t part[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int g0 = 0; g0 < n_graphs; g0 += blockDim.x) {
+        const int g = g0 + (int)threadIdx.x;
+        const int64_t v = g < n_graphs ? (int64_t)max(graph_n[g], 0) : 0;
+        int64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) part[wid] = incl;
+        __syncthreads();
+        int64_t before = carry;
+        for (int w = 0; w < wid; ++w) before += part[w];
+        if (g < n_graphs) row[g] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t t = 0;
+            for (int w = 0; w < nw; ++w) t += part[w];
+            carry += t;
+        }
+        __syncthreads();
+    }
+}
+
+// Builds the graph table (graph g gets Wg-word bit-set rows from row[g]), the identity pair
+// order, and validates what the packing and K-Best kernels rely on before any of them runs:
+// vertex and edge counts, label and edge ranges, bit-set rows within total_vertices, edge
+// endpoints, edge labels, pair indices and map ranges. Any violation sets bit kErrInvalid of
+// *err (and the edges of a graph whose ranges are invalid are not read).
 constexpr int32_t kErrInvalid = 2;
 
 __global__ void noalloc_prepare(const fastged_device_batch b, int Wg, int B, int max_m,
-                                GraphMeta *meta, int32_t *order, int32_t *err)
+                                const int64_t *row, GraphMeta *meta, int32_t *order,
+                                int32_t *err)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int g = gw; g < b.n_graphs; g += nwarps) {
         const int n = b.graph_n[g], m = b.graph_m[g];
-        const int64_t lo = b.vlabel_off[g], eo = b.edge_off[g];
+        const int64_t lo = b.vlabel_off[g], eo = b.edge_off[g], r = row[g];
+        const bool ok = n >= 0 && n <= b.max_n && m >= 0 && m <= max_m && lo >= 0 && eo >= 0 &&
+                        lo + n <= b.total_vertices && eo + m <= b.total_edges &&
+                        r + n <= b.total_vertices;
         if (lane == 0) {
             GraphMeta mt;
             mt.n = n;
             mt.m = m;
             mt.W = Wg;
             mt.pad = 0;
-            mt.adj_off = lo * Wg;
-            mt.plane_off = lo * Wg * B;
+            mt.adj_off = r * Wg;
+            mt.plane_off = r * Wg * B;
             mt.lab_off = lo;
             mt.edge_off = eo;
             meta[g] = mt;
-            if (n < 0 || n > b.max_n || m < 0 || m > max_m || lo < 0 || eo < 0 ||
-                lo + n > b.total_vertices)
-                atomicOr(err, kErrInvalid);
+            if (!ok) atomicOr(err, kErrInvalid);
         }
-        if (n < 0 || n > b.max_n || m < 0 || m > max_m) continue;
+        if (!ok) continue;
         for (int k = lane; k < m; k += 32) {
             const int u = b.edges[2 * (eo + k)], v = b.edges[2 * (eo + k) + 1];
             const int lab = b.elabel ? b.elabel[eo + k] : 0;
@@ -79,7 +155,12 @@ __global__ void noalloc_prepare(const fastged_device_batch b, int Wg, int B, int
     for (int p = t; p < b.n_pairs; p += gridDim.x * blockDim.x) {
         order[p] = p;
         const int a = b.pairs[2 * p], d = b.pairs[2 * p + 1];
-        if (a < 0 || d < 0 || a >= b.n_graphs || d >= b.n_graphs) atomicOr(err, kErrInvalid);
+        if (a < 0 || d < 0 || a >= b.n_graphs || d >= b.n_graphs) {
+            atomicOr(err, kErrInvalid);
+            continue;
+        }
+        const int64_t mo = b.map_off[p];
+        if (mo < 0 || mo + max(b.graph_n[a], 0) > b.map_len) atomicOr(err, kErrInvalid);
     }
 }
 
@@ -103,11 +184,12 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     if (K < 1 || K > FASTGED_MAX_K) return set_error(FASTGED_ERR_INVALID_ARG, "K out of range");
     if (b->n_graphs < 0 || b->n_pairs < 0 || b->max_n < 1 || b->max_n > FASTGED_MAX_N ||
         b->max_m < 0 || (int64_t)b->max_m > (int64_t)b->max_n * (b->max_n - 1) / 2 ||
-        b->max_elabel < 0 || b->max_elabel > FASTGED_MAX_ELABEL || b->total_vertices < 0)
+        b->max_elabel < 0 || b->max_elabel > FASTGED_MAX_ELABEL || b->total_vertices < 0 ||
+        b->total_edges < 0 || b->map_len < 0)
         return set_error(FASTGED_ERR_INVALID_ARG, "batch limits out of range");
     if (b->n_pairs == 0) return FASTGED_OK;
     if (!b->graph_n || !b->graph_m || !b->vlabel_off || !b->edge_off || !b->pairs ||
-        !b->map_off || (b->total_vertices > 0 && !b->vlabel))
+        !b->map_off || (b->total_vertices > 0 && !b->vlabel) || (b->total_edges > 0 && !b->edges))
         return set_error(FASTGED_ERR_INVALID_ARG, "null device array");
     {
         const long long n = b->max_n, m = b->max_m;
@@ -119,17 +201,24 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return set_error(FASTGED_ERR_CUDA, "no usable current device");
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            char msg[160];
-            snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return set_error(FASTGED_ERR_CUDA, msg);
+    uint8_t *base = nullptr;
+    {
+        const unsigned long long ctx = current_context_id();
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        ScratchAddr &sa = g_scratch_addr[dev];
+        if (ctx == 0 || sa.ctx != ctx || !sa.addr) {
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                char msg[160];
+                snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+                return set_error(FASTGED_ERR_CUDA, msg);
+            }
+            sa.addr = ptr;
+            sa.ctx = ctx;
         }
-        g_scratch_addr[dev] = ptr;
+        base = (uint8_t *)sa.addr;
     }
-    uint8_t *base = (uint8_t *)g_scratch_addr[dev];
     cudaStream_t st = (cudaStream_t)stream;
 
     // one size class covering every graph of the batch
@@ -170,10 +259,12 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     if (e != cudaSuccess || occ < 1)
         return set_error(FASTGED_ERR_CUDA, "team does not fit on an SM");
 
-    // carve the scratch array: status | graph table | pair order | bitset pools | teams
+    // carve the scratch array: status | graph table | bit-set rows | pair order | bitset
+    // pools | teams
     const size_t off_status = 0;
     const size_t off_meta = 256;
-    const size_t off_order = na_align(off_meta + sizeof(GraphMeta) * (size_t)b->n_graphs, 256);
+    const size_t off_row = na_align(off_meta + sizeof(GraphMeta) * (size_t)b->n_graphs, 256);
+    const size_t off_order = na_align(off_row + 8 * (size_t)b->n_graphs, 256);
     const size_t off_pool = na_align(off_order + 4 * (size_t)b->n_pairs, 256);
     const size_t adj_words = (size_t)b->total_vertices * (size_t)Wg;
     const size_t pool_bytes = 8 * adj_words * (size_t)(1 + B);
@@ -192,6 +283,7 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
 
     int32_t *status = (int32_t *)(base + off_status);   // [0] error bits, [1] queue head
     GraphMeta *meta = (GraphMeta *)(base + off_meta);
+    int64_t *row = (int64_t *)(base + off_row);
     int32_t *order = (int32_t *)(base + off_order);
     uint64_t *pool = (uint64_t *)(base + off_pool);
 
@@ -213,7 +305,11 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
         int pgrid = (int)std::min<int64_t>(4096, ((int64_t)std::max(b->n_graphs, b->n_pairs) * 32 +
                                                   pblock - 1) / pblock);
         pgrid = std::max(pgrid, 1);
-        noalloc_prepare<<<pgrid, pblock, 0, st>>>(*b, Wg, B, b->max_m, meta, order, status);
+        if (b->n_graphs > 0) {
+            noalloc_rows<<<1, 1024, 0, st>>>(b->graph_n, b->n_graphs, row);
+            NA_CK(cudaGetLastError());
+        }
+        noalloc_prepare<<<pgrid, pblock, 0, st>>>(*b, Wg, B, b->max_m, row, meta, order, status);
         NA_CK(cudaGetLastError());
     }
     NA_CK(cudaMemcpyAsync(&host_err, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

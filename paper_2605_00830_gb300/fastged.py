@@ -91,7 +91,8 @@ class DeviceBatch(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
                 ("max_n", ctypes.c_int32), ("max_m", ctypes.c_int32),
                 ("max_elabel", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("total_vertices", ctypes.c_int64),
+                ("total_vertices", ctypes.c_int64), ("total_edges", ctypes.c_int64),
+                ("map_len", ctypes.c_int64),
                 ("graph_n", ctypes.c_void_p), ("graph_m", ctypes.c_void_p),
                 ("vlabel_off", ctypes.c_void_p), ("edge_off", ctypes.c_void_p),
                 ("vlabel", ctypes.c_void_p), ("edges", ctypes.c_void_p),

@@ -38,7 +38,8 @@ def _device_batch(w, torch):
     keep["pairs"] = torch.from_numpy(mm.pairs.reshape(-1)).to(dev)
     keep["moff"] = torch.from_numpy(mm.map_off[:-1].copy()).to(dev)
     maxlab = int(mm.el.max()) if mm.el is not None and mm.el.size else 0
-    b = F.DeviceBatch(len(n), mm.n_pairs, int(n.max()), int(m.max()), maxlab, 0, int(n.sum()),
+    b = F.DeviceBatch(len(n), mm.n_pairs, int(max(n.max(), 1)), int(m.max()), maxlab, 0,
+                      int(n.sum()), int(m.sum()), int(mm.map_off[-1]),
                       keep["n"].data_ptr(), keep["m"].data_ptr(), keep["voff"].data_ptr(),
                       keep["eoff"].data_ptr(), keep["vl"].data_ptr(), keep["ed"].data_ptr(),
                       keep["el"].data_ptr() if keep["el"] is not None else None,
@@ -81,3 +82,96 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     with pytest.raises(F.FastGEDError) as ei:
         F.fastged_batch_noalloc(w.cost, b, w.K, oc.data_ptr(), om.data_ptr())
     assert ei.value.code == F.FASTGED_ERR_INVALID_ARG
+
+
+def _run_noalloc(w, b, mm, torch):
+    """fastged_batch_noalloc on device outputs; (status, cost, map, n_evals) on the host."""
+    oc = torch.full((max(mm.n_pairs, 1),), -7, dtype=torch.int32, device="cuda")
+    om = torch.full((max(int(mm.map_off[-1]), 1),), -7, dtype=torch.int32, device="cuda")
+    on = torch.full((max(mm.n_pairs, 1),), -7, dtype=torch.int64, device="cuda")
+    try:
+        F.fastged_batch_noalloc(w.cost, b, w.K, oc.data_ptr(), om.data_ptr(), on.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+        rc = F.FASTGED_OK
+    except F.FastGEDError as e:
+        rc = e.code
+    torch.cuda.synchronize()
+    return rc, oc.cpu().numpy(), om.cpu().numpy(), on.cpu().numpy()
+
+
+def _bad_cases(w, mm):
+    """(name, change to the device arrays or host bounds) that the device-side checks must
+    reject before any kernel reads an edge or writes a map."""
+    g0 = int(mm.pairs[0][0])
+    return [
+        ("endpoint past n", lambda k, b: k["ed"].__setitem__(0, 999)),
+        ("self-loop", lambda k, b: k["ed"].__setitem__(1, int(k["ed"][0]))),
+        ("pair index past n_graphs", lambda k, b: k["pairs"].__setitem__(1, 10 ** 6)),
+        ("graph_n above max_n", lambda k, b: k["n"].__setitem__(g0, b.max_n + 1)),
+        ("edge range past total_edges",
+         lambda k, b: k["eoff"].__setitem__(g0, b.total_edges)),
+        ("map past map_len", lambda k, b: k["moff"].__setitem__(0, b.map_len)),
+    ]
+
+
+def test_noalloc_rejects_inconsistent_device_data_and_recovers():
+    """Device data that contradicts the host bounds (or is malformed) returns
+    FASTGED_ERR_INVALID_ARG without reading or writing out of range; the next valid call on the
+    same (shared) scratch array gives the results of fastged_batch_ex again."""
+    torch = pytest.importorskip("torch")
+    w = W.config2(60)
+    with F.FastGED(w.cost) as g:
+        ref = g.run(w)
+    for name, spoil in _bad_cases(w, F.marshal(w)):
+        b, keep, mm = _device_batch(w, torch)
+        spoil(keep, b)
+        rc, *_ = _run_noalloc(w, b, mm, torch)
+        assert rc == F.FASTGED_ERR_INVALID_ARG, name
+        b, keep, mm = _device_batch(w, torch)
+        rc, c, m, n = _run_noalloc(w, b, mm, torch)
+        assert rc == F.FASTGED_OK, name
+        for x, y in zip((c, m, n), ref):
+            assert np.array_equal(x, y), name
+
+
+def test_noalloc_eight_label_planes_and_an_empty_batch():
+    """Edge labels up to 5 (three planes, served by the eight-plane kernel), then a batch
+    with no pairs (nothing to do, FASTGED_OK)."""
+    torch = pytest.importorskip("torch")
+    w = W.config2(80, seed=21)
+    st = W.Stream(21, 5)
+    for gr in w.graphs:
+        gr.elabel = st.randint(0, 5, gr.m).astype(np.int32)
+    with F.FastGED(w.cost) as g:
+        ref = g.run(w)
+    b, keep, mm = _device_batch(w, torch)
+    assert b.max_elabel >= 4
+    for _ in range(2):
+        rc, c, m, n = _run_noalloc(w, b, mm, torch)
+        assert rc == F.FASTGED_OK
+        for x, y in zip((c, m, n), ref):
+            assert np.array_equal(x, y)
+    b.n_pairs = 0
+    rc, *_ = _run_noalloc(w, b, mm, torch)
+    assert rc == F.FASTGED_OK
+
+
+def test_noalloc_graphs_sharing_label_rows():
+    """Two graphs whose label ranges coincide (the caller stores one label array for both):
+    each still gets bit-set rows of its own, so the results equal those of two separate
+    copies."""
+    torch = pytest.importorskip("torch")
+    base = W.config2(30, seed=23)
+    a = base.graphs[0]
+    twin = W.Graph(a.n, a.vlabel.copy(), base.graphs[2].edges[:0].copy(), None)
+    # twin: same vertices and labels as graph 0, no edges
+    w = W.Workload("twins", [a, twin, base.graphs[1]],
+                   np.array([[0, 2], [1, 2], [2, 0], [2, 1]], np.int32), base.cost, base.K)
+    with F.FastGED(w.cost) as g:
+        ref = g.run(w)
+    b, keep, mm = _device_batch(w, torch)
+    keep["voff"][1] = keep["voff"][0]    # graph 1 reads graph 0's label rows
+    rc, c, m, n = _run_noalloc(w, b, mm, torch)
+    assert rc == F.FASTGED_OK
+    for x, y in zip((c, m, n), ref):
+        assert np.array_equal(x, y)
