@@ -125,7 +125,7 @@ template <typename Word, int BK, bool FOLD, bool EXACT>
 __device__ __forceinline__ int eval_level(const KParams &p,
                                           const WarpRegs<Word, (BK == 8 ? kMaxB : BK)> &R,
                                           int L, int n0, int deg, int n2, int mrow, int A, int H,
-                                          int &hist)
+                                          int &hist, long long *steps = nullptr)
 {
     constexpr int WB = 8 * (int)sizeof(Word);
     constexpr int NPL = BK == 8 ? kMaxB : BK;
@@ -137,7 +137,6 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
     const uint8_t *mapc = R.mapc(wl);
     const TgtRec<Word, NPL> *tgt = R.tgt(wl);
-    uint16_t *dummy = R.ent(wl) + wl.ent_dummy;
     // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 15 steps into
     // acc[m] = buckets (m, m + 4) and acc[4 + m] = (8 + m, 12 + m), 16 bits each
     uint32_t clo = 0, chi = 0, acc[8];
@@ -194,17 +193,16 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         const int off = tot + incl - cnt;
         if (act) R.nodeoff(wl)[s] = (uint16_t)off;
         const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
+#ifdef FASTGED_PHASE_TIMERS
+        if (steps) *steps += maxc;   // profiling builds: loop steps of the level
+#endif
         Word x = act ? (Word)(~im & nmask) : (Word)0;
-        uint16_t *ep = R.ent(wl) + off;
-        // blocks of 15 steps: a 4-bit counter cannot overflow inside one
-        for (int t0 = 0; t0 < maxc; t0 += 15) {
-        const int t1 = min(maxc, t0 + 15);
-        for (int t = t0; t < t1; ++t) {
-            const bool val = t < cnt;
-            // next free vertex in increasing order; once none is left, the deletion (j = n2)
-            const int f = ffsw(x);
-            const int j = x ? f : n2;
-            x &= x - (Word)1;
+        uint16_t *ent = R.ent(wl);
+        const int dummy = wl.ent_dummy;
+        // two successors of the lane's node per step (its next two free vertices, or the
+        // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
+        // overflow inside one
+        auto score = [&](int j) -> int {
             const TgtRec<Word, NPL> r = tgt[j];
             const Word ai = r.a2 & im;
             int d = base + r.crow;
@@ -220,18 +218,36 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                     if (b < B) ld |= PL[b] ^ rec_plane(r, b);
                 d += c_esub * popcw((Word)(r.a2 & P & ld));
             }
-            uint16_t *dst = val ? ep + t : dummy;
-            if (EXACT) {
-                *dst = (uint16_t)d;
-            } else {
-                *dst = (uint16_t)((min(d, 255) << 8) | j);
-                const int dd = min(d, H - 1);
-                const uint32_t inc = val ? 1u << ((dd & 7) << 2) : 0u;
-                clo += dd < 8 ? inc : 0u;
-                chi += dd < 8 ? 0u : inc;
+            return d;
+        };
+        auto count = [&](int d, bool val) {
+            const int dd = min(d, H - 1);
+            const uint32_t inc = val ? 1u << ((dd & 7) << 2) : 0u;
+            clo += dd < 8 ? inc : 0u;
+            chi += dd < 8 ? 0u : inc;
+        };
+        for (int t0 = 0; t0 < maxc; t0 += 14) {
+            const int t1 = min(maxc, t0 + 14);
+            for (int t = t0; t < t1; t += 2) {
+                const int fa = ffsw(x);
+                const int ja = x ? fa : n2;
+                x &= x - (Word)1;
+                const int fb = ffsw(x);
+                const int jb = x ? fb : n2;
+                x &= x - (Word)1;
+                const bool va = t < cnt, vb = t + 1 < cnt;
+                const int da = score(ja), db = score(jb);
+                if (EXACT) {
+                    ent[va ? off + t : dummy] = (uint16_t)da;
+                    ent[vb ? off + t + 1 : dummy] = (uint16_t)db;
+                } else {
+                    ent[va ? off + t : dummy] = (uint16_t)((min(da, 255) << 8) | ja);
+                    ent[vb ? off + t + 1 : dummy] = (uint16_t)((min(db, 255) << 8) | jb);
+                    count(da, va);
+                    count(db, vb);
+                }
             }
-        }
-        if (!EXACT) flush();
+            if (!EXACT) flush();
         }
         tot += __shfl_sync(FULL, incl, 31);
     }
@@ -383,7 +399,14 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
         const int n0 = R.noff(wl)[i], deg = R.noff(wl)[i + 1] - n0;
         const int A = R.pedc(wl)[0];   // least PED of the kept list: a lower bound of every child
         int hist = 0;
+#ifdef FASTGED_PHASE_TIMERS
+        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist,
+                                                          &ph[9]);
+        ph[10] += tot;   // successors (the loop steps above cover them 32 lanes at a time)
+        ph[11] += 1;     // levels
+#else
         const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist);
+#endif
         nevals += tot;
         WPHASE(1);
         const int newL = min(K, tot);
