@@ -36,15 +36,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 
 # DRAM traffic (read + write bytes) of the K-Best launches of one full-size step, from one ncu
-# capture (profiles/kbest_kernel_molecule_20000.md). It describes the kernels as captured:
-# the bench reports it only while the kernel sources (without their // comments and blank
-# lines) hash to the recorded value.
-KERNEL_SOURCES = ["kbest_impl.cuh", "kbest_kernels.cu", "kbest_b0.cu", "kbest_b2.cu",
-                  "kbest_b8.cu", "fastged_internal.h"]
+# capture of the molecule batch's step (the capture and its command are summarised with the
+# other profiles). It describes the kernels as captured: the bench reports it only while the
+# kernel sources (without their // comments and blank lines) hash to the recorded value.
+KERNEL_SOURCES = ["kbest_impl.cuh", "kbest_warp.cuh", "kbest_kernels.cu", "kbest_b0.cu",
+                  "kbest_b2.cu", "kbest_b8.cu", "fastged_internal.h"]
 CAPTURED_TRAFFIC = {
-    "molecule": {"bytes_per_step": 34230016,
-                 "sources_sha256": "ba45f89b2ad5f9913d5aa65c39860908af970cd58305c6cd12da6c3fe57b6011",
-                 "profile": "profiles/kbest_kernel_molecule_20000.md"},
+    "molecule": {"bytes_per_step": 0, "sources_sha256": ""},
 }
 
 
@@ -102,6 +100,11 @@ def parse_args():
                     help="wall-time bound of each CPU oracle leg (checked between chunks)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-form, e2e, serving and CPU-baseline legs")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the other workloads' sub-records (configs 1, 3, 4, wide beam, "
+                         "size sweep)")
+    ap.add_argument("--suite-cpu-seconds", type=float, default=6.0,
+                    help="wall-time bound of each sub-record's CPU oracle sample")
     ap.add_argument("--serve-window", type=float, default=2.0,
                     help="seconds of Poisson arrivals in the serving leg")
     return ap.parse_args()
@@ -231,6 +234,135 @@ def int_ops_per_eval(W: int, B: int, fold: bool) -> int:
     word = 7 if fold else 11
     lab = (4 * B + 5) if B > 0 else 0
     return (word + lab) * W + 6
+
+
+def algorithmic_work(w, mm, n_out):
+    """(integer ops, substitution successors, algorithmic HBM bytes) of one pass over w.
+
+    Integer ops: each pair's substitution successors (deletions and completions do no bitset
+    work; every level expands at most K nodes with one deletion child each, so this count is
+    a lower bound) times the 32-bit operations of one evaluation for that pair's bitset words.
+    HBM bytes, per pair: both graphs' bitsets (W words per row, 1 + b planes) and labels, the
+    cost and map written back, and for classes whose beam lives in global memory the beam
+    state of every level (2 K (2 n1 + 8 W + 16) bytes) plus 8 bytes per scored successor."""
+    fold = w.cost[4] == w.cost[5]
+    B = 0
+    labs = [int(gr.elabel.max()) for gr in w.graphs if gr.elabel is not None and gr.m > 0]
+    if labs:
+        B = max(labs).bit_length()
+    n2s = mm.n[mm.pairs[:, 1]].astype(np.int64)
+    n1s = mm.n1.astype(np.int64)
+    K = (np.asarray(w.k_per_pair, np.int64) if w.k_per_pair is not None
+         else np.full(mm.n_pairs, w.K, np.int64))
+    subs = np.maximum(n_out - (n1s + 1) * K, 0)
+    ops = 0
+    for p_w, sel in ((0, n2s <= 32), (1, (n2s > 32) & (n2s <= 64)), (2, (n2s > 64) & (n2s <= 128)),
+                     (4, (n2s > 128) & (n2s <= 256)), (8, (n2s > 256) & (n2s <= 512)),
+                     (16, n2s > 512)):
+        ops += int_ops_per_eval(p_w, B, fold) * int(subs[sel].sum())
+    W1 = (n1s + 63) // 64
+    W2 = (n2s + 63) // 64
+    io = (n1s * (8 * W1 * (1 + B) + 1) + n2s * (8 * W2 * (1 + B) + 1) + 4 * (1 + n1s)).sum()
+    # beams in global memory: pairs of more than 128 target vertices, or beams of more than
+    # 2^16 successors per level (the cluster teams' regime)
+    spill = (n2s > 128) | (K * (n2s + 1) >= 65536)
+    beam = (n1s * 2 * np.minimum(K, 1 + n1s * n2s) * (2 * n1s + 8 * W2 + 16))[spill].sum()
+    cand = 8 * n_out[spill].sum()
+    return ops, int(subs.sum()), int(io + beam + cand), bool(spill.any())
+
+
+def measure_plan(F, g, w, popt, stream, flush, steps, warmup, before=None, after=None):
+    """Device-resident plan of w replayed `steps` times (after `warmup` runs) on `stream`, the
+    L2 flushed before every step: (per-step ms list, mean K-Best kernel ms, results, plan
+    info, marshalled batch). before() / after() run just before and after the timed steps
+    (with the device synchronised)."""
+    import torch
+    mm = F.marshal(w)
+    K = w.K if w.k_per_pair is None else max(w.K, int(np.max(w.k_per_pair)))
+    plan = F.fastged_plan_create(g.h, mm, K, popt)
+    for _ in range(warmup):
+        flush.zero_()
+        F.fastged_plan_run(plan, stream.cuda_stream)
+    torch.cuda.synchronize()
+    if before:
+        before()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kms = []
+    for s in range(steps):
+        flush.zero_()
+        e0[s].record(stream)
+        F.fastged_plan_run(plan, stream.cuda_stream)
+        e1[s].record(stream)
+        kms.append(F.fastged_plan_kernel_ms(plan))
+    torch.cuda.synchronize()
+    res_after = after() if after else None
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    c = np.zeros(mm.n_pairs, np.int32)
+    m = np.zeros(int(mm.map_off[-1]), np.int32)
+    n = np.zeros(mm.n_pairs, np.int64)
+    F.fastged_plan_read(plan, c, m, n)
+    info = F.fastged_plan_info(plan)
+    F.fastged_plan_destroy(plan)
+    return step_ms, float(np.mean(kms)), (c, m, n), info, mm, res_after
+
+
+# the other workloads measured beside the headline (one line, sub-records under "suite")
+SUITE = [
+    ("config1", "config1", {}, "tiny ER batch (config 1): 200 pairs, 5-8 vertices, K=16, unit costs"),
+    ("dense", "config3", {}, WORKLOADS["dense"][3] + " (config 3)"),
+    ("large", "config4", {}, WORKLOADS["large"][3] + " (config 4)"),
+    ("widebeam", "config_wide_beam", {}, WORKLOADS["widebeam"][3]),
+] + [(f"sizesweep_n{n}", "config_size_sweep", {"n": n},
+      f"graph-size sweep: one pair of G({n}, 0.4) graphs, 4 labels, K=5,000, setting-1 costs")
+     for n in (50, 200, 500, 950)]
+
+
+def suite_leg(F, g_cost_cache, stream, flush, alu_peak, hbm_peak, cpu_seconds):
+    """Every SUITE workload through the same plan path as the headline (built-in team rules,
+    no autotuning): pairs/s, evaluations/s, kernel time, ALU roofline (and HBM roofline where
+    the beam lives in global memory), and a bounded CPU oracle sample."""
+    from paper_2605_00830_gb300 import workloads as W
+    out = {}
+    threads = os.cpu_count() or 1
+    for key, fn, extra, desc in SUITE:
+        w = getattr(W, fn)(**extra)
+        g = g_cost_cache.get(tuple(w.cost))
+        if g is None:
+            g = g_cost_cache[tuple(w.cost)] = F.FastGED(w.cost)
+        big = key in ("large",) or key.startswith("sizesweep_n9")
+        steps, warm = (2, 1) if big else (5, 2)
+        step_ms, kms, (c, m, n), info, mm, _ = measure_plan(F, g, w, F.make_options(), stream,
+                                                            flush, steps, warm)
+        ops, subs, hbm, spill = algorithmic_work(w, mm, n)
+        rec = {"workload": desc, "n_pairs": w.n_pairs, "K": w.K, "steps": steps,
+               "ms_per_step": float(np.mean(step_ms)), "kernel_ms": kms,
+               "value": w.n_pairs / (np.mean(step_ms) / 1e3), "unit": UNIT,
+               "evals_per_step": int(n.sum()),
+               "evals_per_s": int(n.sum()) / (np.mean(step_ms) / 1e3),
+               "gpu_launches": info["launches_per_run"],
+               "classes": {"block_threads": info["block_threads"][:info["n_classes"]],
+                           "words": info["words"][:info["n_classes"]]},
+               "roofline": {"bound": "alu", "achieved": ops / (kms / 1e3) / 1e12,
+                            "peak": alu_peak / 1e12, "unit": "Tops/s (32-bit integer)",
+                            "frac": ops / (kms / 1e3) / alu_peak if alu_peak > 0 else None,
+                            "ops_per_eval": ops / max(1, subs)}}
+        if spill:
+            rec["roofline_hbm"] = {"bound": "hbm", "achieved": hbm / (kms / 1e3) / 1e9,
+                                   "peak": hbm_peak, "unit": "GB/s", "bytes_per_step": hbm,
+                                   "frac": hbm / (kms / 1e3) / 1e9 / hbm_peak if hbm_peak else None,
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        idx = list(range(w.n_pairs))
+        dt, res = run_cpu_oracle(w, idx, threads, cpu_seconds)
+        if dt is None:
+            rec["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": threads,
+                                   "kind": "oracle", "sample": res}
+        else:
+            rec["cpu_baseline"] = {"value": len(res) / dt, "unit": UNIT, "cores": threads,
+                                   "kind": "oracle",
+                                   "sample": f"first {len(res)} of the {w.n_pairs:,} pairs"}
+        out[key] = rec
+    return out
 
 
 def serving_leg(window_s: float, rate: float = 5000.0):
@@ -386,65 +518,29 @@ def ours(args):
     popt = (F.make_options(block_threads=args.block, team=team, hist_window=args.hist_window)
             if args.block else
             F.make_options(autotune=1, team=team, hist_window=args.hist_window))
-    plan = F.fastged_plan_create(g.h, mm, w.K, popt)
     # a dedicated stream: the legacy default stream has handle 0, which the C ABI reads as
     # "the plan's own stream"
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    c_out = np.zeros(mm.n_pairs, np.int32)
-    m_out = np.zeros(int(mm.map_off[-1]), np.int32)
-    n_out = np.zeros(mm.n_pairs, np.int64)
-
-    for _ in range(max(args.warmup, 3)):
-        flush.zero_()
-        F.fastged_plan_run(plan, stream.cuda_stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    clocks.start()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kms = []
-    for s in range(args.steps):
-        flush.zero_()
-        e0[s].record(stream)
-        F.fastged_plan_run(plan, stream.cuda_stream)
-        e1[s].record(stream)
-        kms.append(F.fastged_plan_kernel_ms(plan))
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    clk = clocks.stop()
+
+    def before():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+
+    step_ms, kernel_ms, (c_out, m_out, n_out), info, mm, clk = measure_plan(
+        F, g, w, popt, stream, flush, args.steps, max(args.warmup, 3), before, clocks.stop)
     tot_ms = max_over_ranks(float(sum(step_ms)))
     if ws > 1:
         torch.distributed.barrier()
-    F.fastged_plan_read(plan, c_out, m_out, n_out)
-    info = F.fastged_plan_info(plan)
     evals = int(n_out.sum())
     value = mm.n_pairs * ws * args.steps / (tot_ms / 1e3)
 
     # roofline of the K-Best launches (ALU bound)
-    fold = w.cost[4] == w.cost[5]
-    B = 0
-    labs = [int(gr.elabel.max()) for gr in w.graphs if gr.elabel is not None and gr.m > 0]
-    if labs:
-        B = max(labs).bit_length()
-    # Algorithmic integer work of the K-Best launches: each pair's substitution successors
-    # (deletions and completions do no bitset work; every level expands at most K nodes with
-    # one deletion child each, so this count is a lower bound) times the 32-bit operations
-    # of one evaluation for that pair's bitset words (one 32-bit word when n2 <= 32).
-    n2s = mm.n[mm.pairs[:, 1]].astype(np.int64)
-    n1s = mm.n1.astype(np.int64)
-    subs = np.maximum(n_out - (n1s + 1) * w.K, 0)
-    ops = 0
-    for p_w, sel in ((0, n2s <= 32), (1, (n2s > 32) & (n2s <= 64)), (2, (n2s > 64) & (n2s <= 128)),
-                     (4, (n2s > 128) & (n2s <= 256)), (8, (n2s > 256) & (n2s <= 512)),
-                     (16, n2s > 512)):
-        ops += int_ops_per_eval(p_w, B, fold) * int(subs[sel].sum())
-    Wd = max(info["words"]) if info["words"] else 1
-    kernel_ms = float(np.mean(kms))
+    ops, subs, hbm_bytes, _ = algorithmic_work(w, mm, n_out)
     # the integer peak is measured on rank 0 only, which alone prints the line
     peak = F.fastged_measure_int_peak() if rank == 0 else {"lop3": 0, "iadd": 0, "popc": 0}
     alu_peak = min(peak["lop3"], peak["iadd"])
@@ -466,7 +562,7 @@ def ours(args):
                          "unit": "Tops/s (32-bit integer)", "frac": frac,
                          "traffic": traffic,
                          "traffic_unit": "DRAM bytes per step (both K-Best launches, ncu)",
-                         "ops_per_eval": ops / max(1, int(subs.sum())),
+                         "ops_per_eval": ops / max(1, subs),
                          "peak_source": "measured in-run: LOP3/IADD probe kernels (min of the two)",
                          "popc_peak": peak["popc"] / 1e12},
             "clocks": clk}
@@ -516,6 +612,10 @@ def ours(args):
         line["serve"] = serving_leg(args.serve_window)
         # the same stream at a load the GPU sustains (the 5,000 req/s stream saturates it)
         line["serve_sustained"] = serving_leg(args.serve_window, rate=1000.0)
+    if rank == 0 and ws == 1 and not args.no_extras and not args.no_suite:
+        hbm_peak = float(peaks.get("hbm_gbs", 0.0))
+        line["suite"] = suite_leg(F, {tuple(w.cost): g}, stream, flush, alu_peak, hbm_peak,
+                                  args.suite_cpu_seconds)
     if rank == 0 and ws == 1 and not args.no_extras:
         # CPU oracle on a bounded sample (at most cpu_sample pairs and about cpu_seconds of
         # wall time), all host cores
@@ -531,7 +631,6 @@ def ours(args):
                 line[key] = {"value": len(res) / dt, "unit": UNIT, "cores": cores,
                              "kind": "oracle",
                              "sample": f"first {len(res)} of the {w.n_pairs:,} pairs"}
-    F.fastged_plan_destroy(plan)
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

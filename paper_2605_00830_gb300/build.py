@@ -3,6 +3,12 @@
 Translation units are compiled in parallel to objects under ``_build/`` and linked into one
 shared library with the CUDA runtime linked statically, so nothing outside the tree is
 needed at run time. Rebuilds only when a source or header is newer than the library.
+
+build(checked=True) makes the bounds-checked library (``-DFASTGED_BOUNDS_CHECK``): every
+index of the K-Best kernels is checked against its array, a violation is reported through
+the batch's status word (the access goes to the array's first element instead) and the
+call fails with FASTGED_ERR_CUDA. It is a debugging build; the binding loads it when the
+environment variable FASTGED_LIBRARY names it.
 """
 from __future__ import annotations
 
@@ -22,8 +28,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 
-def lib_path() -> str:
-    return os.path.join(BUILD, f"libfastged_{platform.machine()}.so")
+def lib_path(checked: bool = False) -> str:
+    tag = "_checked" if checked else ""
+    return os.path.join(BUILD, f"libfastged{tag}_{platform.machine()}.so")
 
 
 def _deps():
@@ -42,8 +49,8 @@ def _stale(target: str) -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    out = lib_path()
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out = lib_path(checked)
     if not force and not _stale(out):
         return out
     os.makedirs(BUILD, exist_ok=True)
@@ -51,9 +58,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     "-I", INCLUDE, "-I", CSRC]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    if checked:
+        flags += ["-DFASTGED_BOUNDS_CHECK"]
+    tag = "_checked" if checked else ""
 
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", f"_{platform.machine()}.o"))
+        obj = os.path.join(BUILD, src.replace(".cu", f"{tag}_{platform.machine()}.o"))
         cmd = [NVCC] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -77,4 +87,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

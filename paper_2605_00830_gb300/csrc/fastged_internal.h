@@ -63,6 +63,7 @@ struct Layout {
     // slice per CTA (at cta_off + cluster rank * cta_bytes; their off[] is inside the block)
     uint32_t cta_mask;
     int64_t cta_off, cta_bytes;
+    int64_t rsize[RG_COUNT];   // bytes of every region (bounds-checked builds check against it)
 };
 
 // One-warp teams (kbest_warp_kernel): every warp of a CTA solves its own pair in its own
@@ -100,6 +101,7 @@ struct WarpLayout {
     int32_t mrow;         // bytes per stored vertex map (a multiple of 16)
     int32_t ent_dummy;    // entry index past every level's successors (kmax * (n2max + 1)):
                           // where lanes without a successor at a step store
+    int32_t size[WR_COUNT];   // bytes of every region (bounds-checked builds check against it)
 };
 
 struct KParams {
@@ -130,6 +132,8 @@ struct KParams {
     WarpLayout wl;               // one-warp teams only
     // per-phase cycle counters; profiling builds only (nullptr otherwise)
     unsigned long long *phase_cycles;
+    // element counts of the batch arrays (bounds-checked builds check every index against them)
+    int64_t n_graphs, n_pairs, n_vlab, adj_words, plane_words, map_total;
 };
 
 struct PackParams {
@@ -145,5 +149,24 @@ struct PackParams {
 
 // error bits written by kernels into *err
 constexpr int32_t kErrDuplicateEdge = 1;
+// bounds-checked builds (FASTGED_BOUNDS_CHECK): an index left its array; err[2] holds the
+// source line of the first such access (the access itself went to the array's element 0)
+constexpr int32_t kErrBounds = 4;
+
+#ifdef FASTGED_BOUNDS_CHECK
+__device__ __forceinline__ int64_t fg_bound(int64_t i, int64_t n, int line, int32_t *err)
+{
+    if (i >= 0 && i < n) return i;
+    atomicOr(err, kErrBounds);
+    atomicCAS(err + 2, 0, line);
+    return 0;
+}
+// element i of array a that holds n elements (n counted in elements)
+#define FG_AT(a, i, n) ((a)[fg_bound((int64_t)(i), (int64_t)(n), __LINE__, p.err)])
+#else
+#define FG_AT(a, i, n) ((a)[(i)])
+#endif
+// elements of type T in a region of `bytes` bytes
+#define FG_N(T, bytes) ((int64_t)(bytes) / (int64_t)sizeof(T))
 
 }  // namespace fastged

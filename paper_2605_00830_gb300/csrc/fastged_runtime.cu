@@ -446,6 +446,12 @@ void fastged::plan_layout(ClassPlan &cp, int B, int block, size_t budget)
         return r == RG_ALPHA2 || r == RG_A2T || r == RG_L2T || r == RG_NOFF || r == RG_NBR ||
                r == RG_P || r == RG_PL || r == RG_SBASE || r == RG_IMGL || r == RG_CROW;
     };
+    for (int r = 0; r < RG_COUNT; ++r) L.rsize[r] = (int64_t)align_up(sz[r], 16);
+#ifdef FASTGED_BOUNDS_CHECK
+    // tests of the checked build: declare the selection list four entries long (the buffer
+    // keeps its real size), so that the kernels' own accesses trip the check
+    if (getenv("FASTGED_CHECK_SHRINK_SEL")) L.rsize[RG_SEL] = 16;
+#endif
     size_t s_used = 0, g_used = 0, c_used = 0;
     L.smem_mask = 0;
     L.cta_mask = 0;
@@ -504,6 +510,7 @@ size_t fastged::plan_warp_layout(ClassPlan &cp, int B, bool gmap)
     size_t sh = 0, gl = 0;
     for (int r = 0; r < WR_COUNT; ++r) {
         const size_t a = align_up(sz[r], 16);
+        wl.size[r] = (int32_t)a;
         if (gmap && (r == WR_MAP0 || r == WR_MAP1)) {
             wl.off[r] = (int32_t)gl;
             gl += a;
@@ -512,6 +519,9 @@ size_t fastged::plan_warp_layout(ClassPlan &cp, int B, bool gmap)
             sh += a;
         }
     }
+#ifdef FASTGED_BOUNDS_CHECK
+    if (getenv("FASTGED_CHECK_SHRINK_SEL")) wl.size[WR_SEL] = 16;   // see plan_layout
+#endif
     wl.warp_bytes = (int32_t)sh;
     wl.gmap = gmap ? 1 : 0;
     wl.gmap_bytes = gmap ? (int32_t)align_up(gl, 256) : 0;
@@ -1228,6 +1238,12 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     p.gscratch = wk + b.woff_scratch + cp.scratch_off;
     p.lay = cp.lay;
     p.wl = cp.wl;
+    p.n_graphs = b.n_graphs;
+    p.n_pairs = b.n_pairs;
+    p.n_vlab = b.n_vlab;
+    p.adj_words = b.adj_words;
+    p.plane_words = b.plane_words;
+    p.map_total = b.map_total;
 #ifdef FASTGED_PHASE_TIMERS
     if (!g_phase_dev && cudaMalloc(&g_phase_dev, 128) == cudaSuccess) cudaMemset(g_phase_dev, 0, 128);
     p.phase_cycles = g_phase_dev;
@@ -1332,6 +1348,11 @@ int fastged::finish_outputs(const Batch &b, const uint8_t *host_out, int32_t *ou
     NvtxRange r("fastged results");
     const int32_t err = *(const int32_t *)(host_out + b.woff_err);
     if (err & kErrDuplicateEdge) return set_error(FASTGED_ERR_INVALID_ARG, "duplicate edge in a graph");
+    if (err & kErrBounds) {
+        const int32_t line = ((const int32_t *)(host_out + b.woff_err))[2];
+        return set_error(FASTGED_ERR_CUDA, "device bounds check failed (first at source line " +
+                                               std::to_string(line) + ")");
+    }
     if (err) return set_error(FASTGED_ERR_CUDA, "device error flag " + std::to_string(err));
     if (out_cost) memcpy(out_cost, host_out + b.woff_cost, 4 * (size_t)b.n_pairs);
     if (out_nevals) memcpy(out_nevals, host_out + b.woff_nev, 8 * (size_t)b.n_pairs);

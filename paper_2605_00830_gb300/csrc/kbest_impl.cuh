@@ -161,18 +161,19 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned valid, const unsig
 
 // PED of successor entry k: a packed 32-bit entry (PED << 16 | parent slot << jbits | j) or
 // an unpacked 64-bit one (PED << 32 | parent slot << kSelShift | j).
-__device__ __forceinline__ int entry_ped(const int32_t *cand, int64_t k, bool pk)
+__device__ __forceinline__ int entry_ped(const KParams &p, const int32_t *cand, int64_t k, bool pk)
 {
-    return pk ? (int)(((const uint32_t *)cand)[k] >> 16)
-              : (int)(((const uint64_t *)cand)[k] >> 32);
+    return pk ? (int)(FG_AT((const uint32_t *)cand, k, FG_N(uint32_t, p.lay.rsize[RG_CAND])) >> 16)
+              : (int)(FG_AT((const uint64_t *)cand, k, FG_N(uint64_t, p.lay.rsize[RG_CAND])) >> 32);
 }
 
 // Stable compaction of the kept successors of this warp, in enumeration order: every
 // candidate with PED < T, and the first q with PED == T counted over the whole team.
 // keep_before / eq_before: kept / tied candidates of the warps before this one.
 template <typename Word>
-__device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, int n, int T,
-                                           int q, int keep_before, int eq_before, bool pk)
+__device__ __forceinline__ int compact_kept(const KParams &p, const Regions<Word> &R, int base,
+                                           int n, int T, int q, int keep_before, int eq_before,
+                                           bool pk)
 {
     const int lane = threadIdx.x & 31;
     const int keep0 = keep_before;
@@ -185,7 +186,7 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = kb + 32 * u + lane;
-            v[u] = k < n ? entry_ped(R.cand, (int64_t)base + k, pk) : INT_MAX;
+            v[u] = k < n ? entry_ped(p, R.cand, (int64_t)base + k, pk) : INT_MAX;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(0xffffffffu, v[u] <= T);
@@ -200,8 +201,8 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
             const unsigned kbm = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int pos = keep_before + __popc(kbm & lanemask_lt());
-                R.klist[pos] = base + kb + 32 * u + lane;
-                R.kped[pos] = v[u];
+                FG_AT(R.klist, pos, FG_N(int32_t, p.lay.rsize[RG_KLIST])) = base + kb + 32 * u + lane;
+                FG_AT(R.kped, pos, FG_N(int32_t, p.lay.rsize[RG_KPED])) = v[u];
             }
             keep_before += __popc(kbm);
             eq_before += __popc(eqb);
@@ -214,22 +215,27 @@ __device__ __forceinline__ int compact_kept(const Regions<Word> &R, int base, in
 // smallest PED is found by bisection over team-wide counts, the kept candidates are
 // compacted stably, and ranked by (PED, enumeration order); sel receives successor indices.
 template <typename MapT, typename Word, bool CL, typename TS>
-__device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t *kped,
-                                          int32_t *sel, int32_t *selped, TS &S, int L,
-                                          int stride, int newL, int lo, bool pk)
+__device__ __noinline__ void select_exact(const KParams &p, int32_t *cand, int32_t *klist,
+                                          int32_t *kped, int32_t *sel, int32_t *selped, TS &S,
+                                          int L, int stride, int newL, int lo, bool pk)
 {
     const Team<CL> tm;
     const int tid = tm.tid, lane = threadIdx.x & 31, warp = tm.warp;
     const int T = tm.T, NW = tm.NW;
     const int s_lo = (warp * L) / NW;
-    const int base = s_lo * stride, n = S.wn[warp];
+#define NKP FG_N(int32_t, p.lay.rsize[RG_KPED])
+#define NKL FG_N(int32_t, p.lay.rsize[RG_KLIST])
+#define NSE FG_N(int32_t, p.lay.rsize[RG_SEL])
+#define NSP FG_N(int32_t, p.lay.rsize[RG_SELPED])
+#define NSW ((int64_t)(sizeof(S.wn) / sizeof(S.wn[0])))
+    const int base = s_lo * stride, n = FG_AT(S.wn, warp, NSW);
     Regions<Word> R;
     R.cand = cand;
     R.klist = klist;
     R.kped = kped;
 
     int mx = 0;
-    for (int k = lane; k < n; k += 32) mx = max(mx, entry_ped(cand, base + k, pk));
+    for (int k = lane; k < n; k += 32) mx = max(mx, entry_ped(p, cand, base + k, pk));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) S.mx = 0;
@@ -242,7 +248,7 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (lo < hi) {
         const int mid = lo + (hi - lo) / 2;
         int cnt = 0;
-        for (int k = lane; k < n; k += 32) cnt += (entry_ped(cand, base + k, pk) <= mid);
+        for (int k = lane; k < n; k += 32) cnt += (entry_ped(p, cand, base + k, pk) <= mid);
         cnt = warp_sum(cnt);
         tm.sync();
         if (tid == 0) S.cnt = 0;
@@ -254,37 +260,38 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     const int thr = lo;
     int nlt = 0, neq = 0;
     for (int k = lane; k < n; k += 32) {
-        const int v = entry_ped(cand, base + k, pk);
+        const int v = entry_ped(p, cand, base + k, pk);
         nlt += (v < thr);
         neq += (v == thr);
     }
     nlt = warp_sum(nlt);
     neq = warp_sum(neq);
-    if (lane == 0) { S.wlt[warp] = nlt; S.weq[warp] = neq; }
+    if (lane == 0) { FG_AT(S.wlt, warp, NSW) = nlt; FG_AT(S.weq, warp, NSW) = neq; }
     tm.sync();
     int lt_all = 0;
-    for (int w = 0; w < NW; ++w) lt_all += S.wlt[w];
+    for (int w = 0; w < NW; ++w) lt_all += FG_AT(S.wlt, w, NSW);
     const int q = newL - lt_all;
     int keep_before = 0, eq_before = 0;
     for (int w = 0; w < warp; ++w) {
-        keep_before += S.wlt[w];
-        eq_before += S.weq[w];
+        keep_before += FG_AT(S.wlt, w, NSW);
+        eq_before += FG_AT(S.weq, w, NSW);
     }
     keep_before += min(q, eq_before);
-    compact_kept<Word>(R, base, n, thr, q, keep_before, eq_before, pk);
+    compact_kept<Word>(p, R, base, n, thr, q, keep_before, eq_before, pk);
     tm.sync();
     // order by (PED, enumeration order); klist is in enumeration order and its entries are
     // increasing, so (kped, klist) is that key
     if (newL <= 2048) {
         for (int a = tid; a < newL; a += T) {
-            const int pa = kped[a];
+            const int pa = FG_AT(kped, a, NKP);
             int rank = 0;
             for (int b = 0; b < newL; ++b) {
-                const int pb = kped[b];
+                const int pb = FG_AT(kped, b, NKP);
                 rank += (pb < pa) || (pb == pa && b < a);
             }
-            sel[rank] = klist[a];   // successor index; the caller turns it into (slot, j)
-            selped[rank] = pa;
+            // successor index; the caller turns it into (slot, j)
+            FG_AT(sel, rank, NSE) = FG_AT(klist, a, NKL);
+            FG_AT(selped, rank, NSP) = pa;
         }
         return;
     }
@@ -295,11 +302,13 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
     while (N < newL) N <<= 1;
     auto cmpswap = [&](int i, int j) {
         if (j >= newL) return;
-        const int pi = kped[i], pj = kped[j];
-        const int li = klist[i], lj = klist[j];
+        const int pi = FG_AT(kped, i, NKP), pj = FG_AT(kped, j, NKP);
+        const int li = FG_AT(klist, i, NKL), lj = FG_AT(klist, j, NKL);
         if (pj < pi || (pj == pi && lj < li)) {
-            kped[i] = pj; kped[j] = pi;
-            klist[i] = lj; klist[j] = li;
+            FG_AT(kped, i, NKP) = pj;
+            FG_AT(kped, j, NKP) = pi;
+            FG_AT(klist, i, NKL) = lj;
+            FG_AT(klist, j, NKL) = li;
         }
     };
     for (int size = 2; size <= N; size <<= 1) {
@@ -319,9 +328,14 @@ __device__ __noinline__ void select_exact(int32_t *cand, int32_t *klist, int32_t
         }
     }
     for (int a = tid; a < newL; a += T) {
-        sel[a] = klist[a];
-        selped[a] = kped[a];
+        FG_AT(sel, a, NSE) = FG_AT(klist, a, NKL);
+        FG_AT(selped, a, NSP) = FG_AT(kped, a, NKP);
     }
+#undef NKP
+#undef NKL
+#undef NSE
+#undef NSP
+#undef NSW
 }
 
 // BK: edge-label planes known at compile time: 0 (unlabelled), 2 (exactly two planes), or
@@ -338,10 +352,11 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     const int T = tm.T, NW = tm.NW;
     // CTA-local threads (staging of the per-CTA read-only tables)
     const int ltid = threadIdx.x, LT = blockDim.x;
-    const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
-    const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
+    const int g1 = FG_AT(p.pairs, 2 * pair, 2 * p.n_pairs);
+    const int g2 = FG_AT(p.pairs, 2 * pair + 1, 2 * p.n_pairs);
+    const GraphMeta m1 = FG_AT(p.gmeta, g1, p.n_graphs), m2 = FG_AT(p.gmeta, g2, p.n_graphs);
     const int n1 = m1.n, n2 = m2.n, W1 = m1.W, W2 = m2.W;
-    const int K = p.kpp ? p.kpp[pair] : p.K;
+    const int K = p.kpp ? FG_AT(p.kpp, pair, p.n_pairs) : p.K;
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
     const int N2S = p.lay.n2s;
     const int KM = p.lay.kloc;   // node slots of the P / PL / sbase tables this CTA indexes
@@ -377,39 +392,46 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         for (int idx = ltid; idx < W * n2; idx += LT) {
             const int w = idx / n2, u = idx - w * n2;
             const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
-            R.a2t[w * N2S + u] = (w64 < W2) ? (Word)(adj2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
+            FG_AT(R.a2t, w * N2S + u, FG_N(Word, p.lay.rsize[RG_A2T])) =
+                (w64 < W2) ? (Word)(FG_AT(adj2, (int64_t)u * W2 + w64, p.adj_words - m2.adj_off) >> sh)
+                           : (Word)0;
         }
         for (int b = 0; b < B; ++b) {
             const uint64_t *pl2 = p.planes + m2.plane_off + (int64_t)b * n2 * W2;
             for (int idx = ltid; idx < W * n2; idx += LT) {
                 const int w = idx / n2, u = idx - w * n2;
                 const int w64 = (w * WB) >> 6, sh = (w * WB) & 63;
-                R.l2t[(b * W + w) * N2S + u] =
-                    (w64 < W2) ? (Word)(pl2[(int64_t)u * W2 + w64] >> sh) : (Word)0;
+                FG_AT(R.l2t, (b * W + w) * N2S + u, FG_N(Word, p.lay.rsize[RG_L2T])) =
+                    (w64 < W2) ? (Word)(FG_AT(pl2, (int64_t)u * W2 + w64,
+                                              p.plane_words - m2.plane_off - (int64_t)b * n2 * W2) >> sh)
+                               : (Word)0;
             }
         }
-        for (int u = ltid; u < n2; u += LT) R.alpha2[u] = p.vlab[m2.lab_off + u];
+        for (int u = ltid; u < n2; u += LT)
+            FG_AT(R.alpha2, u, FG_N(int32_t, p.lay.rsize[RG_ALPHA2])) = FG_AT(p.vlab, m2.lab_off + u, p.n_vlab);
         // column n2 of the target tables is the deletion v_i -> eps: no g2 neighbours, so the
         // substitution formula scores it with the deletion's edge costs (see succ_ped)
-        for (int w = ltid; w < W; w += LT) R.a2t[w * N2S + n2] = (Word)0;
-        for (int x = ltid; x < B * W; x += LT) R.l2t[x * N2S + n2] = (Word)0;
+        for (int w = ltid; w < W; w += LT) FG_AT(R.a2t, w * N2S + n2, FG_N(Word, p.lay.rsize[RG_A2T])) = (Word)0;
+        for (int x = ltid; x < B * W; x += LT) FG_AT(R.l2t, x * N2S + n2, FG_N(Word, p.lay.rsize[RG_L2T])) = (Word)0;
         // S1 cost row of level 0 (the row of level i + 1 is written during level i)
         if (n1 > 0) {
-            const int a10 = p.vlab[m1.lab_off];
+            const int a10 = FG_AT(p.vlab, m1.lab_off, p.n_vlab);
             for (int u = ltid; u <= n2; u += LT)
-                R.crow[u] = u < n2 ? ((p.vlab[m2.lab_off + u] != a10) ? c.vsub : 0) : c.vdel;
+                FG_AT(R.crow, u, FG_N(int32_t, p.lay.rsize[RG_CROW])) =
+                    u < n2 ? ((FG_AT(p.vlab, m2.lab_off + u, p.n_vlab) != a10) ? c.vsub : 0) : c.vdel;
         }
         // number of neighbours v_k of v_i with k < i
         for (int v = ltid; v < n1; v += LT) {
-            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+            const int64_t row = m1.adj_off + (int64_t)v * W1;
             int d = 0;
-            for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
-            R.noff[v + 1] = d;
+            for (int w = 0; w < W1; ++w)
+                d += __popcll(FG_AT(p.adj, row + w, p.adj_words) & low_mask(v, w));
+            FG_AT(R.noff, v + 1, FG_N(int32_t, p.lay.rsize[RG_NOFF])) = d;
         }
-        if (ltid == 0) R.noff[0] = 0;
+        if (ltid == 0) FG_AT(R.noff, 0, FG_N(int32_t, p.lay.rsize[RG_NOFF])) = 0;
         // root node: empty lambda, R_V2 = V2, PED 0
-        for (int w = tid; w < W; w += T) R.img0[w] = (Word)0;
-        if (tid == 0) R.ped0[0] = 0;
+        for (int w = tid; w < W; w += T) FG_AT(R.img0, w, FG_N(Word, p.lay.rsize[RG_IMG0])) = (Word)0;
+        if (tid == 0) FG_AT(R.ped0, 0, FG_N(int32_t, p.lay.rsize[RG_PED0])) = 0;
     }
     __syncthreads();
     // prior-neighbour lists of g1: nbr[noff[i] .. noff[i+1]) = k | (edge label << 16)
@@ -417,31 +439,32 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int carry = 0;
         for (int v0 = 0; v0 < n1; v0 += 32) {
             const int v = v0 + lane;
-            const int d = v < n1 ? R.noff[v + 1] : 0;
+            const int d = v < n1 ? FG_AT(R.noff, v + 1, FG_N(int32_t, p.lay.rsize[RG_NOFF])) : 0;
             int incl = d;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            if (v < n1) R.noff[v + 1] = carry + incl;
+            if (v < n1) FG_AT(R.noff, v + 1, FG_N(int32_t, p.lay.rsize[RG_NOFF])) = carry + incl;
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
     __syncthreads();
     for (int v = ltid; v < n1; v += LT) {
-        const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
-        const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
+        const int64_t row = m1.adj_off + (int64_t)v * W1;
+        const int64_t pl = m1.plane_off + (int64_t)v * W1;
         const int64_t pstep = (int64_t)n1 * W1;
-        int o = R.noff[v];
+        int o = FG_AT(R.noff, v, FG_N(int32_t, p.lay.rsize[RG_NOFF]));
         for (int w = 0; w < W1; ++w) {
-            uint64_t bits = row[w] & low_mask(v, w);
+            uint64_t bits = FG_AT(p.adj, row + w, p.adj_words) & low_mask(v, w);
             while (bits) {
                 const int t = __ffsll((long long)bits) - 1;
                 bits &= bits - 1ull;
                 int lab = 0;
-                for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
-                R.nbr[o++] = (w * 64 + t) | (lab << 16);
+                for (int b = 0; b < B; ++b)
+                    lab |= (int)((FG_AT(p.planes, pl + b * pstep + w, p.plane_words) >> t) & 1ull) << b;
+                FG_AT(R.nbr, o++, FG_N(int32_t, p.lay.rsize[RG_NBR])) = (w * 64 + t) | (lab << 16);
             }
         }
     }
@@ -452,11 +475,22 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     Word *imgc = R.img0, *imgn = R.img1;
     int32_t *pedc = R.ped0, *pedn = R.ped1;
     int32_t *crc = R.crow, *crn = R.crow + N2S;   // S1 cost rows of this level and the next
+    // elements of the beam buffers (both buffers of a pair have the same size), the cost-row
+    // halves, the P / PL / sbase tables, the maps in MapT and 16-byte units, the entries
+#define NIMG FG_N(Word, p.lay.rsize[RG_IMG0])
+#define NPED FG_N(int32_t, p.lay.rsize[RG_PED0])
+#define NSW ((int64_t)(sizeof(S.wn) / sizeof(S.wn[0])))   // warps the team scalars hold
+#define NP FG_N(Word, p.lay.rsize[RG_P])
+#define NMAPT FG_N(MapT, p.lay.rsize[RG_MAP0])
+#define NMAP16 FG_N(uint4, p.lay.rsize[RG_MAP0])
+#define NCK FG_N(uint32_t, p.lay.rsize[RG_CAND])
+#define NCK64 FG_N(uint64_t, p.lay.rsize[RG_CAND])
+#define NIMGW (CL ? FG_N(Word, p.lay.rsize[RG_IMGL]) : NIMG)
     tm.sync();
     PHASE_MARK(0);
 
     for (int i = 0; i < n1; ++i) {
-        const int n0 = R.noff[i], deg = R.noff[i + 1] - n0;
+        const int n0 = FG_AT(R.noff, i, FG_N(int32_t, p.lay.rsize[RG_NOFF])), deg = FG_AT(R.noff, i + 1, FG_N(int32_t, p.lay.rsize[RG_NOFF])) - n0;
         const int s_lo = (warp * L) / NW, s_hi = ((warp + 1) * L) / NW;
         const int base = s_lo * stride;              // this warp's successor storage
         // node tables the warp prepares and evaluates are indexed from cs0: 0 for a one-CTA
@@ -469,7 +503,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int r0 = (int)cluster_rank() * nwl;
             cs0 = (r0 * L) / NW;
             const int cs1 = ((r0 + nwl) * L) / NW;
-            for (int x = ltid; x < (cs1 - cs0) * W; x += LT) R.imgl[x] = imgc[(int64_t)cs0 * W + x];
+            for (int x = ltid; x < (cs1 - cs0) * W; x += LT)
+                FG_AT(R.imgl, x, FG_N(Word, p.lay.rsize[RG_IMGL])) = FG_AT(imgc, (int64_t)cs0 * W + x, NIMG);
             __syncthreads();
             imgw = R.imgl;
             ioff = cs0;
@@ -478,7 +513,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int kw = 0;          // successors of this warp so far
         int wmin = INT_MAX;  // least PED this warp scored
         // PED of successor idx
-        auto ped_at = [&](int idx) -> int { return entry_ped(R.cand, idx, pk); };
+        auto ped_at = [&](int idx) -> int { return entry_ped(p, R.cand, idx, pk); };
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
@@ -487,8 +522,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             if (act) {
                 // S2: P = images of the substituted g1 neighbours of v_i (their edge labels in
                 // bit-planes PL at the image positions); dcnt = deleted neighbours
-                Word *Ps = R.P + (int64_t)(s - cs0) * W;
-                const MapT *ms = (const MapT *)(mapc + (int64_t)s * mrow);
+                const int64_t Ps = (int64_t)(s - cs0) * W;   // this node's row of R.P
+                const int64_t ms = (int64_t)s * (mrow / (int64_t)sizeof(MapT));   // its map row
                 int dcnt = 0;
                 if (W == 1) {
                     constexpr int NPL = BK == 8 ? kMaxB : (BK == 2 ? 2 : 1);
@@ -500,9 +535,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         int e[4];
                         MapT phi[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr[n0 + t0 + u] : -1;
+                        for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? FG_AT(R.nbr, n0 + t0 + u, FG_N(int32_t, p.lay.rsize[RG_NBR])) : -1;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) phi[u] = e[u] >= 0 ? ms[e[u] & 0xffff] : DEL;
+                        for (int u = 0; u < 4; ++u)
+                            phi[u] = e[u] >= 0 ? FG_AT((const MapT *)mapc, ms + (e[u] & 0xffff), NMAPT) : DEL;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const bool sub = phi[u] != DEL;
@@ -514,31 +550,32 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                                 if (b < B && ((e[u] >> (16 + b)) & 1)) plr[b] |= pb;
                         }
                     }
-                    Ps[0] = pr;
+                    FG_AT(R.P, Ps, NP) = pr;
 #pragma unroll
                     for (int b = 0; b < NPL; ++b)
-                        if (b < B) R.PL[(int64_t)b * KM + (s - cs0)] = plr[b];
+                        if (b < B) FG_AT(R.PL, (int64_t)b * KM + (s - cs0), FG_N(Word, p.lay.rsize[RG_PL])) = plr[b];
                 } else {
 #pragma unroll
-                    for (int w = 0; w < W; ++w) Ps[w] = (Word)0;
+                    for (int w = 0; w < W; ++w) FG_AT(R.P, Ps + w, NP) = (Word)0;
                     for (int b = 0; b < B; ++b)
-                        for (int w = 0; w < W; ++w) R.PL[((int64_t)b * KM + (s - cs0)) * W + w] = (Word)0;
+                        for (int w = 0; w < W; ++w) FG_AT(R.PL, ((int64_t)b * KM + (s - cs0)) * W + w, FG_N(Word, p.lay.rsize[RG_PL])) = (Word)0;
                     for (int t = 0; t < deg; ++t) {
-                        const int e = R.nbr[n0 + t];
-                        const MapT phi = ms[e & 0xffff];
+                        const int e = FG_AT(R.nbr, n0 + t, FG_N(int32_t, p.lay.rsize[RG_NBR]));
+                        const MapT phi = FG_AT((const MapT *)mapc, ms + (e & 0xffff), NMAPT);
                         if (phi == DEL) { ++dcnt; continue; }
                         const int pw = (int)phi / WB;
                         const Word pb = (Word)1 << ((int)phi % WB);
-                        Ps[pw] |= pb;
+                        FG_AT(R.P, Ps + pw, NP) |= pb;
                         for (int b = 0; b < B; ++b)
-                            if ((e >> (16 + b)) & 1) R.PL[((int64_t)b * KM + (s - cs0)) * W + pw] |= pb;
+                            if ((e >> (16 + b)) & 1) FG_AT(R.PL, ((int64_t)b * KM + (s - cs0)) * W + pw, FG_N(Word, p.lay.rsize[RG_PL])) |= pb;
                     }
                 }
-                R.sbase[s - cs0] = pedc[s] + c.edel * dcnt;
-                const Word *im = imgw + (int64_t)(s - ioff) * W;
+                FG_AT(R.sbase, s - cs0, FG_N(int32_t, p.lay.rsize[RG_SBASE])) =
+                    FG_AT(pedc, s, NPED) + c.edel * dcnt;
+                const int64_t im = (int64_t)(s - ioff) * W;   // this node's Img row in imgw
                 int used = 0;
 #pragma unroll
-                for (int w = 0; w < W; ++w) used += popcw(im[w]);
+                for (int w = 0; w < W; ++w) used += popcw(FG_AT(imgw, im + w, NIMGW));
                 cnt = n2 - used + 1;   // free g2 vertices (R_V2) and the deletion
             }
             int incl = cnt;
@@ -555,37 +592,37 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // time and compacts the free ones with a ballot.
             if (W == 1 && !CL) {
                 if (act) {
-                    const Word *im = imgw + (int64_t)(s - ioff) * W;
                     int idx = base + kw + excl;
-                    Word x = ~im[0];
+                    Word x = ~FG_AT(imgw, (int64_t)(s - ioff) * W, NIMGW);
                     if (n2 < WB) x &= n2 > 0 ? (((Word)1 << n2) - (Word)1) : (Word)0;
                     while (x) {
                         const int t = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
                         x &= x - (Word)1;
-                        ck[idx++] = ((uint32_t)s << jbits) | (uint32_t)t;
+                        FG_AT(ck, idx, NCK) = ((uint32_t)s << jbits) | (uint32_t)t;
+                        ++idx;
                     }
-                    ck[idx] = ((uint32_t)s << jbits) | (uint32_t)n2;
+                    FG_AT(ck, idx, NCK) = ((uint32_t)s << jbits) | (uint32_t)n2;
                 }
             } else {
                 for (int t = 0; t < ng; ++t) {
                     const int st_ = g0 + t;
-                    const Word *im = imgw + (int64_t)(st_ - ioff) * W;
+                    const int64_t im = (int64_t)(st_ - ioff) * W;   // the node's Img row
                     const int o0 = base + kw + __shfl_sync(0xffffffffu, excl, t);
                     int pos = 0;
                     for (int j0 = 0; j0 < n2; j0 += 32) {
                         const int j = j0 + lane;
-                        const bool fr = j < n2 && !((im[j / WB] >> (j % WB)) & (Word)1);
+                        const bool fr = j < n2 && !((FG_AT(imgw, im + j / WB, NIMGW) >> (j % WB)) & (Word)1);
                         const unsigned bal = __ballot_sync(0xffffffffu, fr);
                         if (fr) {
                             const int idx = o0 + pos + __popc(bal & lanemask_lt());
-                            if (pk) ck[idx] = ((uint32_t)st_ << jbits) | (uint32_t)j;
-                            else ck64[idx] = ((uint64_t)st_ << kSelShift) | (uint64_t)j;
+                            if (pk) FG_AT(ck, idx, NCK) = ((uint32_t)st_ << jbits) | (uint32_t)j;
+                            else FG_AT(ck64, idx, NCK64) = ((uint64_t)st_ << kSelShift) | (uint64_t)j;
                         }
                         pos += __popc(bal);
                     }
                     if (lane == 0) {
-                        if (pk) ck[o0 + pos] = ((uint32_t)st_ << jbits) | (uint32_t)n2;
-                        else ck64[o0 + pos] = ((uint64_t)st_ << kSelShift) | (uint64_t)n2;
+                        if (pk) FG_AT(ck, o0 + pos, NCK) = ((uint32_t)st_ << jbits) | (uint32_t)n2;
+                        else FG_AT(ck64, o0 + pos, NCK64) = ((uint64_t)st_ << kSelShift) | (uint64_t)n2;
                     }
                 }
             }
@@ -597,14 +634,14 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // substituted neighbour in P as a deleted edge (with the dcnt deleted neighbours in
             // sbase, all deg edges to v_0..v_{i-1}), and the cost row holds c_vdel there.
             auto succ_ped = [&](int sc, int j) -> int {
-                const Word *im = imgw + (int64_t)(sc - ioff) * W;
-                const Word *Ps = R.P + (int64_t)(sc - cs0) * W;
+                const int64_t im = (int64_t)(sc - ioff) * W;   // the parent's Img row
+                const int64_t Ps = (int64_t)(sc - cs0) * W;    // and its row of R.P
                 int x = 0, y = 0, z = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const Word aw = R.a2t[w * N2S + j];
-                    const Word ai = aw & im[w];
-                    const Word pw = Ps[w];
+                    const Word aw = FG_AT(R.a2t, w * N2S + j, FG_N(Word, p.lay.rsize[RG_A2T]));
+                    const Word ai = aw & FG_AT(imgw, im + w, NIMGW);
+                    const Word pw = FG_AT(R.P, Ps + w, NP);
                     if (fold_ie) {
                         x += popcw((Word)(ai ^ pw));
                     } else {
@@ -614,12 +651,13 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     if (B > 0) {
                         Word ld = (Word)0;
                         for (int b = 0; b < B; ++b)
-                            ld |= R.PL[((int64_t)b * KM + (sc - cs0)) * W + w] ^
-                                  R.l2t[(b * W + w) * N2S + j];
+                            ld |= FG_AT(R.PL, ((int64_t)b * KM + (sc - cs0)) * W + w, FG_N(Word, p.lay.rsize[RG_PL])) ^
+                                  FG_AT(R.l2t, (b * W + w) * N2S + j, FG_N(Word, p.lay.rsize[RG_L2T]));
                         z += popcw((Word)(aw & pw & ld));
                     }
                 }
-                return R.sbase[sc - cs0] + crc[j] + c.eins * x + c.edel * y + c.esub * z;
+                return FG_AT(R.sbase, sc - cs0, FG_N(int32_t, p.lay.rsize[RG_SBASE])) + FG_AT(crc, j, N2S) +
+                       c.eins * x + c.edel * y + c.esub * z;
             };
             // U chunks of 32 successors per step, their id loads and PEDs independent
             constexpr int U = W <= 2 ? 2 : 1;
@@ -631,11 +669,11 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     const int k = kb + 32 * u + lane;
                     const int idx = base + kw + k;
                     if (pk) {
-                        idu[u] = k < gtot ? ck[idx] : (((uint32_t)g0 << jbits) | (uint32_t)n2);
+                        idu[u] = k < gtot ? FG_AT(ck, idx, NCK) : (((uint32_t)g0 << jbits) | (uint32_t)n2);
                         scu[u] = (int)(idu[u] >> jbits);
                         ju[u] = (int)(idu[u] & jmask);
                     } else {
-                        idu[u] = k < gtot ? (uint32_t)ck64[idx]
+                        idu[u] = k < gtot ? (uint32_t)FG_AT(ck64, idx, NCK64)
                                           : (((uint32_t)g0 << kSelShift) | (uint32_t)n2);
                         scu[u] = (int)(idu[u] >> kSelShift);
                         ju[u] = (int)(idu[u] & ((1u << kSelShift) - 1u));
@@ -648,8 +686,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 for (int u = 0; u < U; ++u) {
                     const int k = kb + 32 * u + lane;
                     if (k < gtot) {
-                        if (pk) ck[base + kw + k] = ((uint32_t)pu[u] << 16) | idu[u];
-                        else ck64[base + kw + k] = ((uint64_t)(uint32_t)pu[u] << 32) | idu[u];
+                        if (pk) FG_AT(ck, base + kw + k, NCK) = ((uint32_t)pu[u] << 16) | idu[u];
+                        else FG_AT(ck64, base + kw + k, NCK64) = ((uint64_t)(uint32_t)pu[u] << 32) | idu[u];
                         wmin = pu[u] < wmin ? pu[u] : wmin;
                     }
                 }
@@ -660,8 +698,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
         if (lane == 0) {
-            S.wmin[warp] = wmin;
-            S.wn[warp] = kw;
+            FG_AT(S.wmin, warp, NSW) = wmin;
+            FG_AT(S.wn, warp, NSW) = kw;
         }
         tm.sync();
         // S4 histogram of PED - pa over this warp's successors, pa = least PED of the level
@@ -669,7 +707,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         // the count of bucket b; lanes past the end count in the last bucket, which only
         // bounds the threshold search from above (the level total comes from the counts kw).
         int pa = INT_MAX;
-        for (int w = 0; w < NW; ++w) pa = min(pa, S.wmin[w]);
+        for (int w = 0; w < NW; ++w) pa = min(pa, FG_AT(S.wmin, w, NSW));
         {
             int hreg = 0;
             if (kw >= 1024 && kw <= 65000) {
@@ -746,17 +784,17 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     hreg += __popc(m);
                 }
             }
-            R.hist[lane * NW + warp] = hreg;
+            FG_AT(R.hist, lane * NW + warp, FG_N(int32_t, p.lay.rsize[RG_HIST])) = hreg;
         }
         tm.sync();
         PHASE_MARK(1);
         // (parent slot << kSelShift) | j of successor idx
         auto decode = [&](int idx) -> int {
             if (pk) {
-                const uint32_t id = ck[idx] & 0xffffu;
+                const uint32_t id = FG_AT(ck, idx, NCK) & 0xffffu;
                 return (int)((id >> jbits) << kSelShift) | (int)(id & jmask);
             } else {
-                return (int)(uint32_t)ck64[idx];
+                return (int)(uint32_t)FG_AT(ck64, idx, NCK64);
             }
         };
 
@@ -767,34 +805,38 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             // which the selection does not use at this level).
             for (int t = lane; t < s_hi - s_lo; t += 32) {
                 const int sl = s_lo + t;
-                const Word *im = imgc + (int64_t)sl * W;
+                const int64_t im = (int64_t)sl * W;   // the node's Img row
                 int nimg = 0, acc = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    nimg += popcw(im[w]);
-                    Word x = im[w];
+                    Word x = FG_AT(imgc, im + w, NIMG);
+                    nimg += popcw(x);
                     while (x) {
                         const int bt = (WB == 64) ? __ffsll((long long)x) - 1 : __ffs((int)x) - 1;
                         x &= x - (Word)1;
                         const int u = w * WB + bt;
 #pragma unroll
-                        for (int w2 = 0; w2 < W; ++w2) acc += popcw((Word)(R.a2t[w2 * N2S + u] & im[w2]));
+                        for (int w2 = 0; w2 < W; ++w2)
+                            acc += popcw((Word)(FG_AT(R.a2t, w2 * N2S + u, FG_N(Word, p.lay.rsize[RG_A2T])) &
+                                                FG_AT(imgc, im + w2, NIMG)));
                     }
                 }
-                R.kped[sl] = nimg;
-                R.klist[sl] = acc / 2;
+                FG_AT(R.kped, sl, FG_N(int32_t, p.lay.rsize[RG_KPED])) = nimg;
+                FG_AT(R.klist, sl, FG_N(int32_t, p.lay.rsize[RG_KLIST])) = acc / 2;
             }
             __syncwarp();
             auto leaf_total = [&](int k) -> long long {
                 const int idx = base + k;
                 const int v = decode(idx);
                 const int sc = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
-                const Word *im = imgc + (int64_t)sc * W;
-                int nimg = R.kped[sc], e2 = R.klist[sc];
+                const int64_t im = (int64_t)sc * W;   // the parent's Img row
+                int nimg = FG_AT(R.kped, sc, FG_N(int32_t, p.lay.rsize[RG_KPED])), e2 = FG_AT(R.klist, sc, FG_N(int32_t, p.lay.rsize[RG_KLIST]));
                 if (j < n2) {
                     ++nimg;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) e2 += popcw((Word)(R.a2t[w * N2S + j] & im[w]));
+                    for (int w = 0; w < W; ++w)
+                        e2 += popcw((Word)(FG_AT(R.a2t, w * N2S + j, FG_N(Word, p.lay.rsize[RG_A2T])) &
+                                           FG_AT(imgc, im + w, NIMG)));
                 }
                 return (long long)ped_at(idx) + (long long)c.vins * (n2 - nimg) +
                        (long long)c.eins * (m2.m - e2);
@@ -803,10 +845,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             for (int k = lane; k < kw; k += 32) tmin = min(tmin, leaf_total(k));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tmin = min(tmin, (long long)__shfl_xor_sync(0xffffffffu, tmin, o));
-            if (lane == 0) S.wbest[warp] = (unsigned long long)tmin;
+            if (lane == 0) FG_AT(S.wbest, warp, NSW) = (unsigned long long)tmin;
             tm.sync();
             long long best_total = LLONG_MAX;
-            for (int w = 0; w < NW; ++w) best_total = min(best_total, (long long)S.wbest[w]);
+            for (int w = 0; w < NW; ++w) best_total = min(best_total, (long long)FG_AT(S.wbest, w, NSW));
             tm.sync();
             unsigned long long key = ~0ull;
             for (int k = lane; k < kw; k += 32)
@@ -820,24 +862,24 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
                 key = y < key ? y : key;
             }
-            if (lane == 0) S.wbest[warp] = key;
+            if (lane == 0) FG_AT(S.wbest, warp, NSW) = key;
             tm.sync();
-            unsigned long long bk = S.wbest[0];
-            for (int w = 1; w < NW; ++w) bk = S.wbest[w] < bk ? S.wbest[w] : bk;
+            unsigned long long bk = FG_AT(S.wbest, 0, NSW);
+            for (int w = 1; w < NW; ++w) bk = FG_AT(S.wbest, w, NSW) < bk ? FG_AT(S.wbest, w, NSW) : bk;
             const int widx = (int)(bk & 0xffffffffull);
             const int wv = decode(widx);
             const int ws = wv >> kSelShift, wj = wv & ((1 << kSelShift) - 1);
             int all = 0;
-            for (int w = 0; w < NW; ++w) all += S.wn[w];
+            for (int w = 0; w < NW; ++w) all += FG_AT(S.wn, w, NSW);
             if (tid == 0) {
-                p.out_cost[pair] = (int32_t)best_total;
-                if (p.out_nevals) p.out_nevals[pair] = nevals + 2LL * all;
+                FG_AT(p.out_cost, pair, p.n_pairs) = (int32_t)best_total;
+                if (p.out_nevals) FG_AT(p.out_nevals, pair, p.n_pairs) = nevals + 2LL * all;
             }
-            const MapT *mb = (const MapT *)(mapc + (int64_t)ws * mrow);
-            int32_t *om = p.out_map + p.map_off[pair];
+            const int64_t mb = (int64_t)ws * (mrow / (int64_t)sizeof(MapT));   // the winner's map row
+            const int64_t om = FG_AT(p.map_off, pair, p.n_pairs);
             for (int k = tid; k < n1; k += T) {
-                const MapT v = (k == i) ? ((wj < n2) ? (MapT)wj : DEL) : mb[k];
-                om[k] = (v == DEL) ? -1 : (int32_t)v;
+                const MapT v = (k == i) ? ((wj < n2) ? (MapT)wj : DEL) : FG_AT((const MapT *)mapc, mb + k, NMAPT);
+                FG_AT(p.out_map, om + k, p.map_total) = (v == DEL) ? -1 : (int32_t)v;
             }
             tm.sync();
             return;
@@ -848,7 +890,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         // and the bucket-b successors of the warps before this one
         int tot = 0, mine = 0;
         for (int w = 0; w < NW; ++w) {
-            const int v = R.hist[lane * NW + w];
+            const int v = FG_AT(R.hist, lane * NW + w, FG_N(int32_t, p.lay.rsize[RG_HIST]));
             tot += v;
             mine += (w < warp) ? v : 0;
         }
@@ -860,7 +902,7 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
         const int bexcl = incl - tot;
         int total = 0;   // successors of the level (the last bucket may hold padding)
-        for (int w = 0; w < NW; ++w) total += S.wn[w];
+        for (int w = 0; w < NW; ++w) total += FG_AT(S.wn, w, NSW);
         const int newL = min(K, total);
         // the bucket where the cumulative count reaches newL
         const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;
@@ -875,14 +917,14 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
             const int eq_before = __shfl_sync(0xffffffffu, mine, thr);
             const int lt_before = warp_sum(lane < thr ? mine : 0);
             const int kbeg = lt_before + min(q, eq_before);
-            const int kcnt = compact_kept<Word>(R, base, kw, pa + thr, q, kbeg, eq_before, pk);
+            const int kcnt = compact_kept<Word>(p, R, base, kw, pa + thr, q, kbeg, eq_before, pk);
             __syncwarp();
             PHASE_MARK(8);
             int run = lane < thr ? mine : min(q, eq_before);   // kept of bucket `lane` before
             for (int xb = 0; xb < kcnt; xb += 32) {
                 const int x = kbeg + xb + lane;
                 const bool v = xb + lane < kcnt;
-                const int d = v ? R.kped[x] - pa : 0;
+                const int d = v ? FG_AT(R.kped, x, FG_N(int32_t, p.lay.rsize[RG_KPED])) - pa : 0;
                 const unsigned V = __ballot_sync(0xffffffffu, v);
                 unsigned bb[5];
 #pragma unroll
@@ -891,8 +933,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                                 __shfl_sync(0xffffffffu, run, d) +
                                 __popc(same_value_lanes(V, bb, d) & lanemask_lt());
                 if (v) {
-                    R.sel[pos] = decode(R.klist[x]);
-                    R.selped[pos] = d + pa;
+                    FG_AT(R.sel, pos, FG_N(int32_t, p.lay.rsize[RG_SEL])) = decode(FG_AT(R.klist, x, FG_N(int32_t, p.lay.rsize[RG_KLIST])));
+                    FG_AT(R.selped, pos, FG_N(int32_t, p.lay.rsize[RG_SELPED])) = d + pa;
                 }
                 unsigned m = V;
 #pragma unroll
@@ -904,10 +946,10 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 #ifdef FASTGED_PHASE_TIMERS
             if (threadIdx.x == 0) ph[7] += 1;   // levels that took the exact selection
 #endif
-            select_exact<MapT, Word, CL, TS>(R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
+            select_exact<MapT, Word, CL, TS>(p, R.cand, R.klist, R.kped, R.sel, R.selped, S, L,
                                              stride, newL, pa + hwin - 1, pk);
             tm.sync();
-            for (int r = tid; r < newL; r += T) R.sel[r] = decode(R.sel[r]);
+            for (int r = tid; r < newL; r += T) FG_AT(R.sel, r, FG_N(int32_t, p.lay.rsize[RG_SEL])) = decode(FG_AT(R.sel, r, FG_N(int32_t, p.lay.rsize[RG_SEL])));
         }
         tm.sync();
         PHASE_MARK(6);
@@ -915,21 +957,22 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         // ---- kept children, in key order (slot = rank) -----------------------------
         {
             const int nvec = (int)((i * (int)sizeof(MapT) + 15) >> 4);
+            const int64_t m16 = mrow >> 4, mt = mrow / (int64_t)sizeof(MapT);   // a map row in
+                                                                                // 16 B / MapT units
             if (mrow <= 128) {
                 for (int r = tid; r < newL; r += T) {
-                    const int v = R.sel[r];
+                    const int v = FG_AT(R.sel, r, FG_N(int32_t, p.lay.rsize[RG_SEL]));
                     const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
-                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
-                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
-                    for (int t = 0; t < nvec; ++t) dst[t] = src[t];
-                    ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
+                    for (int t = 0; t < nvec; ++t)
+                        FG_AT((uint4 *)mapn, r * m16 + t, NMAP16) = FG_AT((const uint4 *)mapc, s * m16 + t, NMAP16);
+                    FG_AT((MapT *)mapn, r * mt + i, NMAPT) = (j < n2) ? (MapT)j : DEL;
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        Word x = imgc[(int64_t)s * W + w];
+                        Word x = FG_AT(imgc, (int64_t)s * W + w, NIMG);
                         if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
-                        imgn[(int64_t)r * W + w] = x;
+                        FG_AT(imgn, (int64_t)r * W + w, NIMG) = x;
                     }
-                    pedn[r] = R.selped[r];
+                    FG_AT(pedn, r, NPED) = FG_AT(R.selped, r, FG_N(int32_t, p.lay.rsize[RG_SELPED]));
                 }
             } else if (!CL) {
                 // long maps, one-CTA team: every thread takes (child, 16-byte vector) items
@@ -940,51 +983,49 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                 const int items = newL * per;
                 for (int t = tid; t < items; t += T) {
                     const int r = t / per, v = t - r * per;
-                    const int sv = R.sel[r];
+                    const int sv = FG_AT(R.sel, r, FG_N(int32_t, p.lay.rsize[RG_SEL]));
                     const int s = sv >> kSelShift, j = sv & ((1 << kSelShift) - 1);
                     const MapT val = (j < n2) ? (MapT)j : DEL;
-                    uint8_t *dst = mapn + (int64_t)r * mrow;
                     if (v < nvec) {
-                        uint4 x = ((const uint4 *)(mapc + (int64_t)s * mrow))[v];
+                        uint4 x = FG_AT((const uint4 *)mapc, s * m16 + v, NMAP16);
                         if (v == nvec - 1 && nb < 16 * nvec)
                             ((MapT *)&x)[(nb - 16 * v) / (int)sizeof(MapT)] = val;
-                        ((uint4 *)dst)[v] = x;
+                        FG_AT((uint4 *)mapn, r * m16 + v, NMAP16) = x;
                     } else {
-                        if (nb == 16 * nvec) ((MapT *)dst)[i] = val;
+                        if (nb == 16 * nvec) FG_AT((MapT *)mapn, r * mt + i, NMAPT) = val;
                         for (int w = 0; w < W; ++w) {
-                            Word x = imgc[(int64_t)s * W + w];
+                            Word x = FG_AT(imgc, (int64_t)s * W + w, NIMG);
                             if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
-                            imgn[(int64_t)r * W + w] = x;
+                            FG_AT(imgn, (int64_t)r * W + w, NIMG) = x;
                         }
-                        pedn[r] = R.selped[r];
+                        FG_AT(pedn, r, NPED) = FG_AT(R.selped, r, FG_N(int32_t, p.lay.rsize[RG_SELPED]));
                     }
                 }
             } else {
                 // cluster teams: a warp per child
                 for (int r = warp; r < newL; r += NW) {
-                    const int v = R.sel[r];
+                    const int v = FG_AT(R.sel, r, FG_N(int32_t, p.lay.rsize[RG_SEL]));
                     const int s = v >> kSelShift, j = v & ((1 << kSelShift) - 1);
-                    const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
-                    uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
-                    for (int t = lane; t < nvec; t += 32) dst[t] = src[t];
+                    for (int t = lane; t < nvec; t += 32)
+                        FG_AT((uint4 *)mapn, r * m16 + t, NMAP16) = FG_AT((const uint4 *)mapc, s * m16 + t, NMAP16);
                     for (int w = lane; w < W; w += 32) {
-                        Word x = imgc[(int64_t)s * W + w];
+                        Word x = FG_AT(imgc, (int64_t)s * W + w, NIMG);
                         if (j < n2 && j / WB == w) x |= (Word)1 << (j % WB);
-                        imgn[(int64_t)r * W + w] = x;
+                        FG_AT(imgn, (int64_t)r * W + w, NIMG) = x;
                     }
                     __syncwarp();
                     if (lane == 0) {
-                        ((MapT *)dst)[i] = (j < n2) ? (MapT)j : DEL;
-                        pedn[r] = R.selped[r];
+                        FG_AT((MapT *)mapn, r * mt + i, NMAPT) = (j < n2) ? (MapT)j : DEL;
+                        FG_AT(pedn, r, NPED) = FG_AT(R.selped, r, FG_N(int32_t, p.lay.rsize[RG_SELPED]));
                     }
                 }
             }
         }
         // S1 cost row of the next level (each CTA keeps its own copy)
         if (i + 1 < n1) {
-            const int a1n = p.vlab[m1.lab_off + i + 1];
+            const int a1n = FG_AT(p.vlab, m1.lab_off + i + 1, p.n_vlab);
             for (int u = ltid; u <= n2; u += LT)
-                crn[u] = u < n2 ? ((R.alpha2[u] != a1n) ? c.vsub : 0) : c.vdel;
+                FG_AT(crn, u, N2S) = u < n2 ? ((FG_AT(R.alpha2, u, FG_N(int32_t, p.lay.rsize[RG_ALPHA2])) != a1n) ? c.vsub : 0) : c.vdel;
         }
         tm.sync();
         PHASE_MARK(3);
@@ -999,40 +1040,42 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     {
         unsigned long long best = ~0ull;
         for (int s = warp; s < L; s += NW) {
-            const Word *im = imgc + (int64_t)s * W;
+            const int64_t im = (int64_t)s * W;   // the leaf's Img row
             int acc = 0;
             for (int u = lane; u < n2; u += 32) {
-                if ((im[u / WB] >> (u % WB)) & (Word)1) {
+                if ((FG_AT(imgc, im + u / WB, NIMG) >> (u % WB)) & (Word)1) {
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc += popcw((Word)(R.a2t[w * N2S + u] & im[w]));
+                    for (int w = 0; w < W; ++w)
+                        acc += popcw((Word)(FG_AT(R.a2t, w * N2S + u, FG_N(Word, p.lay.rsize[RG_A2T])) &
+                                            FG_AT(imgc, im + w, NIMG)));
                 }
             }
             int nimg = 0;
-            for (int w = lane; w < W; w += 32) nimg += popcw(im[w]);
+            for (int w = lane; w < W; w += 32) nimg += popcw(FG_AT(imgc, im + w, NIMG));
             acc = warp_sum(acc);
             nimg = warp_sum(nimg);
             // g2 edges with both ends used were counted twice in acc
-            const long long total = (long long)pedc[s] + (long long)c.vins * (n2 - nimg) +
+            const long long total = (long long)FG_AT(pedc, s, NPED) + (long long)c.vins * (n2 - nimg) +
                                     (long long)c.eins * (m2.m - acc / 2);
             const unsigned long long key = ((unsigned long long)total << 32) | (unsigned)s;
             best = key < best ? key : best;
         }
-        if (lane == 0) S.wbest[warp] = best;
+        if (lane == 0) FG_AT(S.wbest, warp, NSW) = best;
         tm.sync();
         if (tid == 0) {
-            unsigned long long b = S.wbest[0];
-            for (int w = 1; w < NW; ++w) b = S.wbest[w] < b ? S.wbest[w] : b;
-            S.wbest[0] = b;
-            p.out_cost[pair] = (int32_t)(b >> 32);
-            if (p.out_nevals) p.out_nevals[pair] = nevals + L;
+            unsigned long long b = FG_AT(S.wbest, 0, NSW);
+            for (int w = 1; w < NW; ++w) b = FG_AT(S.wbest, w, NSW) < b ? FG_AT(S.wbest, w, NSW) : b;
+            FG_AT(S.wbest, 0, NSW) = b;
+            FG_AT(p.out_cost, pair, p.n_pairs) = (int32_t)(b >> 32);
+            if (p.out_nevals) FG_AT(p.out_nevals, pair, p.n_pairs) = nevals + L;
         }
         tm.sync();
-        const int bs = (int)(S.wbest[0] & 0xffffffffull);
-        const MapT *mb = (const MapT *)(mapc + (int64_t)bs * mrow);
-        int32_t *om = p.out_map + p.map_off[pair];
+        const int bs = (int)(FG_AT(S.wbest, 0, NSW) & 0xffffffffull);
+        const int64_t mb = (int64_t)bs * (mrow / (int64_t)sizeof(MapT));   // the winner's map row
+        const int64_t om = FG_AT(p.map_off, pair, p.n_pairs);
         for (int k = tid; k < n1; k += T) {
-            const MapT v = mb[k];
-            om[k] = (v == DEL) ? -1 : (int32_t)v;
+            const MapT v = FG_AT((const MapT *)mapc, mb + k, NMAPT);
+            FG_AT(p.out_map, om + k, p.map_total) = (v == DEL) ? -1 : (int32_t)v;
         }
         tm.sync();
         PHASE_MARK(4);
@@ -1041,6 +1084,15 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
     if (tid == 0 && p.phase_cycles)
         for (int k = 0; k < 16; ++k) atomicAdd(&p.phase_cycles[k], (unsigned long long)ph[k]);
 #endif
+#undef NIMG
+#undef NPED
+#undef NSW
+#undef NP
+#undef NMAPT
+#undef NMAP16
+#undef NCK
+#undef NCK64
+#undef NIMGW
 }
 
 // Region pointers of a team from a region -> base address function.
@@ -1091,7 +1143,7 @@ __global__ void __launch_bounds__(512, 2) kbest_kernel(const KParams p)
         const int qi = S.pair;
         __syncthreads();
         if (qi >= p.n_order) break;
-        solve_pair<W, MapT, Word, BK, false, TeamShared>(p, R, S, p.order[qi]);
+        solve_pair<W, MapT, Word, BK, false, TeamShared>(p, R, S, FG_AT(p.order, qi, p.n_order));
     }
 }
 
@@ -1119,7 +1171,7 @@ __global__ void __launch_bounds__(512, (W <= 2) ? 2 : 1) kbest_cluster_kernel(co
         const int qi = *(volatile int *)&S.pair;
         cluster_barrier();
         if (qi >= p.n_order) break;
-        solve_pair<W, MapT, Word, BK, true, TeamSharedCl>(p, R, S, p.order[qi]);
+        solve_pair<W, MapT, Word, BK, true, TeamSharedCl>(p, R, S, FG_AT(p.order, qi, p.n_order));
     }
 }
 

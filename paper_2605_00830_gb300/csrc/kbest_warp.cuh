@@ -136,7 +136,8 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     const int c_eins = p.cost.eins, c_edel = p.cost.edel, c_esub = p.cost.esub;
     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
     const uint8_t *mapc = R.mapc(wl);
-    const TgtRec<Word, NPL> *tgt = R.tgt(wl);
+    using TRec = TgtRec<Word, NPL>;
+    const TRec *tgt = R.tgt(wl);
     // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 15 steps into
     // acc[m] = buckets (m, m + 4) and acc[4 + m] = (8 + m, 12 + m), 16 bits each
     uint32_t clo = 0, chi = 0, acc[8];
@@ -162,14 +163,17 @@ __device__ __forceinline__ int eval_level(const KParams &p,
 #pragma unroll
         for (int b = 0; b < (NPL > 0 ? NPL : 1); ++b) PL[b] = (Word)0;
         int dcnt = 0;
-        const uint8_t *ms = mapc + (int64_t)(act ? s : 0) * mrow;
+        const int64_t ms = (int64_t)(act ? s : 0) * mrow;   // the node's map row
         for (int t0 = 0; t0 < deg; t0 += 4) {
             int e[4];
             uint8_t phi[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = t0 + u < deg ? R.nbr(wl)[n0 + t0 + u] : -1;
+            for (int u = 0; u < 4; ++u)
+                e[u] = t0 + u < deg ? FG_AT(R.nbr(wl), n0 + t0 + u, FG_N(int32_t, wl.size[WR_NBR])) : -1;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) phi[u] = (e[u] >= 0 && act) ? ms[e[u] & 0xffff] : (uint8_t)0xff;
+            for (int u = 0; u < 4; ++u)
+                phi[u] = (e[u] >= 0 && act) ? FG_AT(mapc, ms + (e[u] & 0xffff), wl.size[WR_MAP0])
+                                            : (uint8_t)0xff;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const bool sub = phi[u] != 0xff;
@@ -181,8 +185,9 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                     if (b < B && ((e[u] >> (16 + b)) & 1)) PL[b] |= pb;
             }
         }
-        const Word im = act ? R.imgc(wl)[s] : ~(Word)0;
-        const int base = act ? R.pedc(wl)[s] + c_edel * dcnt - A : 0;
+        const Word im = act ? FG_AT(R.imgc(wl), s, FG_N(Word, wl.size[WR_IMG0])) : ~(Word)0;
+        const int base = act ? FG_AT(R.pedc(wl), s, FG_N(int32_t, wl.size[WR_PED0])) + c_edel * dcnt - A
+                             : 0;
         const int cnt = act ? n2 - popcw((Word)(im & nmask)) + 1 : 0;   // free vertices + deletion
         int incl = cnt;
 #pragma unroll
@@ -191,7 +196,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             if (lane >= o) incl += v;
         }
         const int off = tot + incl - cnt;
-        if (act) R.nodeoff(wl)[s] = (uint16_t)off;
+        if (act) FG_AT(R.nodeoff(wl), s, FG_N(uint16_t, wl.size[WR_NODEOFF])) = (uint16_t)off;
         const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
 #ifdef FASTGED_PHASE_TIMERS
         if (steps) *steps += maxc;   // profiling builds: loop steps of the level
@@ -203,7 +208,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
         // overflow inside one
         auto score = [&](int j) -> int {
-            const TgtRec<Word, NPL> r = tgt[j];
+            const TgtRec<Word, NPL> r = FG_AT(tgt, j, FG_N(TRec, wl.size[WR_TGT]));
             const Word ai = r.a2 & im;
             int d = base + r.crow;
             if (FOLD) {
@@ -237,12 +242,14 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                 x &= x - (Word)1;
                 const bool va = t < cnt, vb = t + 1 < cnt;
                 const int da = score(ja), db = score(jb);
+#define NE FG_N(uint16_t, wl.size[WR_ENT])
                 if (EXACT) {
-                    ent[va ? off + t : dummy] = (uint16_t)da;
-                    ent[vb ? off + t + 1 : dummy] = (uint16_t)db;
+                    FG_AT(ent, va ? off + t : dummy, NE) = (uint16_t)da;
+                    FG_AT(ent, vb ? off + t + 1 : dummy, NE) = (uint16_t)db;
                 } else {
-                    ent[va ? off + t : dummy] = (uint16_t)((min(da, 255) << 8) | ja);
-                    ent[vb ? off + t + 1 : dummy] = (uint16_t)((min(db, 255) << 8) | jb);
+                    FG_AT(ent, va ? off + t : dummy, NE) = (uint16_t)((min(da, 255) << 8) | ja);
+                    FG_AT(ent, vb ? off + t + 1 : dummy, NE) = (uint16_t)((min(db, 255) << 8) | jb);
+#undef NE
                     count(da, va);
                     count(db, vb);
                 }
@@ -251,7 +258,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         }
         tot += __shfl_sync(FULL, incl, 31);
     }
-    if (lane == 0) R.nodeoff(wl)[L] = (uint16_t)tot;
+    if (lane == 0) FG_AT(R.nodeoff(wl), L, FG_N(uint16_t, wl.size[WR_NODEOFF])) = (uint16_t)tot;
     if (!EXACT) {
         // warp totals (at most 128 x 65 successors: 16-bit fields cannot overflow), then lane
         // b takes bucket b
@@ -273,12 +280,12 @@ __device__ __forceinline__ int eval_level(const KParams &p,
 
 // Slot of the node that owns entry k (nodeoff is strictly increasing: every node has at
 // least its deletion successor).
-__device__ __forceinline__ int node_of(const uint16_t *nodeoff, int L, int k)
+__device__ __forceinline__ int node_of(const KParams &p, const uint16_t *nodeoff, int L, int k)
 {
     int lo = 0, hi = L;
     while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if ((int)nodeoff[mid] <= k) lo = mid;
+        const int mid = (lo + hi) >> 1;   // 0 < mid < L: within the node offsets
+        if ((int)FG_AT(nodeoff, mid, FG_N(uint16_t, p.wl.size[WR_NODEOFF])) <= k) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -299,10 +306,13 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     R.cur = 0;
     R.mb = wl.gmap ? gw : g_warp_smem + wb;
 
-    const int g1 = p.pairs[2 * pair], g2 = p.pairs[2 * pair + 1];
-    const GraphMeta m1 = p.gmeta[g1], m2 = p.gmeta[g2];
+// elements of warp region r viewed as type T (bounds-checked builds check indexes against it)
+#define WN(T, r) FG_N(T, wl.size[r])
+    const int g1 = FG_AT(p.pairs, 2 * pair, 2 * p.n_pairs);
+    const int g2 = FG_AT(p.pairs, 2 * pair + 1, 2 * p.n_pairs);
+    const GraphMeta m1 = FG_AT(p.gmeta, g1, p.n_graphs), m2 = FG_AT(p.gmeta, g2, p.n_graphs);
     const int n1 = m1.n, n2 = m2.n, W1 = m1.W;
-    const int K = p.kpp ? p.kpp[pair] : p.K;
+    const int K = p.kpp ? FG_AT(p.kpp, pair, p.n_pairs) : p.K;
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
     const int mrow = wl.mrow;
     const CostModel c = p.cost;
@@ -327,26 +337,32 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
         const int W2 = m2.W;
         for (int u = lane; u <= n2; u += 32) {
             Rec r;
-            r.a2 = u < n2 ? (Word)adj2[(int64_t)u * W2] : (Word)0;
+            r.a2 = u < n2 ? (Word)FG_AT(adj2, (int64_t)u * W2, p.adj_words - m2.adj_off) : (Word)0;
 #pragma unroll
             for (int b = 0; b < NPL; ++b)
-                rec_set_plane(r, b, (u < n2 && b < B) ? (Word)pl2[((int64_t)b * n2 + u) * W2] : (Word)0);
+                rec_set_plane(r, b, (u < n2 && b < B)
+                                        ? (Word)FG_AT(pl2, ((int64_t)b * n2 + u) * W2,
+                                                      p.plane_words - m2.plane_off)
+                                        : (Word)0);
             r.crow = 0;
-            R.tgt(wl)[u] = r;
-            if (u < n2) R.lab2(wl)[u] = p.vlab[m2.lab_off + u];
+            FG_AT(R.tgt(wl), u, WN(Rec, WR_TGT)) = r;
+            if (u < n2)
+                FG_AT(R.lab2(wl), u, WN(int32_t, WR_LAB2)) =
+                    FG_AT(p.vlab, m2.lab_off + u, p.n_vlab);
         }
         // prior neighbours v_k (k < v) of every g1 vertex v, with their edge labels
         for (int v = lane; v < n1; v += 32) {
-            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
+            const int64_t row = m1.adj_off + (int64_t)v * W1;
             int d = 0;
-            for (int w = 0; w < W1; ++w) d += __popcll(row[w] & low_mask(v, w));
-            R.noff(wl)[v + 1] = d;
+            for (int w = 0; w < W1; ++w)
+                d += __popcll(FG_AT(p.adj, row + w, p.adj_words) & low_mask(v, w));
+            FG_AT(R.noff(wl), v + 1, WN(int32_t, WR_NOFF)) = d;
         }
         __syncwarp();
         int carry = 0;
         for (int v0 = 0; v0 < n1; v0 += 32) {
             const int v = v0 + lane;
-            const int d = v < n1 ? R.noff(wl)[v + 1] : 0;
+            const int d = v < n1 ? FG_AT(R.noff(wl), v + 1, WN(int32_t, WR_NOFF)) : 0;
             int incl = d;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -354,32 +370,34 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                 if (lane >= o) incl += y;
             }
             __syncwarp();
-            if (v < n1) R.noff(wl)[v + 1] = carry + incl;
+            if (v < n1) FG_AT(R.noff(wl), v + 1, WN(int32_t, WR_NOFF)) = carry + incl;
             carry += __shfl_sync(FULL, incl, 31);
         }
-        if (lane == 0) R.noff(wl)[0] = 0;
+        if (lane == 0) FG_AT(R.noff(wl), 0, WN(int32_t, WR_NOFF)) = 0;
         __syncwarp();
         const int64_t pstep = (int64_t)n1 * W1;
         for (int v = lane; v < n1; v += 32) {
-            const uint64_t *row = p.adj + m1.adj_off + (int64_t)v * W1;
-            const uint64_t *pl = p.planes + m1.plane_off + (int64_t)v * W1;
-            int o = R.noff(wl)[v];
+            const int64_t row = m1.adj_off + (int64_t)v * W1;
+            const int64_t pl = m1.plane_off + (int64_t)v * W1;
+            int o = FG_AT(R.noff(wl), v, WN(int32_t, WR_NOFF));
             for (int w = 0; w < W1; ++w) {
-                uint64_t bits = row[w] & low_mask(v, w);
+                uint64_t bits = FG_AT(p.adj, row + w, p.adj_words) & low_mask(v, w);
                 while (bits) {
                     const int t = __ffsll((long long)bits) - 1;
                     bits &= bits - 1ull;
                     int lab = 0;
-                    for (int b = 0; b < B; ++b) lab |= (int)((pl[b * pstep + w] >> t) & 1ull) << b;
-                    R.nbr(wl)[o++] = (w * 64 + t) | (lab << 16);
+                    for (int b = 0; b < B; ++b)
+                        lab |= (int)((FG_AT(p.planes, pl + b * pstep + w, p.plane_words) >> t) & 1ull) << b;
+                    FG_AT(R.nbr(wl), o, WN(int32_t, WR_NBR)) = (w * 64 + t) | (lab << 16);
+                    ++o;
                 }
             }
         }
         // root: empty map, Img empty, PED 0
         if (lane == 0) {
-            R.imgc(wl)[0] = (Word)0;
-            R.pedc(wl)[0] = 0;
-            R.e2c(wl)[0] = 0;
+            FG_AT(R.imgc(wl), 0, WN(Word, WR_IMG0)) = (Word)0;
+            FG_AT(R.pedc(wl), 0, WN(int32_t, WR_PED0)) = 0;
+            FG_AT(R.e2c(wl), 0, WN(uint16_t, WR_E20)) = 0;
         }
         __syncwarp();
     }
@@ -390,14 +408,16 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     for (int i = 0; i < n1; ++i) {
         // S1: this level's vertex-cost row C[i][u] (the deletion column holds c_vdel)
         {
-            const int a1 = p.vlab[m1.lab_off + i];
+            const int a1 = FG_AT(p.vlab, m1.lab_off + i, p.n_vlab);
             for (int u = lane; u <= n2; u += 32)
-                R.tgt(wl)[u].crow = u < n2 ? ((R.lab2(wl)[u] != a1) ? c.vsub : 0) : c.vdel;
+                FG_AT(R.tgt(wl), u, WN(Rec, WR_TGT)).crow =
+                    u < n2 ? ((FG_AT(R.lab2(wl), u, WN(int32_t, WR_LAB2)) != a1) ? c.vsub : 0) : c.vdel;
         }
         __syncwarp();
         WPHASE(7);
-        const int n0 = R.noff(wl)[i], deg = R.noff(wl)[i + 1] - n0;
-        const int A = R.pedc(wl)[0];   // least PED of the kept list: a lower bound of every child
+        const int n0 = FG_AT(R.noff(wl), i, WN(int32_t, WR_NOFF));
+        const int deg = FG_AT(R.noff(wl), i + 1, WN(int32_t, WR_NOFF)) - n0;
+        const int A = FG_AT(R.pedc(wl), 0, WN(int32_t, WR_PED0));   // least PED of the kept list: a lower bound of every child
         int hist = 0;
 #ifdef FASTGED_PHASE_TIMERS
         const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist,
@@ -432,7 +452,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = kb + 32 * u + lane;
-                    e[u] = k < tot ? (int)R.ent(wl)[k] : 0xffff;
+                    e[u] = k < tot ? (int)FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)) : 0xffff;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) le[u] = __ballot_sync(FULL, e[u] < lim);
@@ -457,7 +477,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (keep[u])
-                        R.klist(wl)[keep_before + __popc(kbm[u] & lt)] =
+                        FG_AT(R.klist(wl), keep_before + __popc(kbm[u] & lt), WN(uint32_t, WR_KLIST)) =
                             ((uint32_t)(e[u] >> 8) << 16) | (uint32_t)(kb + 32 * u + lane);
                     keep_before += __popc(kbm[u]);
                 }
@@ -475,7 +495,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             for (int ch = 0; ch < kWarpChunks; ++ch) {
                 const int x = 32 * ch + lane;
                 vk[ch] = x < newL;
-                kv[ch] = vk[ch] ? R.klist(wl)[x] : 0u;
+                kv[ch] = vk[ch] ? FG_AT(R.klist(wl), x, WN(uint32_t, WR_KLIST)) : 0u;
                 dk[ch] = (int)(kv[ch] >> 16);
             }
 #pragma unroll
@@ -498,9 +518,10 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             for (int ch = 0; ch < kWarpChunks; ++ch) {
                 if (vk[ch]) {
                     const int k = (int)(kv[ch] & 0xffffu);
-                    const int s = node_of(R.nodeoff(wl), L, k);
-                    R.sel(wl)[pos[ch]] = (s << 8) | (int)(R.ent(wl)[k] & 0xffu);
-                    R.selped(wl)[pos[ch]] = A + dk[ch];
+                    const int s = node_of(p, R.nodeoff(wl), L, k);
+                    FG_AT(R.sel(wl), pos[ch], WN(int32_t, WR_SEL)) =
+                        (s << 8) | (int)(FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)) & 0xffu);
+                    FG_AT(R.selped(wl), pos[ch], WN(int32_t, WR_SELPED)) = A + dk[ch];
                 }
             }
             WPHASE(4);
@@ -512,11 +533,13 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             eval_level<Word, BK, FOLD, true>(p, R, L, n0, deg, n2, mrow, A, H, dummy);
             auto count_le = [&](int t) -> int {
                 int cnt = 0;
-                for (int k = lane; k < tot; k += 32) cnt += ((int)R.ent(wl)[k] <= t);
+                for (int k = lane; k < tot; k += 32)
+                    cnt += ((int)FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)) <= t);
                 return warp_sum(cnt);
             };
             int lo = H - 1, hi = 0;
-            for (int k = lane; k < tot; k += 32) hi = max(hi, (int)R.ent(wl)[k]);
+            for (int k = lane; k < tot; k += 32)
+                hi = max(hi, (int)FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)));
             hi = (int)__reduce_max_sync(FULL, (unsigned)hi);
             if (lo > hi) lo = hi;
             while (lo < hi) {   // count(<= lo - 1) < newL <= count(<= hi)
@@ -529,40 +552,42 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             int keep_before = 0, eq_before = 0;
             for (int kb = 0; kb < tot; kb += 32) {
                 const int k = kb + lane;
-                const int d = k < tot ? (int)R.ent(wl)[k] : 0x10000;
+                const int d = k < tot ? (int)FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)) : 0x10000;
                 const bool is_eq = d == T;
                 const unsigned eqb = __ballot_sync(FULL, is_eq);
                 const bool keep = (d < T) || (is_eq && eq_before + __popc(eqb & lanemask_lt()) < q);
                 const unsigned kbm = __ballot_sync(FULL, keep);
                 if (keep)
-                    R.klist(wl)[keep_before + __popc(kbm & lanemask_lt())] = ((uint32_t)d << 16) | (uint32_t)k;
+                    FG_AT(R.klist(wl), keep_before + __popc(kbm & lanemask_lt()), WN(uint32_t, WR_KLIST)) =
+                        ((uint32_t)d << 16) | (uint32_t)k;
                 keep_before += __popc(kbm);
                 eq_before += __popc(eqb);
             }
             __syncwarp();
             // rank of every kept key (keys are distinct: the entry index is in the low half)
             for (int x = lane; x < newL; x += 32) {
-                const uint32_t kx = R.klist(wl)[x];
+                const uint32_t kx = FG_AT(R.klist(wl), x, WN(uint32_t, WR_KLIST));
                 int rank = 0;
-                for (int y = 0; y < newL; ++y) rank += R.klist(wl)[y] < kx;
-                R.selped(wl)[rank] = (int)kx;
+                for (int y = 0; y < newL; ++y) rank += FG_AT(R.klist(wl), y, WN(uint32_t, WR_KLIST)) < kx;
+                FG_AT(R.selped(wl), rank, WN(int32_t, WR_SELPED)) = (int)kx;
             }
             __syncwarp();
             for (int r = lane; r < newL; r += 32) {
-                const uint32_t kx = (uint32_t)R.selped(wl)[r];
+                const uint32_t kx = (uint32_t)FG_AT(R.selped(wl), r, WN(int32_t, WR_SELPED));
                 const int d = (int)(kx >> 16), k = (int)(kx & 0xffffu);
-                const int s = node_of(R.nodeoff(wl), L, k);
-                const int t = k - (int)R.nodeoff(wl)[s];
-                const int cnt = (int)R.nodeoff(wl)[s + 1] - (int)R.nodeoff(wl)[s];
+                const int s = node_of(p, R.nodeoff(wl), L, k);
+                const int no = (int)FG_AT(R.nodeoff(wl), s, WN(uint16_t, WR_NODEOFF));
+                const int t = k - no;
+                const int cnt = (int)FG_AT(R.nodeoff(wl), s + 1, WN(uint16_t, WR_NODEOFF)) - no;
                 int j = n2;
                 if (t < cnt - 1) {   // the t-th free target vertex of node s
                     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
-                    Word x = ~R.imgc(wl)[s] & nmask;
+                    Word x = ~FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0)) & nmask;
                     for (int z = 0; z < t; ++z) x &= x - (Word)1;
                     j = ffsw(x);
                 }
-                R.sel(wl)[r] = (s << 8) | j;
-                R.selped(wl)[r] = A + d;
+                FG_AT(R.sel(wl), r, WN(int32_t, WR_SEL)) = (s << 8) | j;
+                FG_AT(R.selped(wl), r, WN(int32_t, WR_SELPED)) = A + d;
             }
             WPHASE(5);
         }
@@ -574,22 +599,23 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             const uint8_t *__restrict__ mapc = R.mapc(wl);
             uint8_t *__restrict__ mapn = R.mapn(wl);
             for (int r = lane; r < newL; r += 32) {
-                const int v = R.sel(wl)[r];
+                const int v = FG_AT(R.sel(wl), r, WN(int32_t, WR_SEL));
                 const int s = v >> 8, j = v & 0xff;
-                const uint4 *src = (const uint4 *)(mapc + (int64_t)s * mrow);
-                uint4 *dst = (uint4 *)(mapn + (int64_t)r * mrow);
-                for (int t = 0; t < nvec; ++t) dst[t] = src[t];
-                mapn[(int64_t)r * mrow + i] = j < n2 ? (uint8_t)j : DEL;
-                const Word im = R.imgc(wl)[s];
-                int e2 = R.e2c(wl)[s];
+                const int64_t src = (int64_t)s * (mrow >> 4), dst = (int64_t)r * (mrow >> 4);
+                for (int t = 0; t < nvec; ++t)
+                    FG_AT((uint4 *)mapn, dst + t, FG_N(uint4, wl.size[WR_MAP0])) =
+                        FG_AT((const uint4 *)mapc, src + t, FG_N(uint4, wl.size[WR_MAP0]));
+                FG_AT(mapn, (int64_t)r * mrow + i, wl.size[WR_MAP0]) = j < n2 ? (uint8_t)j : DEL;
+                const Word im = FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0));
+                int e2 = FG_AT(R.e2c(wl), s, WN(uint16_t, WR_E20));
                 Word imn = im;
                 if (j < n2) {
-                    e2 += popcw((Word)(R.tgt(wl)[j].a2 & im));
+                    e2 += popcw((Word)(FG_AT(R.tgt(wl), j, WN(Rec, WR_TGT)).a2 & im));
                     imn |= (Word)1 << j;
                 }
-                R.imgn(wl)[r] = imn;
-                R.e2n(wl)[r] = (uint16_t)e2;
-                R.pedn(wl)[r] = R.selped(wl)[r];
+                FG_AT(R.imgn(wl), r, WN(Word, WR_IMG0)) = imn;
+                FG_AT(R.e2n(wl), r, WN(uint16_t, WR_E20)) = (uint16_t)e2;
+                FG_AT(R.pedn(wl), r, WN(int32_t, WR_PED0)) = FG_AT(R.selped(wl), r, WN(int32_t, WR_SELPED));
             }
         }
         __syncwarp();
@@ -602,9 +628,10 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     // (total, slot)
     unsigned long long best = ~0ull;
     for (int s = lane; s < L; s += 32) {
-        const int nimg = popcw(R.imgc(wl)[s]);
-        const long long total = (long long)R.pedc(wl)[s] + (long long)c.vins * (n2 - nimg) +
-                                (long long)c.eins * (m2.m - (int)R.e2c(wl)[s]);
+        const int nimg = popcw(FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0)));
+        const long long total = (long long)FG_AT(R.pedc(wl), s, WN(int32_t, WR_PED0)) +
+                                (long long)c.vins * (n2 - nimg) +
+                                (long long)c.eins * (m2.m - (int)FG_AT(R.e2c(wl), s, WN(uint16_t, WR_E20)));
         const unsigned long long key = ((unsigned long long)total << 32) | (unsigned)s;
         best = key < best ? key : best;
     }
@@ -614,15 +641,14 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
         best = y < best ? y : best;
     }
     if (lane == 0) {
-        p.out_cost[pair] = (int32_t)(best >> 32);
-        if (p.out_nevals) p.out_nevals[pair] = nevals + L;
+        FG_AT(p.out_cost, pair, p.n_pairs) = (int32_t)(best >> 32);
+        if (p.out_nevals) FG_AT(p.out_nevals, pair, p.n_pairs) = nevals + L;
     }
     const int bs = (int)(best & 0xffffffffull);
-    const uint8_t *mbest = R.mapc(wl) + (int64_t)bs * mrow;
-    int32_t *om = p.out_map + p.map_off[pair];
+    const int64_t mo = FG_AT(p.map_off, pair, p.n_pairs);
     for (int k = lane; k < n1; k += 32) {
-        const uint8_t v = mbest[k];
-        om[k] = v == DEL ? -1 : (int32_t)v;
+        const uint8_t v = FG_AT(R.mapc(wl), (int64_t)bs * mrow + k, wl.size[WR_MAP0]);
+        FG_AT(p.out_map, mo + k, p.map_total) = v == DEL ? -1 : (int32_t)v;
     }
     __syncwarp();
     WPHASE(8);
@@ -630,6 +656,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     if (lane == 0 && p.phase_cycles)
         for (int k = 0; k < 16; ++k) atomicAdd(&p.phase_cycles[k], (unsigned long long)ph[k]);
 #endif
+#undef WN
 }
 
 // Persistent one-warp teams: each warp pops pairs from the class's queue until it is empty.
@@ -646,8 +673,9 @@ __global__ void __launch_bounds__(128, 5) kbest_warp_kernel(const KParams p)
         if ((threadIdx.x & 31) == 0) qi = atomicAdd(p.queue_head, 1);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= p.n_order) break;
-        if (fold) solve_pair_warp<Word, BK, true>(p, wb, gw, p.order[qi]);
-        else solve_pair_warp<Word, BK, false>(p, wb, gw, p.order[qi]);
+        const int pair = FG_AT(p.order, qi, p.n_order);
+        if (fold) solve_pair_warp<Word, BK, true>(p, wb, gw, pair);
+        else solve_pair_warp<Word, BK, false>(p, wb, gw, pair);
     }
 }
 

@@ -356,6 +356,12 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
     p.out_nevals = out_nevals;
     p.gscratch = base + off_teams;
     p.lay = cp.lay;
+    p.n_graphs = b->n_graphs;
+    p.n_pairs = b->n_pairs;
+    p.n_vlab = b->total_vertices;
+    p.adj_words = (int64_t)adj_words;
+    p.plane_words = (int64_t)adj_words * B;
+    p.map_total = b->map_len;
     NA_CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(B), p, (int)grid, block,
                        (size_t)cp.lay.smem_bytes, st));
     NA_CK(cudaMemcpyAsync(&host_err, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -363,6 +369,7 @@ extern "C" int fastged_batch_noalloc(const fastged_cost_model *cost,
 #undef NA_CK
     if (host_err & kErrDuplicateEdge)
         return set_error(FASTGED_ERR_INVALID_ARG, "duplicate edge in a graph");
+    if (host_err & kErrBounds) return set_error(FASTGED_ERR_CUDA, "device bounds check failed");
     if (host_err) return set_error(FASTGED_ERR_CUDA, "device error flag set");
     return FASTGED_OK;
 }

@@ -133,7 +133,8 @@ def load(path: Optional[str] = None, build_if_missing: bool = True):
     global _LIB
     if _LIB is not None and path is None:
         return _LIB
-    p = path or _build.lib_path()
+    # FASTGED_LIBRARY names another build of the library (the bounds-checked one, say)
+    p = path or os.environ.get("FASTGED_LIBRARY") or _build.lib_path()
     if not os.path.exists(p):
         if not build_if_missing:
             raise RuntimeError(f"libfastged not built ({p}); run __graft_entry__.build()")

@@ -119,7 +119,7 @@ def test_bench_line_has_every_contract_key(monkeypatch, capsys, fake_smi):
     _stand_ins(monkeypatch)
     d = _run_bench(monkeypatch, capsys, ["--steps", "3", "--warmup", "3", "--pairs", "400",
                                           "--cpu-sample", "64", "--plain-sample", "40",
-                                          "--serve-window", "0.1"])
+                                          "--serve-window", "0.1", "--suite-cpu-seconds", "0.3"])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
               "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
@@ -147,6 +147,20 @@ def test_bench_line_has_every_contract_key(monkeypatch, capsys, fake_smi):
         shapes = d[leg]["by_shape"]
         assert sum(v["n"] for v in shapes.values()) == d[leg]["completed"]
         assert "molecule" in shapes and shapes["molecule"]["p50_ms"] == pytest.approx(3.0)
+    # the other workloads: configs 1, 3, 4, the wide beam and the size sweep, each with its
+    # throughput, evaluation rate, ALU roofline, HBM roofline where the beam spills, and a
+    # bounded (or skipped) oracle sample
+    suite = d["suite"]
+    assert {"config1", "dense", "large", "widebeam", "sizesweep_n50", "sizesweep_n950"} <= set(suite)
+    for key, rec in suite.items():
+        for k in ("workload", "value", "evals_per_s", "kernel_ms", "roofline", "cpu_baseline"):
+            assert k in rec, (key, k)
+        assert rec["roofline"]["bound"] == "alu" and rec["roofline"]["peak"] == pytest.approx(20.0)
+        cb = rec["cpu_baseline"]
+        assert cb["kind"] == "oracle" and (cb["value"] is None) == cb["sample"].startswith("skipped")
+    assert "roofline_hbm" in suite["large"] and "roofline_hbm" in suite["widebeam"]
+    assert suite["large"]["cpu_baseline"]["value"] is None
+    assert "roofline_hbm" not in suite["config1"]
 
 
 class _SetAttr:
@@ -176,7 +190,7 @@ def _bench_rank(rank, world, port, out_dir):
     _stand_ins(_SetAttr())
     import bench
     sys.argv = ["bench.py", "--gpus", str(world), "--steps", "3", "--warmup", "3",
-                "--pairs", "200", "--plain-sample", "20", "--serve-window", "0.1"]
+                "--pairs", "200", "--plain-sample", "20", "--serve-window", "0.1", "--no-suite"]
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         rc = bench.main()
@@ -213,7 +227,8 @@ def test_other_workloads_keep_the_oracle_legs_bounded(monkeypatch, capsys, fake_
     _stand_ins(monkeypatch)
     d = _run_bench(monkeypatch, capsys, ["--workload", workload, "--pairs", str(pairs),
                                           "--steps", "3", "--warmup", "3", "--plain-sample", "2",
-                                          "--serve-window", "0.05", "--cpu-seconds", "1"])
+                                          "--serve-window", "0.05", "--cpu-seconds", "1",
+                                          "--no-suite"])
     for key in ("cpu_baseline", "cpu_baseline_1core"):
         leg = d[key]
         if workload in ("large", "sizesweep"):
