@@ -42,9 +42,10 @@ cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int
                             size_t smem, int *out);
 bool kbest_has_smem_variant(int W, bool wide, bool w32);
 bool kbest_has_cluster_variant(int W, bool wide, bool w32);
-cudaError_t launch_kbest_cluster(int W, int bk, const KParams &p, int grid, int block,
+cudaError_t launch_kbest_cluster(int W, bool wide, int bk, const KParams &p, int grid, int block,
                                  size_t smem, int cluster, cudaStream_t st);
-cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int cluster, int *out);
+cudaError_t kbest_cluster_occupancy(int W, bool wide, int bk, int block, size_t smem, int cluster,
+                                    int *out);
 size_t team_shared_cluster_bytes();
 cudaError_t launch_pack(const PackParams &pp, int n_graphs, cudaStream_t st);
 size_t team_shared_static_bytes();
@@ -706,7 +707,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
         plan_layout(cp, B, forced_block ? forced_block : 512, max_dyn);
         const int block = cp.block = forced_block ? forced_block : 512;
         int nclu = 0;
-        cudaError_t e = kbest_cluster_occupancy(cp.W, label_instance(B), block,
+        cudaError_t e = kbest_cluster_occupancy(cp.W, cp.wide, label_instance(B), block,
                                                 (size_t)cp.lay.smem_bytes, cp.cluster, &nclu);
         if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
         if (nclu < 1) return set_error(FASTGED_ERR_CUDA, "a cluster team does not fit the GPU");
@@ -1298,7 +1299,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
                 CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, 1, 32, (size_t)cp.wl.warp_bytes,
                                      st));
             else if (cp.cluster > 1)
-                CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.cluster, cp.block, cp.smem,
+                CK(launch_kbest_cluster(cp.W, cp.wide, label_instance(b.B), p, cp.cluster, cp.block, cp.smem,
                                         cp.cluster, st));
             else
                 CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, 1,
@@ -1311,7 +1312,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
         if (cp.warp)
             CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, cp.grid, cp.block, cp.smem, st));
         else if (cp.cluster > 1)
-            CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
+            CK(launch_kbest_cluster(cp.W, cp.wide, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
                                     cp.cluster, st));
         else
             CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p, cp.grid,
@@ -1327,7 +1328,7 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
                 CK(launch_kbest_warp(cp.w32, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
                                      h->class_stream[k]));
             else if (cp.cluster > 1)
-                CK(launch_kbest_cluster(cp.W, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
+                CK(launch_kbest_cluster(cp.W, cp.wide, label_instance(b.B), p, cp.grid, cp.block, cp.smem,
                                         cp.cluster, h->class_stream[k]));
             else
                 CK(launch_kbest(cp.W, cp.wide, cp.w32, cp.all_smem, label_instance(b.B), p,

@@ -5,9 +5,9 @@ namespace fastged {
 template cudaError_t launch_kbest_bk<2>(int, bool, bool, bool, const KParams &, int, int,
                                           size_t, cudaStream_t);
 template cudaError_t kbest_occupancy_bk<2>(int, bool, bool, bool, int, size_t, int *);
-template cudaError_t launch_kbest_cluster_bk<2>(int, const KParams &, int, int, size_t, int,
+template cudaError_t launch_kbest_cluster_bk<2>(int, bool, const KParams &, int, int, size_t, int,
                                                   cudaStream_t);
-template cudaError_t kbest_cluster_occupancy_bk<2>(int, int, size_t, int, int *);
+template cudaError_t kbest_cluster_occupancy_bk<2>(int, bool, int, size_t, int, int *);
 template cudaError_t launch_kbest_warp_bk<2>(bool, const KParams &, int, int, size_t,
                                               cudaStream_t);
 template cudaError_t kbest_warp_occupancy_bk<2>(bool, int, size_t, int *);

@@ -1303,12 +1303,14 @@ static cudaError_t cluster_occupancy_one(int block, size_t smem, int cluster, in
     return cudaOccupancyMaxActiveClusters(out, kbest_cluster_kernel<W, MapT, Word, BK>, &cfg);
 }
 
-// cluster teams are built for the 16-bit-map classes of 4, 8 and 16 words
-#define FASTGED_CLUSTER_DISPATCH(W_, CALL)                                               \
+// cluster teams are built for the 8-bit-map classes of 2 and 4 words and the 16-bit-map
+// classes of 4, 8 and 16 words
+#define FASTGED_CLUSTER_DISPATCH(W_, wide, CALL)                                         \
     do {                                                                                 \
         switch (W_) {                                                                    \
         case 2: return CALL(2, uint8_t, uint64_t);                                       \
-        case 4: return CALL(4, uint16_t, uint64_t);                                      \
+        case 4: if (wide) return CALL(4, uint16_t, uint64_t);                            \
+                else return CALL(4, uint8_t, uint64_t);                                  \
         case 8: return CALL(8, uint16_t, uint64_t);                                      \
         case 16: return CALL(16, uint16_t, uint64_t);                                    \
         default: return cudaErrorInvalidValue;                                           \
@@ -1316,19 +1318,20 @@ static cudaError_t cluster_occupancy_one(int block, size_t smem, int cluster, in
     } while (0)
 
 template <int BK>
-cudaError_t launch_kbest_cluster_bk(int W, const KParams &p, int grid, int block, size_t smem,
-                                    int cluster, cudaStream_t st)
+cudaError_t launch_kbest_cluster_bk(int W, bool wide, const KParams &p, int grid, int block,
+                                    size_t smem, int cluster, cudaStream_t st)
 {
 #define CALL_CL(w, M, Wd) launch_cluster_one<w, M, Wd, BK>(p, grid, block, smem, cluster, st)
-    FASTGED_CLUSTER_DISPATCH(W, CALL_CL);
+    FASTGED_CLUSTER_DISPATCH(W, wide, CALL_CL);
 #undef CALL_CL
 }
 
 template <int BK>
-cudaError_t kbest_cluster_occupancy_bk(int W, int block, size_t smem, int cluster, int *out)
+cudaError_t kbest_cluster_occupancy_bk(int W, bool wide, int block, size_t smem, int cluster,
+                                       int *out)
 {
 #define CALL_CO(w, M, Wd) cluster_occupancy_one<w, M, Wd, BK>(block, smem, cluster, out)
-    FASTGED_CLUSTER_DISPATCH(W, CALL_CO);
+    FASTGED_CLUSTER_DISPATCH(W, wide, CALL_CO);
 #undef CALL_CO
 }
 

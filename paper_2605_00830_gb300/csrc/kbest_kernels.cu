@@ -58,9 +58,9 @@ bool kbest_has_smem_variant(int W, bool wide, bool w32) { return w32 || (W <= 4 
                                                     int, size_t, cudaStream_t);                \
     extern template cudaError_t kbest_occupancy_bk<BK>(int, bool, bool, bool, int, size_t,      \
                                                        int *);                                 \
-    extern template cudaError_t launch_kbest_cluster_bk<BK>(int, const KParams &, int, int,     \
+    extern template cudaError_t launch_kbest_cluster_bk<BK>(int, bool, const KParams &, int, int, \
                                                             size_t, int, cudaStream_t);        \
-    extern template cudaError_t kbest_cluster_occupancy_bk<BK>(int, int, size_t, int, int *);  \
+    extern template cudaError_t kbest_cluster_occupancy_bk<BK>(int, bool, int, size_t, int, int *); \
     extern template cudaError_t launch_kbest_warp_bk<BK>(bool, const KParams &, int, int,       \
                                                          size_t, cudaStream_t);                \
     extern template cudaError_t kbest_warp_occupancy_bk<BK>(bool, int, size_t, int *);
@@ -87,29 +87,30 @@ cudaError_t kbest_occupancy(int W, bool wide_map, bool w32, bool sm, int bk, int
 }
 
 template <int BK>
-cudaError_t launch_kbest_cluster_bk(int W, const KParams &p, int grid, int block, size_t smem,
+cudaError_t launch_kbest_cluster_bk(int W, bool wide, const KParams &p, int grid, int block, size_t smem,
                                     int cluster, cudaStream_t st);
 template <int BK>
-cudaError_t kbest_cluster_occupancy_bk(int W, int block, size_t smem, int cluster, int *out);
+cudaError_t kbest_cluster_occupancy_bk(int W, bool wide, int block, size_t smem, int cluster, int *out);
 
 bool kbest_has_cluster_variant(int W, bool wide, bool w32)
 {
-    return !w32 && ((wide && W >= 4) || (W == 2 && !wide));
+    return !w32 && ((wide && W >= 4) || ((W == 2 || W == 4) && !wide));
 }
 
-cudaError_t launch_kbest_cluster(int W, int bk, const KParams &p, int grid, int block,
+cudaError_t launch_kbest_cluster(int W, bool wide, int bk, const KParams &p, int grid, int block,
                                  size_t smem, int cluster, cudaStream_t st)
 {
-    if (bk == 0) return launch_kbest_cluster_bk<0>(W, p, grid, block, smem, cluster, st);
-    if (bk == 2) return launch_kbest_cluster_bk<2>(W, p, grid, block, smem, cluster, st);
-    return launch_kbest_cluster_bk<8>(W, p, grid, block, smem, cluster, st);
+    if (bk == 0) return launch_kbest_cluster_bk<0>(W, wide, p, grid, block, smem, cluster, st);
+    if (bk == 2) return launch_kbest_cluster_bk<2>(W, wide, p, grid, block, smem, cluster, st);
+    return launch_kbest_cluster_bk<8>(W, wide, p, grid, block, smem, cluster, st);
 }
 
-cudaError_t kbest_cluster_occupancy(int W, int bk, int block, size_t smem, int cluster, int *out)
+cudaError_t kbest_cluster_occupancy(int W, bool wide, int bk, int block, size_t smem, int cluster,
+                                    int *out)
 {
-    if (bk == 0) return kbest_cluster_occupancy_bk<0>(W, block, smem, cluster, out);
-    if (bk == 2) return kbest_cluster_occupancy_bk<2>(W, block, smem, cluster, out);
-    return kbest_cluster_occupancy_bk<8>(W, block, smem, cluster, out);
+    if (bk == 0) return kbest_cluster_occupancy_bk<0>(W, wide, block, smem, cluster, out);
+    if (bk == 2) return kbest_cluster_occupancy_bk<2>(W, wide, block, smem, cluster, out);
+    return kbest_cluster_occupancy_bk<8>(W, wide, block, smem, cluster, out);
 }
 
 // one-warp teams (kbest_warp.cuh): w32 = one 32-bit bitset word, else one 64-bit word

@@ -255,7 +255,7 @@ cudaError_t launch_kbest(int, bool, bool, bool, int, const KParams &, int, int b
     note_launch(block, 1);
     return cudaSuccess;
 }
-cudaError_t launch_kbest_cluster(int, int, const KParams &, int, int block, size_t, int cluster,
+cudaError_t launch_kbest_cluster(int, bool, int, const KParams &, int, int block, size_t, int cluster,
                                  cudaStream_t)
 {
     note_launch(block, cluster);
@@ -266,7 +266,7 @@ cudaError_t kbest_occupancy(int, bool, bool, bool, int, int, size_t, int *out)
     *out = 2;
     return cudaSuccess;
 }
-cudaError_t kbest_cluster_occupancy(int, int, int, size_t, int cluster, int *out)
+cudaError_t kbest_cluster_occupancy(int, bool, int, int, size_t, int cluster, int *out)
 {
     *out = 152 / cluster;
     return cudaSuccess;
@@ -287,7 +287,7 @@ cudaError_t kbest_warp_occupancy(bool, int, int block, size_t smem, int *out)
 bool kbest_has_smem_variant(int, bool, bool) { return true; }
 bool kbest_has_cluster_variant(int W, bool wide, bool w32)
 {
-    return !w32 && ((wide && W >= 4) || (W == 2 && !wide));
+    return !w32 && ((wide && W >= 4) || ((W == 2 || W == 4) && !wide));
 }
 size_t team_shared_static_bytes() { return 2048; }
 size_t team_shared_cluster_bytes() { return 4096; }

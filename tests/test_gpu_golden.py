@@ -28,7 +28,7 @@ G = importlib.util.module_from_spec(_spec)
 _spec.loader.exec_module(G)
 
 TARGETS = ["config2", "config3", "config4", "config5_2000", "widebeam", "sizesweep_200",
-           "sizesweep_300", "sizesweep_500"]
+           "sizesweep_300", "sizesweep_500", "sizesweep_950"]
 
 
 def compare(name, w, cost, maps, nev):
