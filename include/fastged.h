@@ -118,6 +118,10 @@ typedef struct {
                              /* and g2 and K <= 128 are solved by one warp each, the others   */
                              /* by a CTA (or a cluster of CTAs) each; FASTGED_TEAM_CTA (1):   */
                              /* every pair by a CTA or cluster. Results do not depend on it   */
+    int32_t max_sms;         /* 0 = no cap; else the resident teams of each size class are   */
+                             /* capped to what fits this many SMs (whole clusters, at least   */
+                             /* one team), so that other work keeps the remaining SMs; pairs  */
+                             /* then queue for the capped teams. Results do not depend on it  */
 } fastged_options;
 
 #define FASTGED_TEAM_AUTO 0
@@ -206,16 +210,18 @@ void fastged_plan_destroy(fastged_plan *p);
  * fastged_serve_submit copies a query (g1, g2, K) into the server and returns. A dispatcher
  * thread keeps up to `lanes` batches in flight, each lane owning its own streams and
  * grow-only device buffers (graph bit-sets, beams and outputs stay resident between
- * batches). While batches run, newly arrived queries are grouped by size bucket (bit-set
- * words of g2, K range) and launched as the next batch as soon as a lane is free and one of
- * these holds: min_batch_pairs of the oldest query's bucket are pending, the oldest query
- * has waited max_wait_us, or nothing else is running. Before launching, free device memory
- * must exceed the batch's footprint plus hbm_reserve_bytes (otherwise the batch waits for a
- * running one to finish). Results are identical to fastged_batch_ex on the same query.
+ * batches). While batches run, newly arrived queries are grouped by size bucket (target
+ * graphs of at most 64, at most 256 or more vertices, each by K range) and launched as the
+ * next batch as soon as a lane is free and one of these holds: min_batch_pairs of the oldest
+ * query's bucket are pending, the oldest query has waited max_wait_us, or nothing else is
+ * running. Batches of pairs with more than 256 target vertices share an SM budget (all SMs
+ * but a sixth, at least 8 kept for the other queries) and leave two lanes free. Before
+ * launching, free device memory must exceed the batch's footprint plus hbm_reserve_bytes
+ * (otherwise the batch waits for a running one to finish). Results are identical to
+ * fastged_batch_ex on the same query.
  * --------------------------------------------------------------------------------------- */
 typedef struct {
-    int32_t lanes;             /* batches in flight at most, 1..16 (default 6); batches of */
-                               /* pairs with > 256 target vertices hold at most half      */
+    int32_t lanes;             /* batches in flight at most, 1..16 (default 12)            */
     int32_t max_batch_pairs;   /* queries per batch at most (default 4096)                 */
     int32_t min_batch_pairs;   /* launch once this many queries of a bucket wait (64)      */
     int32_t max_pending;       /* queued queries at most; beyond: FASTGED_ERR_BUSY (2^20)  */

@@ -644,13 +644,38 @@ static bool cluster_eligible(const ClassPlan &cp, int npairs, int sm_count)
     return cp.W >= 4 || (int64_t)cp.kmax * (cp.n2max + 1) >= 65536;
 }
 
+// CTAs per cluster without a tuning entry: about 20,000 successors of a level (K times the
+// target's vertices and the deletion) per CTA, between 2 and 8 CTAs (16 for a handful of
+// very wide pairs), then halved while the class's teams would take more than two waves of
+// the GPU (smaller teams spend fewer cluster barriers per successor).
+static int cluster_rule(const ClassPlan &cp, int npairs, int sm_count)
+{
+    const int64_t succ = (int64_t)cp.kmax * (cp.n2max + 1);
+    int cl = succ <= 40000 ? 2 : succ <= 160000 ? 4 : 8;
+    if (succ >= 2000000 && (int64_t)npairs * 16 <= sm_count) cl = 16;
+    while (cl > 2 && (int64_t)npairs * cl > 2 * (int64_t)sm_count) cl >>= 1;
+    return cl;
+}
+
+// The resident teams of a class capped to max_sms SMs (0 = no cap): whole clusters, or as
+// many teams as fit that many SMs at per_sm teams each; at least one team.
+static void cap_grid(ClassPlan &cp, int max_sms, int per_sm)
+{
+    if (max_sms <= 0) return;
+    const int teams = cp.grid / cp.cluster;
+    const int cap = cp.cluster > 1 ? std::max(1, max_sms / cp.cluster)
+                                   : std::max(1, max_sms * std::max(1, per_sm));
+    cp.grid = std::min(teams, cap) * cp.cluster;
+}
+
 // Chooses the team shape of a class (threads, CTAs per team) and its shared-memory budget.
 // Classes of large pairs that are too few to fill the GPU one pair per CTA get a cluster of
 // CTAs per pair.
 // One-warp classes: warps per CTA (threads / 32, at most 4) and where the vertex maps live.
 // Without a tuning entry the maps stay in shared memory when that still leaves room for 16
 // warps per SM, and CTAs hold 4 warps.
-static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
+static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block,
+                           int max_sms)
 {
     const int npairs = (int)std::max<size_t>(cp.order.size(), 1);
     TuneChoice tc;
@@ -682,12 +707,13 @@ static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_b
     cp.lay.slice_bytes = gmap ? (int64_t)wpc * cp.wl.gmap_bytes : 0;
     const int64_t need = ((int64_t)cp.order.size() + wpc - 1) / wpc;
     cp.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * occ, need));
+    cap_grid(cp, max_sms, occ);
     return FASTGED_OK;
 }
 
-static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
+static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block, int max_sms)
 {
-    if (cp.warp) return tune_warp_class(h, cp, B, forced_block);
+    if (cp.warp) return tune_warp_class(h, cp, B, forced_block, max_sms);
     const size_t stat = team_shared_static_bytes() + 1024;   // + per-block reservation
     const size_t per_sm = (size_t)h->smem_per_sm;
     const size_t max_dyn = (size_t)h->smem_optin - team_shared_static_bytes();
@@ -698,7 +724,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     if (tuned) forced_block = tc.block;
     if (cluster_eligible(cp, npairs, h->sm_count)) {
         const char *env = getenv("FASTGED_CLUSTER");
-        int cl = env ? atoi(env) : (tuned ? tc.cluster : 8);
+        int cl = env ? atoi(env) : (tuned ? tc.cluster : cluster_rule(cp, npairs, h->sm_count));
         if (cl == 1 || cl == 2 || cl == 4 || cl == 8 || cl == 16) {
             cp.cluster = cl;
         }
@@ -715,6 +741,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
         cp.smem = (size_t)cp.lay.smem_bytes;
         cp.all_smem = false;
         cp.grid = std::min(nclu, npairs) * cp.cluster;
+        cap_grid(cp, max_sms, 1);
         return FASTGED_OK;
     }
     int block = forced_block;
@@ -737,6 +764,7 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block)
     cp.smem = (size_t)cp.lay.smem_bytes;
     const int64_t want = (int64_t)h->sm_count * occ;
     cp.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)cp.order.size()));
+    cap_grid(cp, max_sms, occ);
     return FASTGED_OK;
 }
 
@@ -826,6 +854,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
         return set_error(FASTGED_ERR_INVALID_ARG, "vertex_order must be 0 or 1");
     if (opt.team != FASTGED_TEAM_AUTO && opt.team != FASTGED_TEAM_CTA)
         return set_error(FASTGED_ERR_INVALID_ARG, "team must be 0 or 1");
+    if (opt.max_sms < 0) return set_error(FASTGED_ERR_INVALID_ARG, "max_sms must be >= 0");
     b.perm.clear();
     Reordered ro;
     if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
@@ -1059,7 +1088,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     }
     b.map_total = mtot;
     for (auto &cp : b.classes) {
-        int rc = tune_class(h, cp, B, opt.block_threads);
+        int rc = tune_class(h, cp, B, opt.block_threads, opt.max_sms);
         if (rc) return rc;
     }
     if ((int)b.classes.size() > kMaxClasses)
@@ -1492,7 +1521,7 @@ static int autotune_batch(fastged_handle *h, const fastged_pair_list *pl, int32_
                     cands.push_back(c);
                 }
         } else if (cluster_eligible(cp, npairs, h->sm_count)) {
-            for (int cl : {1, 4, 8, 16}) {
+            for (int cl : {1, 2, 4, 8, 16}) {
                 TuneChoice c;
                 c.block = cl == 1 ? 256 : 512;
                 c.cluster = cl;

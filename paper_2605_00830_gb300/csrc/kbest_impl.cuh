@@ -268,14 +268,21 @@ __device__ __noinline__ void select_exact(const KParams &p, int32_t *cand, int32
     neq = warp_sum(neq);
     if (lane == 0) { FG_AT(S.wlt, warp, NSW) = nlt; FG_AT(S.weq, warp, NSW) = neq; }
     tm.sync();
-    int lt_all = 0;
-    for (int w = 0; w < NW; ++w) lt_all += FG_AT(S.wlt, w, NSW);
-    const int q = newL - lt_all;
-    int keep_before = 0, eq_before = 0;
-    for (int w = 0; w < warp; ++w) {
-        keep_before += FG_AT(S.wlt, w, NSW);
-        eq_before += FG_AT(S.weq, w, NSW);
+    // the warps' counts are read by all lanes at once (for a cluster team they live in
+    // global scratch, so a serial walk would pay one round trip per warp)
+    int lt_all = 0, keep_before = 0, eq_before = 0;
+    for (int w = lane; w < NW; w += 32) {
+        const int lt = FG_AT(S.wlt, w, NSW);
+        lt_all += lt;
+        if (w < warp) {
+            keep_before += lt;
+            eq_before += FG_AT(S.weq, w, NSW);
+        }
     }
+    lt_all = warp_sum(lt_all);
+    keep_before = warp_sum(keep_before);
+    eq_before = warp_sum(eq_before);
+    const int q = newL - lt_all;
     keep_before += min(q, eq_before);
     compact_kept<Word>(p, R, base, n, thr, q, keep_before, eq_before, pk);
     tm.sync();
@@ -707,7 +714,9 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         // the count of bucket b; lanes past the end count in the last bucket, which only
         // bounds the threshold search from above (the level total comes from the counts kw).
         int pa = INT_MAX;
-        for (int w = 0; w < NW; ++w) pa = min(pa, FG_AT(S.wmin, w, NSW));
+        for (int w = lane; w < NW; w += 32) pa = min(pa, FG_AT(S.wmin, w, NSW));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pa = min(pa, __shfl_xor_sync(0xffffffffu, pa, o));
         {
             int hreg = 0;
             if (kw >= 1024 && kw <= 65000) {
@@ -887,12 +896,27 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
 
         // ---- S4 selection ---------------------------------------------------------
         // every warp reads the (bucket, warp) table: bucket totals, their exclusive prefix,
-        // and the bucket-b successors of the warps before this one
+        // and the bucket-b successors of the warps before this one; eight loads in flight
+        // per lane (a cluster team's table is in global scratch)
         int tot = 0, mine = 0;
-        for (int w = 0; w < NW; ++w) {
-            const int v = FG_AT(R.hist, lane * NW + w, FG_N(int32_t, p.lay.rsize[RG_HIST]));
-            tot += v;
-            mine += (w < warp) ? v : 0;
+        {
+            const int64_t hb = (int64_t)lane * NW;
+            int w = 0;
+            for (; w + 8 <= NW; w += 8) {
+                int v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = FG_AT(R.hist, hb + w + u, FG_N(int32_t, p.lay.rsize[RG_HIST]));
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    tot += v[u];
+                    mine += (w + u < warp) ? v[u] : 0;
+                }
+            }
+            for (; w < NW; ++w) {
+                const int v = FG_AT(R.hist, hb + w, FG_N(int32_t, p.lay.rsize[RG_HIST]));
+                tot += v;
+                mine += (w < warp) ? v : 0;
+            }
         }
         int incl = tot;
 #pragma unroll
@@ -902,7 +926,8 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         }
         const int bexcl = incl - tot;
         int total = 0;   // successors of the level (the last bucket may hold padding)
-        for (int w = 0; w < NW; ++w) total += FG_AT(S.wn, w, NSW);
+        for (int w = lane; w < NW; w += 32) total += FG_AT(S.wn, w, NSW);
+        total = warp_sum(total);
         const int newL = min(K, total);
         // the bucket where the cumulative count reaches newL
         const int thr = __ffs(__ballot_sync(0xffffffffu, bexcl < newL && incl >= newL)) - 1;

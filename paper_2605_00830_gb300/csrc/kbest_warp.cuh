@@ -12,7 +12,9 @@
 //   * evaluation runs lane <-> parent node: each lane keeps its node's vectors (Img, P, label
 //     planes of P, base PED) in registers and walks the node's free target vertices in
 //     increasing order, so no successor-id list is built; every step of that walk scores one
-//     successor per lane against the staged target record of its vertex, without branches;
+//     successor per lane against the staged target record of its vertex, without branches.
+//     A group of at most 16 nodes (the tail of the beam, or an early level) gives each node
+//     2-32 lanes, each walking the free vertices of one slice of the target's vertex range;
 //   * the PED histogram of the selection is counted in the same loop in per-lane 4-bit
 //     counters (16 buckets, widened to 16 bits every 15 steps and summed over the warp once
 //     per level), anchored at the PED of the best parent, a lower bound of every child (costs
@@ -153,8 +155,16 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     };
     int tot = 0;
     for (int g0 = 0; g0 < L; g0 += 32) {
-        const int s = g0 + lane;
-        const bool act = s < L;
+        // a group of ng nodes: one lane per node when ng > 16, else q = 2^qs lanes per node
+        // (ng * q <= 32), lane part r taking the free vertices in its slice of the target's
+        // vertex range and the last part the deletion too, so that a short group (the last
+        // of a beam of 100, or a level of few nodes) keeps every lane busy
+        const int ng = min(32, L - g0);
+        const int qs = ng > 16 ? 0 : ng > 8 ? 1 : ng > 4 ? 2 : ng > 2 ? 3 : ng > 1 ? 4 : 5;
+        const int q = 1 << qs;
+        const int r = lane & (q - 1);
+        const int s = g0 + (lane >> qs);
+        const bool act = (lane >> qs) < ng;
         // S2: P = images of the substituted g1 neighbours of v_i, their edge labels as planes
         // at the image positions, dcnt = deleted neighbours (the neighbour list is the same
         // for every lane: v_i's prior neighbours)
@@ -188,23 +198,30 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         const Word im = act ? FG_AT(R.imgc(wl), s, FG_N(Word, wl.size[WR_IMG0])) : ~(Word)0;
         const int base = act ? FG_AT(R.pedc(wl), s, FG_N(int32_t, wl.size[WR_PED0])) + c_edel * dcnt - A
                              : 0;
-        const int cnt = act ? n2 - popcw((Word)(im & nmask)) + 1 : 0;   // free vertices + deletion
-        int incl = cnt;
+        const Word fr = act ? (Word)(~im & nmask) : (Word)0;   // the node's free vertices
+        const int ncnt = act ? popcw(fr) + 1 : 0;               // and its deletion
+        // this lane's slice [lo, hi) of 0..n2-1 (lo < n2 <= WB unless n2 = 0)
+        const int lo = (r * n2) >> qs, hi = ((r + 1) * n2) >> qs;
+        const Word below = lo >= WB ? ~(Word)0 : (((Word)1 << lo) - (Word)1);
+        const Word upto = hi >= WB ? ~(Word)0 : (((Word)1 << hi) - (Word)1);
+        Word x = fr & upto & ~below;
+        const int cnt = act ? popcw(x) + (r == q - 1 ? 1 : 0) : 0;   // this lane's successors
+        int incl = r == 0 ? ncnt : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
-        const int off = tot + incl - cnt;
-        if (act) FG_AT(R.nodeoff(wl), s, FG_N(uint16_t, wl.size[WR_NODEOFF])) = (uint16_t)off;
+        const int noff = tot + incl - ncnt;   // the node's first entry (same on all its parts)
+        if (act && r == 0) FG_AT(R.nodeoff(wl), s, FG_N(uint16_t, wl.size[WR_NODEOFF])) = (uint16_t)noff;
+        const int off = noff + popcw((Word)(fr & below));   // this lane's first entry
         const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
 #ifdef FASTGED_PHASE_TIMERS
         if (steps) *steps += maxc;   // profiling builds: loop steps of the level
 #endif
-        Word x = act ? (Word)(~im & nmask) : (Word)0;
         uint16_t *ent = R.ent(wl);
         const int dummy = wl.ent_dummy;
-        // two successors of the lane's node per step (its next two free vertices, or the
+        // two successors of the lane's slice per step (its next two free vertices, or the
         // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
         // overflow inside one
         auto score = [&](int j) -> int {

@@ -52,6 +52,7 @@ struct Lane {
     fastged_handle *h = nullptr;
     bool busy = false;
     bool large = false;   // running a batch of large pairs
+    int sms = 0;          // SMs the large batch's teams may hold at once
     bool done = false;
     std::vector<Request *> reqs;
     std::vector<fastged_graph> graphs;
@@ -66,16 +67,24 @@ double ms_between(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// Size buckets. A batch carries a K per pair, so small and medium queries are split only
+// where their kernels differ: target graphs of at most 64 vertices (one-warp teams up to
+// K = 128, CTA teams above) and of 65-256 vertices, each by K <= 128 or above. Larger
+// targets (cluster teams) are split by bitset words (<= 512 vertices or more) and K range,
+// so that each large batch is one size class whose team shape fits its K.
 int bucket_of(int n2, int K)
 {
-    const int w = n2 <= 32 ? 0 : n2 <= 64 ? 1 : n2 <= 128 ? 2 : n2 <= 256 ? 3 : n2 <= 512 ? 4 : 5;
+    if (n2 <= 64) return K <= 128 ? 0 : 1;
+    if (n2 <= 256) return K <= 128 ? 2 : 3;
+    const int w = n2 <= 512 ? 0 : 1;
     const int k = K <= 32 ? 0 : K <= 128 ? 1 : K <= 512 ? 2 : 3;
-    return w * 4 + k;
+    return 4 + 4 * w + k;
 }
 
-// Buckets of pairs with more than 256 target vertices: such batches run for long, so they
-// may hold at most half of the lanes and never starve the small queries.
-bool bucket_is_large(int bucket) { return bucket / 4 >= 4; }
+// Buckets of pairs with more than 256 target vertices: such batches run for long, so
+// together they hold at most the SMs of the large-batch budget and leave lanes free for the
+// small queries.
+bool bucket_is_large(int bucket) { return bucket >= 4; }
 
 // The checks fastged_batch applies to one graph, plus duplicate edges (found by sorting).
 int validate_graph(const fastged_graph *g, bool *labelled)
@@ -116,6 +125,8 @@ struct fastged_server {
     std::thread dispatcher;
     bool stopping = false;
     fastged_serve_stats st{};
+    int sm_count = 1;
+    int large_sms = 1;   // SMs that the large batches in flight may hold together
 };
 
 // Queries of a failed batch that may still be retried go back to the front of the queue in
@@ -182,7 +193,8 @@ static void collect_lane(fastged_server *s, Lane &l)
 
 // Builds and enqueues one batch on a free lane (caller holds mu; it is released while the
 // batch is flattened and launched).
-static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex> &lk)
+static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex> &lk,
+                         int max_sms)
 {
     NvtxRange r("fastged serve batch");
     const int np = (int)l.reqs.size();
@@ -223,7 +235,14 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
     pl.pairs = l.pairs.data();
     fastged_options o = default_options();
     o.k_per_pair = l.kpp.data();
+    o.max_sms = max_sms;
     int rc = batch_enqueue(l.h, &pl, kmax, o);
+    int sms = 0;
+    if (rc == FASTGED_OK && l.large) {
+        // large classes run one CTA per SM
+        for (const ClassPlan &cp : l.h->batch.classes) sms += cp.grid;
+        sms = std::min(sms, s->sm_count);
+    }
     if (rc == FASTGED_OK && cudaLaunchHostFunc(l.h->stream, lane_done_cb, &l) != cudaSuccess)
         rc = FASTGED_ERR_CUDA;
     if (rc != FASTGED_OK) {
@@ -232,6 +251,7 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
         cudaGetLastError();
     }
     lk.lock();
+    l.sms = rc == FASTGED_OK ? sms : 0;
     if (rc != FASTGED_OK) {
         // nothing is in flight on this lane: queue the requests again while they may be
         // retried, report the failure for the others
@@ -287,9 +307,18 @@ static void dispatcher_main(fastged_server *s)
         if (s->stopping && s->pending.empty() && busy == 0) break;
         bool launched = false;
         if (free_lane && !s->pending.empty()) {
-            int large_busy = 0;
-            for (const Lane &l : s->lanes) large_busy += (l.busy && l.large) ? 1 : 0;
-            const bool large_ok = large_busy < std::max(1, (int)s->lanes.size() / 2);
+            // large batches: while one runs, another starts only if two lanes stay free for
+            // the small queries and the SM budget has room for a team of a few CTAs
+            int large_busy = 0, large_held = 0;
+            for (const Lane &l : s->lanes)
+                if (l.busy && l.large) {
+                    ++large_busy;
+                    large_held += l.sms;
+                }
+            const int large_room = s->large_sms - large_held;
+            const bool large_ok =
+                large_busy == 0 ||
+                (large_busy < std::max(1, (int)s->lanes.size() - 2) && large_room >= 4);
             // the oldest query whose bucket may run now
             const Request *oldest = nullptr;
             for (const Request *q : s->pending)
@@ -326,7 +355,8 @@ static void dispatcher_main(fastged_server *s)
                 } else {
                     free_lane->reqs = std::move(take);
                     free_lane->large = bucket_is_large(bkt);
-                    launch_batch(s, *free_lane, lk);
+                    launch_batch(s, *free_lane, lk,
+                                 free_lane->large ? std::max(large_room, 2) : 0);
                     launched = true;
                 }
             }
@@ -340,7 +370,7 @@ static fastged_serve_config serve_defaults()
 {
     fastged_serve_config c;
     memset(&c, 0, sizeof(c));
-    c.lanes = 6;
+    c.lanes = 12;
     c.max_batch_pairs = 4096;
     c.min_batch_pairs = 64;
     c.max_pending = 1 << 20;
@@ -372,6 +402,10 @@ extern "C" int fastged_serve_start(const fastged_cost_model *cost, const fastged
             return rc;
         }
     }
+    // the large batches together keep off a sixth of the SMs (at least 8), which stay free
+    // for the small queries' teams
+    s->sm_count = std::max(1, s->lanes[0].h->sm_count);
+    s->large_sms = std::max(2, s->sm_count - std::max(8, s->sm_count / 6));
     s->dispatcher = std::thread(dispatcher_main, s);
     *out = s;
     return FASTGED_OK;

@@ -43,12 +43,12 @@ def _plan(L, h, mm, K, **opts):
     return p.value, st
 
 
-def _probe_classes(L, w, K, team=F.FASTGED_TEAM_CTA, full=False):
+def _probe_classes(L, w, K, team=F.FASTGED_TEAM_CTA, full=False, **opts):
     """(block, cluster) of every size class when the batch is planned now (with full=True,
     a dict of the class's fields)."""
     c = (ctypes.c_int32 * 6)(*w.cost)
     mm = F.Marshalled(w.graphs, w.pairs)
-    o = F.make_options(team=team)
+    o = F.make_options(team=team, **opts)
     assert L.probe_flatten(ctypes.addressof(mm.pl), K, ctypes.addressof(o), c) == 0
     v = (ctypes.c_int64 * 31)()
     L.probe_batch(v)
@@ -159,7 +159,7 @@ def test_one_warp_classes_and_their_tuning(lib):
 def test_autotuner_picks_the_fastest_cluster_size(lib):
     lib.fastged_autotune_clear()
     lib.fake_set_shape_ms(0, 0, 0.0)
-    for (block, cl), ms in (((256, 1), 5.0), ((512, 4), 1.0), ((512, 8), 2.0),
+    for (block, cl), ms in (((256, 1), 5.0), ((512, 2), 4.0), ((512, 4), 1.0), ((512, 8), 2.0),
                             ((512, 16), 3.0)):
         lib.fake_set_shape_ms(block, cl, ms)
     w = W.config4(4, n_range=(600, 700))      # a few large pairs: cluster teams are eligible
@@ -168,7 +168,7 @@ def test_autotuner_picks_the_fastest_cluster_size(lib):
     n0 = lib.fake_kbest_launches()
     p, st = _plan(lib, h, mm, 64, autotune=1)
     ncls = st.n_classes
-    assert lib.fake_kbest_launches() - n0 == ncls * 4 * 2
+    assert lib.fake_kbest_launches() - n0 == ncls * 5 * 2
     assert all(b == (512, 4) for b in _probe_classes(lib, w, 64))
     lib.fastged_plan_destroy(p)
     lib.fastged_destroy(h)
@@ -233,3 +233,60 @@ def test_failed_device_allocation_leaves_the_handle_usable(lib):
     assert run(small)[0] == F.FASTGED_OK
     lib.fastged_destroy(h)
 
+
+
+def _cluster_rule(kmax, n2max, npairs, sms=152):
+    """CTAs per cluster team without a tuning entry: about 20,000 successors of a level per
+    CTA (2 to 8; 16 for a handful of very wide pairs), halved while the teams would take
+    more than two waves of the GPU."""
+    succ = kmax * (n2max + 1)
+    cl = 2 if succ <= 40000 else 4 if succ <= 160000 else 8
+    if succ >= 2000000 and npairs * 16 <= sms:
+        cl = 16
+    while cl > 2 and npairs * cl > 2 * sms:
+        cl //= 2
+    return cl
+
+
+def test_cluster_size_follows_the_beam_and_the_pair_count(lib):
+    lib.fastged_autotune_clear()
+    lib.fake_set_shape_ms(0, 0, 0.0)
+    seen = {}
+    for K, npairs in ((32, 3), (128, 3), (512, 3), (1024, 60), (5000, 2)):
+        w = W.config4(npairs, n_range=(600, 700))
+        cls = _probe_classes(lib, w, K, full=True)
+        assert cls and all(c["cluster"] > 1 for c in cls)
+        for c in cls:
+            assert c["cluster"] == _cluster_rule(c["kmax"], c["n2max"], c["n_order"])
+            assert c["grid"] == min(152 // c["cluster"], c["n_order"]) * c["cluster"]
+        seen[(K, npairs)] = cls[0]["cluster"]
+    # hand-checked cases: 600-700 target vertices
+    assert seen == {(32, 3): 2, (128, 3): 4, (512, 3): 8, (1024, 60): 4, (5000, 2): 16}
+
+
+def test_max_sms_caps_the_resident_teams(lib):
+    lib.fastged_autotune_clear()
+    w = W.config4(20, n_range=(600, 700))
+    base = _probe_classes(lib, w, 512, full=True)
+    for cap in (1, 24, 100):
+        capped = _probe_classes(lib, w, 512, full=True, max_sms=cap)
+        for b, c in zip(base, capped):
+            cl = b["cluster"]
+            assert c["cluster"] == cl and c["grid"] % cl == 0
+            assert c["grid"] == min(b["grid"] // cl, max(1, cap // cl)) * cl
+    # one-CTA teams (two per SM in the fake) and one-warp teams (CTAs per SM by their
+    # shared memory)
+    w2 = W.config2(3000)
+    for team in (F.FASTGED_TEAM_AUTO, F.FASTGED_TEAM_CTA):
+        base = _probe_classes(lib, w2, 100, team=team, full=True)
+        capped = _probe_classes(lib, w2, 100, team=team, full=True, max_sms=10)
+        for b, c in zip(base, capped):
+            if c["warp"]:
+                occ = min((233472 - 1024) // (c["smem_bytes"] + 1024), 2048 // c["block"])
+            else:
+                occ = 2
+            assert c["grid"] == min(b["grid"], 10 * occ) < b["grid"]
+    c = (ctypes.c_int32 * 6)(*w2.cost)
+    mm = F.Marshalled(w2.graphs, w2.pairs)
+    o = F.make_options(max_sms=-1)
+    assert lib.probe_flatten(ctypes.addressof(mm.pl), 100, ctypes.addressof(o), c) == F.FASTGED_ERR_INVALID_ARG
