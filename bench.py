@@ -34,6 +34,9 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# the serving leg runs up to 16 lanes of batches concurrently: give their streams distinct
+# hardware queues (read when the CUDA context is created, so before torch starts CUDA)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 # DRAM traffic (read + write bytes) of the K-Best launches of one full-size step, from one ncu
 # capture of the molecule batch's step (the capture and its command are summarised with the
@@ -105,7 +108,7 @@ def parse_args():
                          "size sweep)")
     ap.add_argument("--suite-cpu-seconds", type=float, default=6.0,
                     help="wall-time bound of each sub-record's CPU oracle sample")
-    ap.add_argument("--serve-window", type=float, default=2.0,
+    ap.add_argument("--serve-window", type=float, default=20.0,
                     help="seconds of Poisson arrivals in the serving leg")
     return ap.parse_args()
 

@@ -122,6 +122,10 @@ typedef struct {
                              /* capped to what fits this many SMs (whole clusters, at least   */
                              /* one team), so that other work keeps the remaining SMs; pairs  */
                              /* then queue for the capped teams. Results do not depend on it  */
+    int32_t cluster;         /* 0 = built-in rule or tuning table; 1, 2, 4, 8 or 16: CTAs per */
+                             /* team for the classes that may use cluster teams (fewer pairs  */
+                             /* than SMs, wide bitsets or very wide beams). Small clusters do */
+                             /* the most work per SM, large ones finish a single pair soonest */
 } fastged_options;
 
 #define FASTGED_TEAM_AUTO 0
@@ -210,18 +214,23 @@ void fastged_plan_destroy(fastged_plan *p);
  * fastged_serve_submit copies a query (g1, g2, K) into the server and returns. A dispatcher
  * thread keeps up to `lanes` batches in flight, each lane owning its own streams and
  * grow-only device buffers (graph bit-sets, beams and outputs stay resident between
- * batches). While batches run, newly arrived queries are grouped by size bucket (target
- * graphs of at most 64, at most 256 or more vertices, each by K range) and launched as the
+ * batches). While batches run, newly arrived queries are grouped by size bucket (the
+ * bitset words of the target graph, and for targets of at most 64 vertices K <= 128 or
+ * above) and launched as the
  * next batch as soon as a lane is free and one of these holds: min_batch_pairs of the oldest
  * query's bucket are pending, the oldest query has waited max_wait_us, or nothing else is
- * running. Batches of pairs with more than 256 target vertices share an SM budget (all SMs
- * but a sixth, at least 8 kept for the other queries) and leave two lanes free. Before
+ * running. Batches of pairs with more than 256 target vertices run on two-CTA clusters
+ * (the most work per SM), hold at most three lanes in eight and share an SM budget (all SMs
+ * but a sixth, at least 8 kept for the other queries). Before
  * launching, free device memory must exceed the batch's footprint plus hbm_reserve_bytes
  * (otherwise the batch waits for a running one to finish). Results are identical to
  * fastged_batch_ex on the same query.
  * --------------------------------------------------------------------------------------- */
+/* A server's lanes run concurrently only on distinct hardware queues: start the process with
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 (read when the CUDA context is created), or small queries
+ * may wait behind large batches that share their queue. */
 typedef struct {
-    int32_t lanes;             /* batches in flight at most, 1..16 (default 12)            */
+    int32_t lanes;             /* batches in flight at most, 1..16 (default 16)            */
     int32_t max_batch_pairs;   /* queries per batch at most (default 4096)                 */
     int32_t min_batch_pairs;   /* launch once this many queries of a bucket wait (64)      */
     int32_t max_pending;       /* queued queries at most; beyond: FASTGED_ERR_BUSY (2^20)  */

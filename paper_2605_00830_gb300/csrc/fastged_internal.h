@@ -99,8 +99,6 @@ struct WarpLayout {
     int32_t gmap;         // 1: WR_MAP0 / WR_MAP1 are offsets into the warp's global block
     int32_t gmap_bytes;   // bytes of that global block (0 when the maps are in shared memory)
     int32_t mrow;         // bytes per stored vertex map (a multiple of 16)
-    int32_t ent_dummy;    // entry index past every level's successors (kmax * (n2max + 1)):
-                          // where lanes without a successor at a step store
     int32_t size[WR_COUNT];   // bytes of every region (bounds-checked builds check against it)
 };
 

@@ -87,22 +87,36 @@ static int cuda_fail(cudaError_t e, const char *what)
 // ------------------------------------------------------------------------------------
 // buffers
 // ------------------------------------------------------------------------------------
-int DevBuf::ensure(size_t n)
+static size_t grown(size_t n, size_t cap, bool headroom)
+{
+    if (!headroom) return n;
+    const size_t g = std::max(n, cap + cap / 2);
+    return (g + ((size_t)1 << 20) - 1) >> 20 << 20;
+}
+
+int DevBuf::ensure(size_t n, cudaStream_t st, bool headroom)
 {
     if (n <= cap) return 0;
     if (inject_fire(FASTGED_INJECT_ALLOC))
         return set_error(FASTGED_ERR_OOM, "injected device allocation failure");
-    if (p) cudaFree(p);
+    const size_t want = grown(n, cap, headroom);
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     cap = 0;
     if (n == 0) return 0;
-    cudaError_t e = cudaMalloc(&p, n);
+    cudaError_t e = cudaMallocAsync(&p, want, st);
+    size_t got = want;
+    if (e != cudaSuccess && want > n) {   // no room for the headroom: the exact size
+        cudaGetLastError();
+        e = cudaMallocAsync(&p, n, st);
+        got = n;
+    }
     if (e != cudaSuccess) {
         p = nullptr;
         cudaGetLastError();
-        return cuda_fail(e, "cudaMalloc");
+        return cuda_fail(e, "cudaMallocAsync");
     }
-    cap = n;
+    cap = got;
     return 0;
 }
 
@@ -113,22 +127,29 @@ void DevBuf::release()
     cap = 0;
 }
 
-int PinBuf::ensure(size_t n)
+int PinBuf::ensure(size_t n, bool headroom)
 {
     if (n <= cap) return 0;
     if (inject_fire(FASTGED_INJECT_ALLOC))
         return set_error(FASTGED_ERR_OOM, "injected pinned allocation failure");
+    const size_t want = grown(n, cap, headroom);
     if (p) cudaFreeHost(p);
     p = nullptr;
     cap = 0;
     if (n == 0) return 0;
-    cudaError_t e = cudaMallocHost(&p, n);
+    cudaError_t e = cudaMallocHost(&p, want);
+    size_t got = want;
+    if (e != cudaSuccess && want > n) {
+        cudaGetLastError();
+        e = cudaMallocHost(&p, n);
+        got = n;
+    }
     if (e != cudaSuccess) {
         p = nullptr;
         cudaGetLastError();
         return cuda_fail(e, "cudaMallocHost");
     }
-    cap = n;
+    cap = got;
     return 0;
 }
 
@@ -338,9 +359,10 @@ extern "C" int fastged_create(const fastged_cost_model *cost, fastged_handle **o
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // the class streams are created when a batch first has several size classes: the
+    // device maps streams onto a few hardware queues, and a process with many handles (a
+    // server's lanes) keeps its main streams on queues of their own that way
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-    for (int k = 0; k < kMaxClasses && e == cudaSuccess; ++k)
-        e = cudaStreamCreateWithFlags(&h->class_stream[k], cudaStreamNonBlocking);
     for (int k = 0; k < kMaxClasses + 1 && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
@@ -501,8 +523,7 @@ size_t fastged::plan_warp_layout(ClassPlan &cp, int B, bool gmap)
     sz[WR_IMG0] = sz[WR_IMG1] = km * wb;
     sz[WR_PED0] = sz[WR_PED1] = km * 4;
     sz[WR_E20] = sz[WR_E21] = km * 2;
-    sz[WR_ENT] = (km * (n2 + 1) + 1) * 2;   // + the slot idle lanes store to
-    wl.ent_dummy = (int32_t)(km * (n2 + 1));
+    sz[WR_ENT] = km * (n2 + 1) * 2;
     sz[WR_NODEOFF] = (km + 1) * 2;
     sz[WR_KLIST] = km * 4;
     sz[WR_SEL] = km * 4;
@@ -711,7 +732,8 @@ static int tune_warp_class(fastged_handle *h, ClassPlan &cp, int B, int forced_b
     return FASTGED_OK;
 }
 
-static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block, int max_sms)
+static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block, int max_sms,
+                      int forced_cluster)
 {
     if (cp.warp) return tune_warp_class(h, cp, B, forced_block, max_sms);
     const size_t stat = team_shared_static_bytes() + 1024;   // + per-block reservation
@@ -724,7 +746,9 @@ static int tune_class(fastged_handle *h, ClassPlan &cp, int B, int forced_block,
     if (tuned) forced_block = tc.block;
     if (cluster_eligible(cp, npairs, h->sm_count)) {
         const char *env = getenv("FASTGED_CLUSTER");
-        int cl = env ? atoi(env) : (tuned ? tc.cluster : cluster_rule(cp, npairs, h->sm_count));
+        int cl = env ? atoi(env)
+                     : forced_cluster ? forced_cluster
+                                      : (tuned ? tc.cluster : cluster_rule(cp, npairs, h->sm_count));
         if (cl == 1 || cl == 2 || cl == 4 || cl == 8 || cl == 16) {
             cp.cluster = cl;
         }
@@ -855,6 +879,9 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     if (opt.team != FASTGED_TEAM_AUTO && opt.team != FASTGED_TEAM_CTA)
         return set_error(FASTGED_ERR_INVALID_ARG, "team must be 0 or 1");
     if (opt.max_sms < 0) return set_error(FASTGED_ERR_INVALID_ARG, "max_sms must be >= 0");
+    if (opt.cluster != 0 && opt.cluster != 1 && opt.cluster != 2 && opt.cluster != 4 &&
+        opt.cluster != 8 && opt.cluster != 16)
+        return set_error(FASTGED_ERR_INVALID_ARG, "cluster must be 0, 1, 2, 4, 8 or 16");
     b.perm.clear();
     Reordered ro;
     if (opt.vertex_order == FASTGED_ORDER_DEGREE) {
@@ -1088,7 +1115,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     }
     b.map_total = mtot;
     for (auto &cp : b.classes) {
-        int rc = tune_class(h, cp, B, opt.block_threads, opt.max_sms);
+        int rc = tune_class(h, cp, B, opt.block_threads, opt.max_sms, opt.cluster);
         if (rc) return rc;
     }
     if ((int)b.classes.size() > kMaxClasses)
@@ -1139,7 +1166,7 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
     b.woff_scratch = w; w += std::max<size_t>(scratch, 256);
     b.work_bytes = w;
     // the pinned staging buffer carries the inputs up and the results back
-    int rc = h->pin.ensure(std::max<size_t>(std::max(b.in_bytes, b.out_bytes), 256));
+    int rc = h->pin.ensure(std::max<size_t>(std::max(b.in_bytes, b.out_bytes), 256), true);
     if (rc) return rc;
     uint8_t *S = (uint8_t *)h->pin.p;
     GraphMeta *smeta = (GraphMeta *)(S + b.off_meta);
@@ -1281,6 +1308,22 @@ static KParams make_params(const fastged_handle *h, const Batch &b, int k, uint8
     return p;
 }
 
+// Creates the class streams a batch of nc size classes runs on (once per handle; never
+// inside a stream capture).
+static int ensure_class_streams(fastged_handle *h, int nc)
+{
+    if (nc < 2) return FASTGED_OK;
+    for (int k = 0; k < nc && k < kMaxClasses; ++k) {
+        if (h->class_stream[k]) continue;
+        const cudaError_t e = cudaStreamCreateWithFlags(&h->class_stream[k], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            h->class_stream[k] = nullptr;
+            return cuda_fail(e, "class stream creation");
+        }
+    }
+    return FASTGED_OK;
+}
+
 // Enqueues the device path of a batch: zero pools and queues, pack, one launch per class.
 int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk,
                      cudaStream_t st, int *launches, cudaEvent_t t0, cudaEvent_t t1,
@@ -1348,6 +1391,8 @@ int fastged::enqueue(fastged_handle *h, const Batch &b, uint8_t *in, uint8_t *wk
                             cp.block, cp.smem, st));
         ++nl;
     } else if (nc > 1) {
+        for (int k = 0; k < nc; ++k)
+            if (!h->class_stream[k]) return set_error(FASTGED_ERR_CUDA, "class stream missing");
         CK(cudaEventRecord(h->ev[kMaxClasses], st));
         for (int k = 0; k < nc; ++k) {
             const ClassPlan &cp = b.classes[k];
@@ -1427,10 +1472,11 @@ int fastged::batch_enqueue(fastged_handle *h, const fastged_pair_list *pairs, in
     }
     if (rc) return rc;
     if (b.n_pairs == 0) return FASTGED_OK;
+    if ((rc = ensure_class_streams(h, (int)b.classes.size()))) return rc;
     NvtxRange r("fastged upload + launch");
-    if ((rc = h->dev_in.ensure(b.in_bytes))) return rc;
-    if ((rc = h->dev_work.ensure(b.work_bytes))) return rc;
     cudaStream_t st = h->stream;
+    if ((rc = h->dev_in.ensure(b.in_bytes, st, true))) return rc;
+    if ((rc = h->dev_work.ensure(b.work_bytes, st, true))) return rc;
     CK(cudaMemcpyAsync(h->dev_in.p, h->pin.p, b.in_bytes, cudaMemcpyHostToDevice, st));
     rc = enqueue(h, b, (uint8_t *)h->dev_in.p, (uint8_t *)h->dev_work.p, st, nullptr);
     if (rc) return rc;
@@ -1607,13 +1653,21 @@ extern "C" int fastged_plan_create(fastged_handle *h, const fastged_pair_list *p
     int rc = flatten(h, pairs, K, o, p->b);
     if (rc) { delete p; return rc; }
     p->b.opt.k_per_pair = nullptr;   // copied into the staging buffer; never dereferenced
-    if ((rc = p->dev_in.ensure(std::max<size_t>(p->b.in_bytes, 256))) ||
-        (rc = p->dev_work.ensure(p->b.work_bytes)) ||
-        (rc = p->pin_out.ensure(std::max<size_t>(p->b.out_bytes, 256)))) {
+    if ((rc = ensure_class_streams(h, (int)p->b.classes.size()))) {
+        delete p;
+        return rc;
+    }
+    // exact sizes, allocated on the handle's stream, which is idle: the upload below starts
+    // once that stream has caught up
+    if ((rc = p->dev_in.ensure(std::max<size_t>(p->b.in_bytes, 256), h->stream, false)) ||
+        (rc = p->dev_work.ensure(p->b.work_bytes, h->stream, false)) ||
+        (rc = p->pin_out.ensure(std::max<size_t>(p->b.out_bytes, 256), false))) {
         fastged_plan_destroy(p);
         return rc;
     }
-    cudaError_t e = cudaMemcpy(p->dev_in.p, h->pin.p, p->b.in_bytes, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->dev_in.p, h->pin.p, p->b.in_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&p->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&p->t1);

@@ -15,17 +15,22 @@ namespace fastged {
 
 constexpr int kMaxClasses = 16;
 
+// Grow-only device buffer. Growth is stream-ordered on the owner's stream (it waits for that
+// stream only, never for the whole device); with headroom = true it takes half again the
+// old capacity as well (rounded to 1 MiB), so that a handle serving batches of growing size
+// re-allocates rarely.
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
-    int ensure(size_t n);   // grow-only; returns a fastged status
+    int ensure(size_t n, cudaStream_t st, bool headroom);   // returns a fastged status
     void release();
 };
 
+// Grow-only pinned host buffer (the same headroom rule).
 struct PinBuf {
     void *p = nullptr;
     size_t cap = 0;
-    int ensure(size_t n);
+    int ensure(size_t n, bool headroom);
     void release();
 };
 

@@ -521,6 +521,39 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
         int wmin = INT_MAX;  // least PED this warp scored
         // PED of successor idx
         auto ped_at = [&](int idx) -> int { return entry_ped(p, R.cand, idx, pk); };
+        // S3: PED of successor (node sc, column j). Column j == n2 is the deletion
+        // v_i -> eps: its A2 column is empty, so the implied-edge terms count every
+        // substituted neighbour in P as a deleted edge (with the dcnt deleted neighbours in
+        // sbase, all deg edges to v_0..v_{i-1}), and the cost row holds c_vdel there.
+        // successors scored during the id sweep (one-CTA teams, two to four words), else in
+        // a chunked pass
+        constexpr bool kFuseEval = !CL && W > 1 && W <= 4;
+        auto succ_ped = [&](int sc, int j) -> int {
+            const int64_t im = (int64_t)(sc - ioff) * W;   // the parent's Img row
+            const int64_t Ps = (int64_t)(sc - cs0) * W;    // and its row of R.P
+            int x = 0, y = 0, z = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const Word aw = FG_AT(R.a2t, w * N2S + j, FG_N(Word, p.lay.rsize[RG_A2T]));
+                const Word ai = aw & FG_AT(imgw, im + w, NIMGW);
+                const Word pw = FG_AT(R.P, Ps + w, NP);
+                if (fold_ie) {
+                    x += popcw((Word)(ai ^ pw));
+                } else {
+                    x += popcw((Word)(ai & ~pw));
+                    y += popcw((Word)(pw & ~aw));
+                }
+                if (B > 0) {
+                    Word ld = (Word)0;
+                    for (int b = 0; b < B; ++b)
+                        ld |= FG_AT(R.PL, ((int64_t)b * KM + (sc - cs0)) * W + w, FG_N(Word, p.lay.rsize[RG_PL])) ^
+                              FG_AT(R.l2t, (b * W + w) * N2S + j, FG_N(Word, p.lay.rsize[RG_L2T]));
+                    z += popcw((Word)(aw & pw & ld));
+                }
+            }
+            return FG_AT(R.sbase, sc - cs0, FG_N(int32_t, p.lay.rsize[RG_SBASE])) + FG_AT(crc, j, N2S) +
+                   c.eins * x + c.edel * y + c.esub * z;
+        };
         for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
             const int ng = min(32, s_hi - g0);
             const int s = g0 + lane;
@@ -611,6 +644,13 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                     FG_AT(ck, idx, NCK) = ((uint32_t)s << jbits) | (uint32_t)n2;
                 }
             } else {
+                // one-CTA teams with two to four words: the sweep scores each free vertex
+                // where it finds it and writes the whole entry (PED and id), so the entries
+                // are not read back for the evaluation. Otherwise it writes ids, scored by the
+                // chunked pass below, where every lane scores a free vertex: that pays off
+                // once an evaluation costs eight words, and for cluster teams, whose pairs
+                // (wide beams) can have fewer target vertices than a warp has lanes
+                __syncwarp();   // the group's node vectors (P, PL, base) are in place
                 for (int t = 0; t < ng; ++t) {
                     const int st_ = g0 + t;
                     const int64_t im = (int64_t)(st_ - ioff) * W;   // the node's Img row
@@ -622,53 +662,27 @@ __device__ __forceinline__ void solve_pair(const KParams &p, const Regions<Word>
                         const unsigned bal = __ballot_sync(0xffffffffu, fr);
                         if (fr) {
                             const int idx = o0 + pos + __popc(bal & lanemask_lt());
-                            if (pk) FG_AT(ck, idx, NCK) = ((uint32_t)st_ << jbits) | (uint32_t)j;
-                            else FG_AT(ck64, idx, NCK64) = ((uint64_t)st_ << kSelShift) | (uint64_t)j;
+                            const int d = kFuseEval ? succ_ped(st_, j) : 0;
+                            if (kFuseEval) wmin = d < wmin ? d : wmin;
+                            if (pk) FG_AT(ck, idx, NCK) = ((uint32_t)d << 16) | ((uint32_t)st_ << jbits) | (uint32_t)j;
+                            else FG_AT(ck64, idx, NCK64) = ((uint64_t)(uint32_t)d << 32) | ((uint64_t)st_ << kSelShift) | (uint64_t)j;
                         }
                         pos += __popc(bal);
                     }
                     if (lane == 0) {
-                        if (pk) FG_AT(ck, o0 + pos, NCK) = ((uint32_t)st_ << jbits) | (uint32_t)n2;
-                        else FG_AT(ck64, o0 + pos, NCK64) = ((uint64_t)st_ << kSelShift) | (uint64_t)n2;
+                        const int d = kFuseEval ? succ_ped(st_, n2) : 0;
+                        if (kFuseEval) wmin = d < wmin ? d : wmin;
+                        if (pk) FG_AT(ck, o0 + pos, NCK) = ((uint32_t)d << 16) | ((uint32_t)st_ << jbits) | (uint32_t)n2;
+                        else FG_AT(ck64, o0 + pos, NCK64) = ((uint64_t)(uint32_t)d << 32) | ((uint64_t)st_ << kSelShift) | (uint64_t)n2;
                     }
                 }
             }
             __syncwarp();
             PHASE_MARK(5);
 
-            // S3: PED of successor (node sc, column j). Column j == n2 is the deletion
-            // v_i -> eps: its A2 column is empty, so the implied-edge terms count every
-            // substituted neighbour in P as a deleted edge (with the dcnt deleted neighbours in
-            // sbase, all deg edges to v_0..v_{i-1}), and the cost row holds c_vdel there.
-            auto succ_ped = [&](int sc, int j) -> int {
-                const int64_t im = (int64_t)(sc - ioff) * W;   // the parent's Img row
-                const int64_t Ps = (int64_t)(sc - cs0) * W;    // and its row of R.P
-                int x = 0, y = 0, z = 0;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    const Word aw = FG_AT(R.a2t, w * N2S + j, FG_N(Word, p.lay.rsize[RG_A2T]));
-                    const Word ai = aw & FG_AT(imgw, im + w, NIMGW);
-                    const Word pw = FG_AT(R.P, Ps + w, NP);
-                    if (fold_ie) {
-                        x += popcw((Word)(ai ^ pw));
-                    } else {
-                        x += popcw((Word)(ai & ~pw));
-                        y += popcw((Word)(pw & ~aw));
-                    }
-                    if (B > 0) {
-                        Word ld = (Word)0;
-                        for (int b = 0; b < B; ++b)
-                            ld |= FG_AT(R.PL, ((int64_t)b * KM + (sc - cs0)) * W + w, FG_N(Word, p.lay.rsize[RG_PL])) ^
-                                  FG_AT(R.l2t, (b * W + w) * N2S + j, FG_N(Word, p.lay.rsize[RG_L2T]));
-                        z += popcw((Word)(aw & pw & ld));
-                    }
-                }
-                return FG_AT(R.sbase, sc - cs0, FG_N(int32_t, p.lay.rsize[RG_SBASE])) + FG_AT(crc, j, N2S) +
-                       c.eins * x + c.edel * y + c.esub * z;
-            };
             // U chunks of 32 successors per step, their id loads and PEDs independent
-            constexpr int U = W <= 2 ? 2 : 1;
-            for (int kb = 0; kb < gtot; kb += 32 * U) {
+            constexpr int U = 2;
+            for (int kb = 0; !kFuseEval && kb < gtot; kb += 32 * U) {
                 int scu[U], ju[U];
                 uint32_t idu[U];
 #pragma unroll

@@ -31,6 +31,14 @@
 
 namespace fastged {
 
+// x << n with PTX semantics: shift amounts of 32 or more give 0
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t x, uint32_t n)
+{
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(n));
+    return r;
+}
+
 // PED histogram buckets of the one-warp kernel: offsets 0..kWarpBuckets-2 from the anchor,
 // and one bucket for everything past them
 constexpr int kWarpBuckets = 16;
@@ -220,7 +228,6 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         if (steps) *steps += maxc;   // profiling builds: loop steps of the level
 #endif
         uint16_t *ent = R.ent(wl);
-        const int dummy = wl.ent_dummy;
         // two successors of the lane's slice per step (its next two free vertices, or the
         // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
         // overflow inside one
@@ -242,11 +249,13 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             }
             return d;
         };
+        // bucket min(d, H - 1) of a valid successor: its 4-bit field is field dd of the
+        // 64-bit pair (chi, clo); a PTX shift by 32 or more yields 0, so the field that does
+        // not hold the bucket gets nothing without a compare
         auto count = [&](int d, bool val) {
-            const int dd = min(d, H - 1);
-            const uint32_t inc = val ? 1u << ((dd & 7) << 2) : 0u;
-            clo += dd < 8 ? inc : 0u;
-            chi += dd < 8 ? 0u : inc;
+            const uint32_t sh = (uint32_t)min(d, H - 1) << 2;
+            clo += shl_clamped((uint32_t)val, sh);
+            chi += shl_clamped((uint32_t)val, sh - 32u);
         };
         for (int t0 = 0; t0 < maxc; t0 += 14) {
             const int t1 = min(maxc, t0 + 14);
@@ -260,12 +269,13 @@ __device__ __forceinline__ int eval_level(const KParams &p,
                 const bool va = t < cnt, vb = t + 1 < cnt;
                 const int da = score(ja), db = score(jb);
 #define NE FG_N(uint16_t, wl.size[WR_ENT])
+                // predicated stores: the slots past the lane's successors write nothing
                 if (EXACT) {
-                    FG_AT(ent, va ? off + t : dummy, NE) = (uint16_t)da;
-                    FG_AT(ent, vb ? off + t + 1 : dummy, NE) = (uint16_t)db;
+                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)da;
+                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)db;
                 } else {
-                    FG_AT(ent, va ? off + t : dummy, NE) = (uint16_t)((min(da, 255) << 8) | ja);
-                    FG_AT(ent, vb ? off + t + 1 : dummy, NE) = (uint16_t)((min(db, 255) << 8) | jb);
+                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)((min(da, 255) << 8) | ja);
+                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)((min(db, 255) << 8) | jb);
 #undef NE
                     count(da, va);
                     count(db, vb);

@@ -67,24 +67,22 @@ double ms_between(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-// Size buckets. A batch carries a K per pair, so small and medium queries are split only
-// where their kernels differ: target graphs of at most 64 vertices (one-warp teams up to
-// K = 128, CTA teams above) and of 65-256 vertices, each by K <= 128 or above. Larger
-// targets (cluster teams) are split by bitset words (<= 512 vertices or more) and K range,
-// so that each large batch is one size class whose team shape fits its K.
+// Size buckets: the bitset word class of the target graph (<= 32 vertices, one 64-bit word,
+// 2, 4, 8, 16 words), and for targets of at most 64 vertices whether K <= 128 (one-warp
+// teams) or above (CTA teams). A batch carries a K per pair, so K splits nothing else, and a
+// batch of one bucket is (nearly always) one size class, launched on its lane's own stream.
 int bucket_of(int n2, int K)
 {
-    if (n2 <= 64) return K <= 128 ? 0 : 1;
-    if (n2 <= 256) return K <= 128 ? 2 : 3;
-    const int w = n2 <= 512 ? 0 : 1;
-    const int k = K <= 32 ? 0 : K <= 128 ? 1 : K <= 512 ? 2 : 3;
-    return 4 + 4 * w + k;
+    const int w = n2 <= 32 ? 0 : n2 <= 64 ? 1 : n2 <= 128 ? 2 : n2 <= 256 ? 3 : n2 <= 512 ? 4 : 5;
+    if (w <= 1) return 2 * w + (K <= 128 ? 0 : 1);
+    return 2 + w;
 }
 
-// Buckets of pairs with more than 256 target vertices: such batches run for long, so
-// together they hold at most the SMs of the large-batch budget and leave lanes free for the
-// small queries.
-bool bucket_is_large(int bucket) { return bucket >= 4; }
+// Buckets of pairs with more than 256 target vertices (two-CTA cluster teams): such batches
+// run for long (a batch holds its lane until its slowest pair ends), so they take every
+// pending pair of their bucket, hold at most three lanes in eight, and together at most the
+// SMs of the large-batch budget.
+bool bucket_is_large(int bucket) { return bucket >= 6; }
 
 // The checks fastged_batch applies to one graph, plus duplicate edges (found by sorting).
 int validate_graph(const fastged_graph *g, bool *labelled)
@@ -236,6 +234,9 @@ static void launch_batch(fastged_server *s, Lane &l, std::unique_lock<std::mutex
     fastged_options o = default_options();
     o.k_per_pair = l.kpp.data();
     o.max_sms = max_sms;
+    // large pairs on two-CTA clusters: the most successors per SM and second, which is what
+    // a stream of queries needs (a bigger cluster only shortens one pair's latency)
+    if (l.large) o.cluster = 2;
     int rc = batch_enqueue(l.h, &pl, kmax, o);
     int sms = 0;
     if (rc == FASTGED_OK && l.large) {
@@ -307,8 +308,8 @@ static void dispatcher_main(fastged_server *s)
         if (s->stopping && s->pending.empty() && busy == 0) break;
         bool launched = false;
         if (free_lane && !s->pending.empty()) {
-            // large batches: while one runs, another starts only if two lanes stay free for
-            // the small queries and the SM budget has room for a team of a few CTAs
+            // large batches: while one runs, another starts only if it would hold at most
+            // three lanes in eight and the SM budget has room for a few teams
             int large_busy = 0, large_held = 0;
             for (const Lane &l : s->lanes)
                 if (l.busy && l.large) {
@@ -318,7 +319,7 @@ static void dispatcher_main(fastged_server *s)
             const int large_room = s->large_sms - large_held;
             const bool large_ok =
                 large_busy == 0 ||
-                (large_busy < std::max(1, (int)s->lanes.size() - 2) && large_room >= 4);
+                (large_busy < std::max(1, 3 * (int)s->lanes.size() / 8) && large_room >= 4);
             // the oldest query whose bucket may run now
             const Request *oldest = nullptr;
             for (const Request *q : s->pending)
@@ -370,7 +371,7 @@ static fastged_serve_config serve_defaults()
 {
     fastged_serve_config c;
     memset(&c, 0, sizeof(c));
-    c.lanes = 12;
+    c.lanes = 16;
     c.max_batch_pairs = 4096;
     c.min_batch_pairs = 64;
     c.max_pending = 1 << 20;

@@ -74,7 +74,8 @@ class Options(ctypes.Structure):
                 ("k_per_pair", ctypes.c_void_p), ("hist_window", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("vertex_order", ctypes.c_int32),
-                ("team", ctypes.c_int32), ("max_sms", ctypes.c_int32)]
+                ("team", ctypes.c_int32), ("max_sms", ctypes.c_int32),
+                ("cluster", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -259,12 +260,12 @@ def marshal(w) -> Marshalled:
 def make_options(form: int = FASTGED_FORM_BATCHED, variant: int = 0, k_per_pair=None,
                  hist_window: int = 0, block_threads: int = 0, use_cuda_graph: int = 1,
                  autotune: int = 0, vertex_order: int = FASTGED_ORDER_INDEX,
-                 team: int = FASTGED_TEAM_AUTO, max_sms: int = 0):
+                 team: int = FASTGED_TEAM_AUTO, max_sms: int = 0, cluster: int = 0):
     kpp = None
     if k_per_pair is not None:
         kpp = np.ascontiguousarray(np.asarray(k_per_pair, dtype=np.int32))
     o = Options(form, variant, kpp.ctypes.data if kpp is not None else None, hist_window,
-                block_threads, use_cuda_graph, autotune, vertex_order, team, max_sms)
+                block_threads, use_cuda_graph, autotune, vertex_order, team, max_sms, cluster)
     o._keep = kpp
     return o
 
@@ -414,7 +415,7 @@ class FastGED:
         return cost, maps, nev
 
 
-def serve_config(lanes=12, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
+def serve_config(lanes=16, max_batch_pairs=4096, min_batch_pairs=64, max_pending=1 << 20,
                  max_wait_us=200, hbm_reserve_bytes=1 << 30, max_retries=0) -> ServeConfig:
     return ServeConfig(lanes, max_batch_pairs, min_batch_pairs, max_pending, max_wait_us,
                        max_retries, hbm_reserve_bytes)

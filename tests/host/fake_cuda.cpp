@@ -135,6 +135,8 @@ cudaError_t cudaFree(void *p)
     free(p);
     return cudaSuccess;
 }
+cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
+cudaError_t cudaFreeAsync(void *p, cudaStream_t) { return cudaFree(p); }
 cudaError_t cudaMemGetInfo(size_t *f, size_t *t)
 {
     *f = g_free_bytes;

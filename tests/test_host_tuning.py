@@ -109,7 +109,7 @@ def _warp_bytes(n1, n2, m1, K, B, w32, gmap):
     rec = a(wb * (1 + B) + 4)
     mrow = a(max(n1, 1))
     parts = [(n2 + 1) * rec, max(n2, 1) * 4, (n1 + 1) * 4, max(m1, 1) * 4, K * wb, K * wb,
-             K * 4, K * 4, K * 2, K * 2, (K * (n2 + 1) + 1) * 2, (K + 1) * 2, K * 4, K * 4,
+             K * 4, K * 4, K * 2, K * 2, K * (n2 + 1) * 2, (K + 1) * 2, K * 4, K * 4,
              K * 4]
     if not gmap:
         parts += [K * mrow, K * mrow]
@@ -224,7 +224,7 @@ def test_failed_device_allocation_leaves_the_handle_usable(lib):
         return rc, cost
 
     assert run(small)[0] == F.FASTGED_OK
-    lib.fake_fail_device_alloc(1)
+    lib.fake_fail_device_alloc(2)   # the allocation with headroom, then the exact size
     rc, cost = run(big)
     assert rc == F.FASTGED_ERR_OOM and b"cudaMalloc" in lib.fastged_last_error(None)
     assert (cost == -5).all()
@@ -290,3 +290,19 @@ def test_max_sms_caps_the_resident_teams(lib):
     mm = F.Marshalled(w2.graphs, w2.pairs)
     o = F.make_options(max_sms=-1)
     assert lib.probe_flatten(ctypes.addressof(mm.pl), 100, ctypes.addressof(o), c) == F.FASTGED_ERR_INVALID_ARG
+
+
+def test_cluster_option_forces_the_team_size(lib):
+    lib.fastged_autotune_clear()
+    w = W.config4(3, n_range=(600, 700))
+    for cl in (1, 2, 4, 16):
+        cls = _probe_classes(lib, w, 512, full=True, cluster=cl)
+        assert cls and all(c["cluster"] == cl for c in cls)
+    # classes that cannot use clusters ignore it: the molecule batch keeps one-CTA teams
+    w2 = W.config2(500)
+    assert all(c[1] == 1 for c in _probe_classes(lib, w2, 100, cluster=8))
+    c = (ctypes.c_int32 * 6)(*w.cost)
+    mm = F.Marshalled(w.graphs, w.pairs)
+    for bad in (3, -1, 32):
+        o = F.make_options(cluster=bad)
+        assert lib.probe_flatten(ctypes.addressof(mm.pl), 64, ctypes.addressof(o), c) == F.FASTGED_ERR_INVALID_ARG
