@@ -80,7 +80,8 @@ enum WarpRegion : int {
     WR_ENT,       // successor entries of a level in enumeration order, uint16[K * (n2 + 1)]
     WR_NODEOFF,   // first entry of every node, uint16[K + 1]
     WR_KLIST,     // kept successors, uint32[K]: PED offset << 16 | entry index
-    WR_SEL,       // selected children in key order, int32[K]: parent slot << 8 | j
+    WR_SEL,       // selected children in key order, int32[K]: parent slot << 8 | j (one-warp
+                  // kernel: record index j, 1 + target vertex or 0 for the deletion)
     WR_SELPED,    // their PEDs, int32[K]
     WR_MAP0, WR_MAP1,     // vertex maps of the kept nodes, uint8[K][mrow]
     WR_COUNT

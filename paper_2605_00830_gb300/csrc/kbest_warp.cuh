@@ -16,9 +16,11 @@
 //     A group of at most 16 nodes (the tail of the beam, or an early level) gives each node
 //     2-32 lanes, each walking the free vertices of one slice of the target's vertex range;
 //   * the PED histogram of the selection is counted in the same loop in per-lane 4-bit
-//     counters (16 buckets, widened to 16 bits every 15 steps and summed over the warp once
-//     per level), anchored at the PED of the best parent, a lower bound of every child (costs
-//     are non-negative and slot 0 holds the least PED of the kept list);
+//     counters (offsets 0-14 from the anchor, widened to 16 bits every 14 slots and summed
+//     over the warp once per level), anchored at the PED of the best parent, a lower bound of
+//     every child (costs are non-negative and slot 0 holds the least PED of the kept list).
+//     Costs are scaled by 4 inside the evaluation, so that an offset is the bit position of
+//     its counter; slots past a lane's successors are counted too and taken off once;
 //   * each successor leaves one 16-bit entry (PED offset clamped to 8 bits, j) in enumeration
 //     order (node by node, j increasing, the deletion last); the kept ones are compacted in
 //     that order and then placed at their rank by a counting sort over the buckets;
@@ -45,9 +47,10 @@ constexpr int kWarpBuckets = 16;
 // kept successors a warp places at once: the largest K of a one-warp class, in 32s
 constexpr int kWarpChunks = 4;
 
-// Target record of g2 vertex u (u < n2), or of the deletion column u = n2 (no neighbours, no
-// labels): adjacency word, NPL edge-label planes, and the vertex-cost entry C[i][u] of the
-// current level.
+// Target record of g2 vertex u, stored at index u + 1, or of the deletion column, stored at
+// index 0 (no neighbours, no labels): adjacency word, NPL edge-label planes, and the
+// vertex-cost entry C[i][u] of the current level times 4 (the evaluation works in units of a
+// quarter, so that a PED offset is directly the bit position of its histogram counter).
 template <typename Word, int NPL>
 struct __align__(16) TgtRec {
     Word a2;
@@ -90,8 +93,10 @@ __device__ __forceinline__ void rec_set_plane(TgtRec<Word, 0> &, int, Word) {}
 #define WPHASE(k) do { } while (0)
 #endif
 
-__device__ __forceinline__ int ffsw(uint32_t x) { return __ffs((int)x) - 1; }
-__device__ __forceinline__ int ffsw(uint64_t x) { return __ffsll((long long)x) - 1; }
+// 1 + index of the lowest set bit, 0 when none is set: the record index of the next free
+// target vertex of a walk, or of the deletion once the walk is over
+__device__ __forceinline__ int ffs1(uint32_t x) { return __ffs((int)x); }
+__device__ __forceinline__ int ffs1(uint64_t x) { return __ffsll((long long)x); }
 
 // Dynamic shared memory of the one-warp kernel (every warp of a CTA has its block in it).
 extern __shared__ __align__(16) uint8_t g_warp_smem[];
@@ -127,14 +132,16 @@ struct WarpRegs {
 
 // Scores every successor of level i (lane <-> parent node). Entries go to ent in enumeration
 // order and nodeoff receives each node's first entry. EXACT = false: entry = (min(PED - A,
-// 255) << 8) | j, and on return lane b < kWarpBuckets holds the number of successors whose
-// offset min(PED - A, H - 1) is b; EXACT = true: entry = PED - A (exact, below 2^16).
+// 255) << 8) | (record index: 1 + target vertex, 0 for the deletion), and on return lane
+// b < kWarpBuckets - 1 holds the number of successors whose offset PED - A is b (lane
+// kWarpBuckets - 1 holds no meaningful count); EXACT = true: entry = PED - A (exact, below
+// 2^16).
 // FOLD: insertion and deletion of an edge cost the same, so the two implied-edge terms are
 // one popcount. Returns the number of successors of the level.
 template <typename Word, int BK, bool FOLD, bool EXACT>
 __device__ __forceinline__ int eval_level(const KParams &p,
                                           const WarpRegs<Word, (BK == 8 ? kMaxB : BK)> &R,
-                                          int L, int n0, int deg, int n2, int mrow, int A, int H,
+                                          int L, int n0, int deg, int n2, int mrow, int A,
                                           int &hist, long long *steps = nullptr)
 {
     constexpr int WB = 8 * (int)sizeof(Word);
@@ -143,7 +150,9 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     const int lane = threadIdx.x & 31;
     const WarpLayout &wl = p.wl;
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
-    const int c_eins = p.cost.eins, c_edel = p.cost.edel, c_esub = p.cost.esub;
+    // costs in quarter units (see TgtRec): a successor's PED offset times 4 is the bit
+    // position of its 4-bit histogram counter in the 64-bit pair (chi, clo)
+    const int c_eins = 4 * p.cost.eins, c_edel = 4 * p.cost.edel, c_esub = 4 * p.cost.esub;
     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
     const uint8_t *mapc = R.mapc(wl);
     using TRec = TgtRec<Word, NPL>;
@@ -204,7 +213,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             }
         }
         const Word im = act ? FG_AT(R.imgc(wl), s, FG_N(Word, wl.size[WR_IMG0])) : ~(Word)0;
-        const int base = act ? FG_AT(R.pedc(wl), s, FG_N(int32_t, wl.size[WR_PED0])) + c_edel * dcnt - A
+        const int base = act ? 4 * (FG_AT(R.pedc(wl), s, FG_N(int32_t, wl.size[WR_PED0])) - A) + c_edel * dcnt
                              : 0;
         const Word fr = act ? (Word)(~im & nmask) : (Word)0;   // the node's free vertices
         const int ncnt = act ? popcw(fr) + 1 : 0;               // and its deletion
@@ -230,7 +239,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         uint16_t *ent = R.ent(wl);
         // two successors of the lane's slice per step (its next two free vertices, or the
         // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
-        // overflow inside one
+        // overflow inside one. score(j) is 4 * (PED - A) of the successor with record j.
         auto score = [&](int j) -> int {
             const TgtRec<Word, NPL> r = FG_AT(tgt, j, FG_N(TRec, wl.size[WR_TGT]));
             const Word ai = r.a2 & im;
@@ -249,39 +258,50 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             }
             return d;
         };
-        // bucket min(d, H - 1) of a valid successor: its 4-bit field is field dd of the
-        // 64-bit pair (chi, clo); a PTX shift by 32 or more yields 0, so the field that does
-        // not hold the bucket gets nothing without a compare
-        auto count = [&](int d, bool val) {
-            const uint32_t sh = (uint32_t)min(d, H - 1) << 2;
-            clo += shl_clamped((uint32_t)val, sh);
-            chi += shl_clamped((uint32_t)val, sh - 32u);
+        // the 4-bit field of offset d = d4 / 4 starts at bit d4 of the 64-bit pair (chi,
+        // clo); a PTX shift by 32 or more yields 0, so the word that does not hold the field
+        // gets nothing, and neither does an offset of 16 or more, without a compare. Every
+        // slot is counted, also the ones past the lane's successors; those all score the
+        // deletion record and are taken off after the loop.
+        auto count = [&](int d4) {
+            clo += shl_clamped(1u, (uint32_t)d4);
+            chi += shl_clamped(1u, (uint32_t)d4 - 32u);
         };
         for (int t0 = 0; t0 < maxc; t0 += 14) {
             const int t1 = min(maxc, t0 + 14);
             for (int t = t0; t < t1; t += 2) {
-                const int fa = ffsw(x);
-                const int ja = x ? fa : n2;
+                const int ja = ffs1(x);
                 x &= x - (Word)1;
-                const int fb = ffsw(x);
-                const int jb = x ? fb : n2;
+                const int jb = ffs1(x);
                 x &= x - (Word)1;
                 const bool va = t < cnt, vb = t + 1 < cnt;
                 const int da = score(ja), db = score(jb);
 #define NE FG_N(uint16_t, wl.size[WR_ENT])
                 // predicated stores: the slots past the lane's successors write nothing
                 if (EXACT) {
-                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)da;
-                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)db;
+                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)(da >> 2);
+                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)(db >> 2);
                 } else {
-                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)((min(da, 255) << 8) | ja);
-                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)((min(db, 255) << 8) | jb);
+                    if (va) FG_AT(ent, off + t, NE) = (uint16_t)((min(da, 1020) << 6) | ja);
+                    if (vb) FG_AT(ent, off + t + 1, NE) = (uint16_t)((min(db, 1020) << 6) | jb);
 #undef NE
-                    count(da, va);
-                    count(db, vb);
+                    count(da);
+                    count(db);
                 }
             }
             if (!EXACT) flush();
+        }
+        if (!EXACT) {
+            // the 2 * ceil(maxc / 2) - cnt slots past this lane's successors scored the
+            // deletion record (its walk was over): take them off that offset's count
+            const int nin = 2 * ((maxc + 1) >> 1) - cnt;
+            const int bd = score(0) >> 2;
+            if (nin > 0 && bd < kWarpBuckets) {
+                const int wsel = (bd & 3) | ((bd >> 3) << 2);
+                const uint32_t sub = (uint32_t)nin << (((bd >> 2) & 1) << 4);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] -= wsel == m ? sub : 0u;
+            }
         }
         tot += __shfl_sync(FULL, incl, 31);
     }
@@ -343,7 +363,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     const int B = BK == 0 ? 0 : (BK == 2 ? 2 : p.lay.B);
     const int mrow = wl.mrow;
     const CostModel c = p.cost;
-    // buckets 0..H-2 hold one PED offset each, H-1 the rest
+    // buckets 0..H-2 hold one PED offset each; a K-th offset past them takes the exact fallback
     const int H = min(p.hwin, kWarpBuckets);
     constexpr uint8_t DEL = 0xff;
     // m &= ballot(bit b of an offset) ^ lb[b] keeps the lanes whose bit b equals bit b of
@@ -356,24 +376,25 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     long long ph_last = clock64();
 #endif
 
-    // ---- stage the target graph (records of u = 0..n2, the last one the deletion) and the
-    // source graph's prior-neighbour lists
+    // ---- stage the target graph (record 0 the deletion, record u + 1 target vertex u) and
+    // the source graph's prior-neighbour lists
     {
         const uint64_t *adj2 = p.adj + m2.adj_off;
         const uint64_t *pl2 = p.planes + m2.plane_off;
         const int W2 = m2.W;
-        for (int u = lane; u <= n2; u += 32) {
+        for (int k = lane; k <= n2; k += 32) {
+            const int u = k - 1;
             Rec r;
-            r.a2 = u < n2 ? (Word)FG_AT(adj2, (int64_t)u * W2, p.adj_words - m2.adj_off) : (Word)0;
+            r.a2 = u >= 0 ? (Word)FG_AT(adj2, (int64_t)u * W2, p.adj_words - m2.adj_off) : (Word)0;
 #pragma unroll
             for (int b = 0; b < NPL; ++b)
-                rec_set_plane(r, b, (u < n2 && b < B)
+                rec_set_plane(r, b, (u >= 0 && b < B)
                                         ? (Word)FG_AT(pl2, ((int64_t)b * n2 + u) * W2,
                                                       p.plane_words - m2.plane_off)
                                         : (Word)0);
             r.crow = 0;
-            FG_AT(R.tgt(wl), u, WN(Rec, WR_TGT)) = r;
-            if (u < n2)
+            FG_AT(R.tgt(wl), k, WN(Rec, WR_TGT)) = r;
+            if (u >= 0)
                 FG_AT(R.lab2(wl), u, WN(int32_t, WR_LAB2)) =
                     FG_AT(p.vlab, m2.lab_off + u, p.n_vlab);
         }
@@ -433,12 +454,14 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     int L = 1;
     WPHASE(0);
     for (int i = 0; i < n1; ++i) {
-        // S1: this level's vertex-cost row C[i][u] (the deletion column holds c_vdel)
+        // S1: this level's vertex-cost row C[i][u] in quarter units (record 0, the deletion
+        // column, holds c_vdel)
         {
             const int a1 = FG_AT(p.vlab, m1.lab_off + i, p.n_vlab);
-            for (int u = lane; u <= n2; u += 32)
-                FG_AT(R.tgt(wl), u, WN(Rec, WR_TGT)).crow =
-                    u < n2 ? ((FG_AT(R.lab2(wl), u, WN(int32_t, WR_LAB2)) != a1) ? c.vsub : 0) : c.vdel;
+            for (int k = lane; k <= n2; k += 32)
+                FG_AT(R.tgt(wl), k, WN(Rec, WR_TGT)).crow =
+                    4 * (k > 0 ? ((FG_AT(R.lab2(wl), k - 1, WN(int32_t, WR_LAB2)) != a1) ? c.vsub : 0)
+                               : c.vdel);
         }
         __syncwarp();
         WPHASE(7);
@@ -447,18 +470,19 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
         const int A = FG_AT(R.pedc(wl), 0, WN(int32_t, WR_PED0));   // least PED of the kept list: a lower bound of every child
         int hist = 0;
 #ifdef FASTGED_PHASE_TIMERS
-        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist,
+        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, hist,
                                                           &ph[9]);
         ph[10] += tot;   // successors (the loop steps above cover them 32 lanes at a time)
         ph[11] += 1;     // levels
 #else
-        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, H, hist);
+        const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, hist);
 #endif
         nevals += tot;
         WPHASE(1);
         const int newL = min(K, tot);
-        // S4: bucket b = PED - A for b < H - 1, bucket H - 1 = everything past the window
-        const int cb = lane < H ? hist : 0;
+        // S4: bucket b = PED - A for b < H - 1; a K-th offset past them goes to the exact
+        // fallback
+        const int cb = lane < H - 1 ? hist : 0;
         int incl = cb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -466,8 +490,9 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             if (lane >= o) incl += v;
         }
         const int bexcl = incl - cb;
-        const int thr = __ffs(__ballot_sync(FULL, lane < H && incl >= newL)) - 1;
-        if (thr < H - 1) {
+        const unsigned hb = __ballot_sync(FULL, lane < H - 1 && incl >= newL);
+        if (hb) {
+            const int thr = __ffs(hb) - 1;
             // kept: every successor below bucket thr and the first q of bucket thr, compacted
             // in enumeration order (the loop stops once all are found)
             const int q = newL - __shfl_sync(FULL, bexcl, thr);
@@ -505,7 +530,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                 for (int u = 0; u < 4; ++u) {
                     if (keep[u])
                         FG_AT(R.klist(wl), keep_before + __popc(kbm[u] & lt), WN(uint32_t, WR_KLIST)) =
-                            ((uint32_t)(e[u] >> 8) << 16) | (uint32_t)(kb + 32 * u + lane);
+                            ((uint32_t)e[u] << 16) | (uint32_t)(kb + 32 * u + lane);
                     keep_before += __popc(kbm[u]);
                 }
             }
@@ -514,6 +539,8 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             // place every kept successor at its rank: (smaller offsets) + (equal offsets
             // earlier in enumeration order). All chunks of the kept list are handled at once;
             // lane b carries the kept successors of bucket b in the chunks before each one.
+            // A kept entry is its 16-bit successor entry (offset << 8 | record index) << 16 |
+            // its index k in enumeration order.
             uint32_t kv[kWarpChunks];
             int dk[kWarpChunks], pos[kWarpChunks];
             bool vk[kWarpChunks];
@@ -523,7 +550,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                 const int x = 32 * ch + lane;
                 vk[ch] = x < newL;
                 kv[ch] = vk[ch] ? FG_AT(R.klist(wl), x, WN(uint32_t, WR_KLIST)) : 0u;
-                dk[ch] = (int)(kv[ch] >> 16);
+                dk[ch] = (int)(kv[ch] >> 24);
             }
 #pragma unroll
             for (int ch = 0; ch < kWarpChunks; ++ch) {
@@ -541,13 +568,26 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                           __popc(same & lanemask_lt());
                 run += __popc(m);
             }
+            // parent slot of every kept entry: the last node whose first entry is at or
+            // before it, by a branch-free binary search over nodeoff (L <= kWarpChunks * 32),
+            // the chunks' searches interleaved so that their loads overlap
+            int sl[kWarpChunks];
+#pragma unroll
+            for (int ch = 0; ch < kWarpChunks; ++ch) sl[ch] = 0;
+            for (int st = L > 1 ? 1 << (31 - __clz(L - 1)) : 0; st > 0; st >>= 1) {
+#pragma unroll
+                for (int ch = 0; ch < kWarpChunks; ++ch) {
+                    const int m = sl[ch] + st;
+                    if (m < L && (int)FG_AT(R.nodeoff(wl), m, WN(uint16_t, WR_NODEOFF)) <=
+                                     (int)(kv[ch] & 0xffffu))
+                        sl[ch] = m;
+                }
+            }
 #pragma unroll
             for (int ch = 0; ch < kWarpChunks; ++ch) {
                 if (vk[ch]) {
-                    const int k = (int)(kv[ch] & 0xffffu);
-                    const int s = node_of(p, R.nodeoff(wl), L, k);
                     FG_AT(R.sel(wl), pos[ch], WN(int32_t, WR_SEL)) =
-                        (s << 8) | (int)(FG_AT(R.ent(wl), k, WN(uint16_t, WR_ENT)) & 0xffu);
+                        (sl[ch] << 8) | (int)((kv[ch] >> 16) & 0xffu);
                     FG_AT(R.selped(wl), pos[ch], WN(int32_t, WR_SELPED)) = A + dk[ch];
                 }
             }
@@ -557,7 +597,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             // by bisection, compact the kept entries in enumeration order and rank them by
             // (PED, enumeration order)
             int dummy = 0;
-            eval_level<Word, BK, FOLD, true>(p, R, L, n0, deg, n2, mrow, A, H, dummy);
+            eval_level<Word, BK, FOLD, true>(p, R, L, n0, deg, n2, mrow, A, dummy);
             auto count_le = [&](int t) -> int {
                 int cnt = 0;
                 for (int k = lane; k < tot; k += 32)
@@ -606,12 +646,12 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                 const int no = (int)FG_AT(R.nodeoff(wl), s, WN(uint16_t, WR_NODEOFF));
                 const int t = k - no;
                 const int cnt = (int)FG_AT(R.nodeoff(wl), s + 1, WN(uint16_t, WR_NODEOFF)) - no;
-                int j = n2;
+                int j = 0;           // record index: the deletion
                 if (t < cnt - 1) {   // the t-th free target vertex of node s
                     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
                     Word x = ~FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0)) & nmask;
                     for (int z = 0; z < t; ++z) x &= x - (Word)1;
-                    j = ffsw(x);
+                    j = ffs1(x);
                 }
                 FG_AT(R.sel(wl), r, WN(int32_t, WR_SEL)) = (s << 8) | j;
                 FG_AT(R.selped(wl), r, WN(int32_t, WR_SELPED)) = A + d;
@@ -627,17 +667,17 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             uint8_t *__restrict__ mapn = R.mapn(wl);
             for (int r = lane; r < newL; r += 32) {
                 const int v = FG_AT(R.sel(wl), r, WN(int32_t, WR_SEL));
-                const int s = v >> 8, j = v & 0xff;
+                const int s = v >> 8, jr = v & 0xff, j = jr - 1;   // record index, vertex (-1: deletion)
                 const int64_t src = (int64_t)s * (mrow >> 4), dst = (int64_t)r * (mrow >> 4);
                 for (int t = 0; t < nvec; ++t)
                     FG_AT((uint4 *)mapn, dst + t, FG_N(uint4, wl.size[WR_MAP0])) =
                         FG_AT((const uint4 *)mapc, src + t, FG_N(uint4, wl.size[WR_MAP0]));
-                FG_AT(mapn, (int64_t)r * mrow + i, wl.size[WR_MAP0]) = j < n2 ? (uint8_t)j : DEL;
+                FG_AT(mapn, (int64_t)r * mrow + i, wl.size[WR_MAP0]) = j >= 0 ? (uint8_t)j : DEL;
                 const Word im = FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0));
                 int e2 = FG_AT(R.e2c(wl), s, WN(uint16_t, WR_E20));
                 Word imn = im;
-                if (j < n2) {
-                    e2 += popcw((Word)(FG_AT(R.tgt(wl), j, WN(Rec, WR_TGT)).a2 & im));
+                if (j >= 0) {
+                    e2 += popcw((Word)(FG_AT(R.tgt(wl), jr, WN(Rec, WR_TGT)).a2 & im));
                     imn |= (Word)1 << j;
                 }
                 FG_AT(R.imgn(wl), r, WN(Word, WR_IMG0)) = imn;
