@@ -70,7 +70,7 @@ struct Layout {
 // block of shared memory; the two vertex-map buffers are in that block too, or in the warp's
 // block of global scratch (gmap). Offsets are in bytes from the start of the block.
 enum WarpRegion : int {
-    WR_TGT = 0,   // g2 records: adjacency word, label planes, cost-row entry (n2 + 1 of them)
+    WR_TGT = 0,   // g2 records: adjacency word, label planes, cost-row entry (n2 + 2 of them)
     WR_LAB2,      // g2 vertex labels, int32[n2]
     WR_NOFF,      // g1 prior-neighbour list offsets, int32[n1 + 1]
     WR_NBR,       // g1 prior-neighbour lists, int32[m1]: k | edge label << 16
@@ -81,7 +81,7 @@ enum WarpRegion : int {
     WR_NODEOFF,   // first entry of every node, uint16[K + 1]
     WR_KLIST,     // kept successors, uint32[K]: PED offset << 16 | entry index
     WR_SEL,       // selected children in key order, int32[K]: parent slot << 8 | j (one-warp
-                  // kernel: record index j, 1 + target vertex or 0 for the deletion)
+                  // kernel: record index j, 1 + target vertex or n2 + 1 for the deletion)
     WR_SELPED,    // their PEDs, int32[K]
     WR_MAP0, WR_MAP1,     // vertex maps of the kept nodes, uint8[K][mrow]
     WR_COUNT

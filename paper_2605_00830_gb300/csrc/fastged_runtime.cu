@@ -10,7 +10,7 @@
 // and by the width of a stored vertex-map entry (8 or 16 bits). Each class gets a region
 // plan: the per-team working set is split into regions placed in shared memory in order
 // of access frequency; what does not fit goes to a per-team slice of global scratch.
-// Pairs of single-word classes with small graphs and beams (n1, n2 <= 64, K <= 128) form
+// Pairs of single-word classes with small graphs and beams (n1 <= 64, n2 <= 63, K <= 128) form
 // their own classes solved by one warp per pair (several warps per CTA, each with its own
 // block of shared memory).
 #include <cuda_runtime.h>
@@ -516,7 +516,7 @@ size_t fastged::plan_warp_layout(ClassPlan &cp, int B, bool gmap)
     const size_t km = (size_t)cp.kmax, n2 = (size_t)cp.n2max, n1 = (size_t)cp.n1max;
     wl.mrow = (int32_t)align_up(std::max<size_t>(n1, 1), 16);
     size_t sz[WR_COUNT];
-    sz[WR_TGT] = (n2 + 1) * rec;
+    sz[WR_TGT] = (n2 + 2) * rec;   // records 1..n2 the vertices, n2 + 1 the deletion, 0 the stand-in
     sz[WR_LAB2] = std::max<size_t>(n2, 1) * 4;
     sz[WR_NOFF] = (n1 + 1) * 4;
     sz[WR_NBR] = (size_t)std::max(cp.m1max, 1) * 4;
@@ -1014,11 +1014,12 @@ int fastged::flatten(fastged_handle *h, const fastged_pair_list *pl, int32_t K,
                                         (long long)g2.m * c.e_ins;
             const bool pk = packable(ped_bound, kp, g2.n);
             if (W == 1 && !pk) W = 2;
-            const bool wide = g2.n >= 255, w32 = W == 1 && g2.n <= 32;
             // one warp per pair: single-word, packable pairs with small source graphs and
             // beams, variant A
             const bool warp = opt.team == FASTGED_TEAM_AUTO && opt.variant == 0 && W == 1 &&
-                              g1.n <= kWarpMaxN && kp <= kWarpMaxK;
+                              g1.n <= kWarpMaxN && g2.n <= kWarpMaxN2 && kp <= kWarpMaxK;
+            const bool wide = g2.n >= 255,
+                       w32 = W == 1 && g2.n <= (warp ? kWarpMaxN2Word32 : 32);
             const int key = warp ? 22 + (w32 ? 1 : 0) :
                 (w32 ? 10 : (W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : 4) * 2 + (wide ? 1 : 0)) * 2 +
                 (pk ? 1 : 0);

@@ -84,9 +84,13 @@ void plan_layout(ClassPlan &cp, int B, int block, size_t budget);
 // lays out one warp's working set for a one-warp class; gmap puts the vertex maps in global
 // scratch. Returns the shared-memory bytes per warp.
 size_t plan_warp_layout(ClassPlan &cp, int B, bool gmap);
-// one-warp teams: largest K and largest graphs (vertices of g1 and g2) they take
+// one-warp teams: largest K, largest source graph, and largest target graph (of the 64-bit and
+// of the 32-bit word instance): a node's successors are a bitset of its free target vertices
+// with the deletion as the bit after the last vertex
 constexpr int kWarpMaxK = 128;
 constexpr int kWarpMaxN = 64;
+constexpr int kWarpMaxN2 = 63;
+constexpr int kWarpMaxN2Word32 = 31;
 // default histogram window of the one-warp kernel (its PED offsets are counted by bit ballots,
 // one per bit of the bucket index)
 constexpr int kWarpHist = 16;

@@ -1,6 +1,7 @@
 // kbest_warp.cuh -- sm_103a K-Best kernel with one warp per pair, for pairs whose target graph
-// fits one bitset word (n2 <= 64), whose source has at most 64 vertices and whose beam is
-// small (the molecule-like batches). Instantiated per edge-label plane count in kbest_b0.cu,
+// fits one bitset word with a bit to spare (n2 <= 63; the bit after the last vertex stands for
+// the deletion), whose source has at most 64 vertices and whose beam is small (the
+// molecule-like batches). Instantiated per edge-label plane count in kbest_b0.cu,
 // kbest_b2.cu and kbest_b8.cu next to the team kernels of kbest_impl.cuh.
 //
 // Method: Algorithm 1 of Dabah & Herten (branching Sec. 4.1.1, evaluation Sec. 4.1.2 and
@@ -46,11 +47,16 @@ __device__ __forceinline__ uint32_t shl_clamped(uint32_t x, uint32_t n)
 constexpr int kWarpBuckets = 16;
 // kept successors a warp places at once: the largest K of a one-warp class, in 32s
 constexpr int kWarpChunks = 4;
+// cost entry of record 0 in quarter units: any slot scoring it has an offset far past every
+// histogram bucket, and adding it to a PED offset (below 2^18 in quarter units) stays in range
+constexpr int kWarpIdleCost = 1 << 24;
 
 // Target record of g2 vertex u, stored at index u + 1, or of the deletion column, stored at
-// index 0 (no neighbours, no labels): adjacency word, NPL edge-label planes, and the
+// index n2 + 1 (no neighbours, no labels): adjacency word, NPL edge-label planes, and the
 // vertex-cost entry C[i][u] of the current level times 4 (the evaluation works in units of a
 // quarter, so that a PED offset is directly the bit position of its histogram counter).
+// Record 0 is a stand-in scored by the slots past a lane's successors: its cost entry is so
+// large that such a slot counts in no histogram bucket.
 template <typename Word, int NPL>
 struct __align__(16) TgtRec {
     Word a2;
@@ -93,8 +99,9 @@ __device__ __forceinline__ void rec_set_plane(TgtRec<Word, 0> &, int, Word) {}
 #define WPHASE(k) do { } while (0)
 #endif
 
-// 1 + index of the lowest set bit, 0 when none is set: the record index of the next free
-// target vertex of a walk, or of the deletion once the walk is over
+// 1 + index of the lowest set bit, 0 when none is set: the record index of the next
+// successor of a walk (a free target vertex, or the deletion as bit n2), record 0 once the
+// walk is over
 __device__ __forceinline__ int ffs1(uint32_t x) { return __ffs((int)x); }
 __device__ __forceinline__ int ffs1(uint64_t x) { return __ffsll((long long)x); }
 
@@ -132,7 +139,7 @@ struct WarpRegs {
 
 // Scores every successor of level i (lane <-> parent node). Entries go to ent in enumeration
 // order and nodeoff receives each node's first entry. EXACT = false: entry = (min(PED - A,
-// 255) << 8) | (record index: 1 + target vertex, 0 for the deletion), and on return lane
+// 255) << 8) | (record index: 1 + target vertex, n2 + 1 for the deletion), and on return lane
 // b < kWarpBuckets - 1 holds the number of successors whose offset PED - A is b (lane
 // kWarpBuckets - 1 holds no meaningful count); EXACT = true: entry = PED - A (exact, below
 // 2^16).
@@ -142,7 +149,7 @@ template <typename Word, int BK, bool FOLD, bool EXACT>
 __device__ __forceinline__ int eval_level(const KParams &p,
                                           const WarpRegs<Word, (BK == 8 ? kMaxB : BK)> &R,
                                           int L, int n0, int deg, int n2, int mrow, int A,
-                                          int &hist, long long *steps = nullptr)
+                                          int &hist, long long *prof = nullptr)
 {
     constexpr int WB = 8 * (int)sizeof(Word);
     constexpr int NPL = BK == 8 ? kMaxB : BK;
@@ -157,7 +164,7 @@ __device__ __forceinline__ int eval_level(const KParams &p,
     const uint8_t *mapc = R.mapc(wl);
     using TRec = TgtRec<Word, NPL>;
     const TRec *tgt = R.tgt(wl);
-    // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 15 steps into
+    // histogram: 4-bit counters (clo: buckets 0-7, chi: 8-15) widened every 14 slots into
     // acc[m] = buckets (m, m + 4) and acc[4 + m] = (8 + m, 12 + m), 16 bits each
     uint32_t clo = 0, chi = 0, acc[8];
 #pragma unroll
@@ -171,11 +178,17 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         clo = chi = 0;
     };
     int tot = 0;
+    // v_i's first prior neighbour (the same for every node): most levels of tree-like source
+    // graphs have at most one, and those take the short S2 path below
+    const int e0 = deg > 0 ? FG_AT(R.nbr(wl), n0, FG_N(int32_t, wl.size[WR_NBR])) : -1;
+#ifdef FASTGED_PHASE_TIMERS
+    long long tprof = clock64();
+#endif
     for (int g0 = 0; g0 < L; g0 += 32) {
         // a group of ng nodes: one lane per node when ng > 16, else q = 2^qs lanes per node
-        // (ng * q <= 32), lane part r taking the free vertices in its slice of the target's
-        // vertex range and the last part the deletion too, so that a short group (the last
-        // of a beam of 100, or a level of few nodes) keeps every lane busy
+        // (ng * q <= 32), lane part r taking the successors in its slice of the bit range
+        // 0..n2 (target vertices, then the deletion as bit n2), so that a short group (the
+        // last of a beam of 100, or a level of few nodes) keeps every lane busy
         const int ng = min(32, L - g0);
         const int qs = ng > 16 ? 0 : ng > 8 ? 1 : ng > 4 ? 2 : ng > 2 ? 3 : ng > 1 ? 4 : 5;
         const int q = 1 << qs;
@@ -191,6 +204,17 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         for (int b = 0; b < (NPL > 0 ? NPL : 1); ++b) PL[b] = (Word)0;
         int dcnt = 0;
         const int64_t ms = (int64_t)(act ? s : 0) * mrow;   // the node's map row
+        if (deg <= 1) {   // warp-uniform
+            if (deg == 1) {
+                const uint8_t ph = act ? FG_AT(mapc, ms + (e0 & 0xffff), wl.size[WR_MAP0]) : (uint8_t)0xff;
+                const bool sub = ph != 0xff;
+                dcnt = sub ? 0 : 1;
+                P = sub ? (Word)1 << ph : (Word)0;
+#pragma unroll
+                for (int b = 0; b < NPL; ++b)
+                    if (b < B && ((e0 >> (16 + b)) & 1)) PL[b] = P;
+            }
+        } else
         for (int t0 = 0; t0 < deg; t0 += 4) {
             int e[4];
             uint8_t phi[4];
@@ -215,14 +239,15 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         const Word im = act ? FG_AT(R.imgc(wl), s, FG_N(Word, wl.size[WR_IMG0])) : ~(Word)0;
         const int base = act ? 4 * (FG_AT(R.pedc(wl), s, FG_N(int32_t, wl.size[WR_PED0])) - A) + c_edel * dcnt
                              : 0;
-        const Word fr = act ? (Word)(~im & nmask) : (Word)0;   // the node's free vertices
-        const int ncnt = act ? popcw(fr) + 1 : 0;               // and its deletion
-        // this lane's slice [lo, hi) of 0..n2-1 (lo < n2 <= WB unless n2 = 0)
-        const int lo = (r * n2) >> qs, hi = ((r + 1) * n2) >> qs;
+        // the node's successors: its free target vertices and the deletion as bit n2 (n2 < WB)
+        const Word fr = act ? (Word)((~im & nmask) | ((Word)1 << n2)) : (Word)0;
+        const int ncnt = popcw(fr);
+        // this lane's slice [lo, hi) of the bits 0..n2 (hi <= n2 + 1 <= WB)
+        const int lo = (r * (n2 + 1)) >> qs, hi = ((r + 1) * (n2 + 1)) >> qs;
         const Word below = lo >= WB ? ~(Word)0 : (((Word)1 << lo) - (Word)1);
         const Word upto = hi >= WB ? ~(Word)0 : (((Word)1 << hi) - (Word)1);
         Word x = fr & upto & ~below;
-        const int cnt = act ? popcw(x) + (r == q - 1 ? 1 : 0) : 0;   // this lane's successors
+        const int cnt = popcw(x);   // this lane's successors
         int incl = r == 0 ? ncnt : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -234,12 +259,18 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         const int off = noff + popcw((Word)(fr & below));   // this lane's first entry
         const int maxc = (int)__reduce_max_sync(FULL, (unsigned)cnt);
 #ifdef FASTGED_PHASE_TIMERS
-        if (steps) *steps += maxc;   // profiling builds: loop steps of the level
+        // profiling builds: loop slots of the level, cycles of the group set-up (prof[12])
+        if (prof && lane == 0) {
+            const long long tn = clock64();
+            prof[9] += maxc;
+            prof[12] += tn - tprof;
+            tprof = tn;
+        }
 #endif
         uint16_t *ent = R.ent(wl);
-        // two successors of the lane's slice per step (its next two free vertices, or the
-        // deletion once none is left), in blocks of 14 so that a 4-bit counter cannot
-        // overflow inside one. score(j) is 4 * (PED - A) of the successor with record j.
+        // two successors of the lane's slice per step (its next two bits, or record 0 once
+        // none is left), in blocks of 14 so that a 4-bit counter cannot overflow inside one.
+        // score(j) is 4 * (PED - A) of the successor with record j.
         auto score = [&](int j) -> int {
             const TgtRec<Word, NPL> r = FG_AT(tgt, j, FG_N(TRec, wl.size[WR_TGT]));
             const Word ai = r.a2 & im;
@@ -261,8 +292,8 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         // the 4-bit field of offset d = d4 / 4 starts at bit d4 of the 64-bit pair (chi,
         // clo); a PTX shift by 32 or more yields 0, so the word that does not hold the field
         // gets nothing, and neither does an offset of 16 or more, without a compare. Every
-        // slot is counted, also the ones past the lane's successors; those all score the
-        // deletion record and are taken off after the loop.
+        // slot is counted: the ones past the lane's successors score record 0, whose offset
+        // is past every bucket.
         auto count = [&](int d4) {
             clo += shl_clamped(1u, (uint32_t)d4);
             chi += shl_clamped(1u, (uint32_t)d4 - 32u);
@@ -291,18 +322,14 @@ __device__ __forceinline__ int eval_level(const KParams &p,
             }
             if (!EXACT) flush();
         }
-        if (!EXACT) {
-            // the 2 * ceil(maxc / 2) - cnt slots past this lane's successors scored the
-            // deletion record (its walk was over): take them off that offset's count
-            const int nin = 2 * ((maxc + 1) >> 1) - cnt;
-            const int bd = score(0) >> 2;
-            if (nin > 0 && bd < kWarpBuckets) {
-                const int wsel = (bd & 3) | ((bd >> 3) << 2);
-                const uint32_t sub = (uint32_t)nin << (((bd >> 2) & 1) << 4);
-#pragma unroll
-                for (int m = 0; m < 8; ++m) acc[m] -= wsel == m ? sub : 0u;
-            }
+#ifdef FASTGED_PHASE_TIMERS
+        // profiling builds: cycles of the scoring loop (prof[13])
+        if (prof && lane == 0) {
+            const long long tn = clock64();
+            prof[13] += tn - tprof;
+            tprof = tn;
         }
+#endif
         tot += __shfl_sync(FULL, incl, 31);
     }
     if (lane == 0) FG_AT(R.nodeoff(wl), L, FG_N(uint16_t, wl.size[WR_NODEOFF])) = (uint16_t)tot;
@@ -322,6 +349,10 @@ __device__ __forceinline__ int eval_level(const KParams &p,
         hist = (int)((wv >> (((b >> 2) & 1) << 4)) & 0xffffu);
     }
     __syncwarp();
+#ifdef FASTGED_PHASE_TIMERS
+    // profiling builds: cycles after the scoring loops (group tails, warp reduction; prof[14])
+    if (prof && lane == 0) prof[14] += clock64() - tprof;
+#endif
     return tot;
 }
 
@@ -376,25 +407,26 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     long long ph_last = clock64();
 #endif
 
-    // ---- stage the target graph (record 0 the deletion, record u + 1 target vertex u) and
-    // the source graph's prior-neighbour lists
+    // ---- stage the target graph (record u + 1 target vertex u, record n2 + 1 the deletion,
+    // record 0 the stand-in of finished walks) and the source graph's prior-neighbour lists
     {
         const uint64_t *adj2 = p.adj + m2.adj_off;
         const uint64_t *pl2 = p.planes + m2.plane_off;
         const int W2 = m2.W;
-        for (int k = lane; k <= n2; k += 32) {
+        for (int k = lane; k <= n2 + 1; k += 32) {
             const int u = k - 1;
+            const bool vtx = u >= 0 && u < n2;
             Rec r;
-            r.a2 = u >= 0 ? (Word)FG_AT(adj2, (int64_t)u * W2, p.adj_words - m2.adj_off) : (Word)0;
+            r.a2 = vtx ? (Word)FG_AT(adj2, (int64_t)u * W2, p.adj_words - m2.adj_off) : (Word)0;
 #pragma unroll
             for (int b = 0; b < NPL; ++b)
-                rec_set_plane(r, b, (u >= 0 && b < B)
+                rec_set_plane(r, b, (vtx && b < B)
                                         ? (Word)FG_AT(pl2, ((int64_t)b * n2 + u) * W2,
                                                       p.plane_words - m2.plane_off)
                                         : (Word)0);
-            r.crow = 0;
+            r.crow = k == 0 ? kWarpIdleCost : 0;
             FG_AT(R.tgt(wl), k, WN(Rec, WR_TGT)) = r;
-            if (u >= 0)
+            if (vtx)
                 FG_AT(R.lab2(wl), u, WN(int32_t, WR_LAB2)) =
                     FG_AT(p.vlab, m2.lab_off + u, p.n_vlab);
         }
@@ -454,14 +486,14 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
     int L = 1;
     WPHASE(0);
     for (int i = 0; i < n1; ++i) {
-        // S1: this level's vertex-cost row C[i][u] in quarter units (record 0, the deletion
-        // column, holds c_vdel)
+        // S1: this level's vertex-cost row C[i][u] in quarter units (record n2 + 1, the
+        // deletion column, holds c_vdel; record 0 keeps its stand-in cost)
         {
             const int a1 = FG_AT(p.vlab, m1.lab_off + i, p.n_vlab);
-            for (int k = lane; k <= n2; k += 32)
+            for (int k = lane + 1; k <= n2 + 1; k += 32)
                 FG_AT(R.tgt(wl), k, WN(Rec, WR_TGT)).crow =
-                    4 * (k > 0 ? ((FG_AT(R.lab2(wl), k - 1, WN(int32_t, WR_LAB2)) != a1) ? c.vsub : 0)
-                               : c.vdel);
+                    4 * (k <= n2 ? ((FG_AT(R.lab2(wl), k - 1, WN(int32_t, WR_LAB2)) != a1) ? c.vsub : 0)
+                                 : c.vdel);
         }
         __syncwarp();
         WPHASE(7);
@@ -471,7 +503,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
         int hist = 0;
 #ifdef FASTGED_PHASE_TIMERS
         const int tot = eval_level<Word, BK, FOLD, false>(p, R, L, n0, deg, n2, mrow, A, hist,
-                                                          &ph[9]);
+                                                          ph);
         ph[10] += tot;   // successors (the loop steps above cover them 32 lanes at a time)
         ph[11] += 1;     // levels
 #else
@@ -646,7 +678,7 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
                 const int no = (int)FG_AT(R.nodeoff(wl), s, WN(uint16_t, WR_NODEOFF));
                 const int t = k - no;
                 const int cnt = (int)FG_AT(R.nodeoff(wl), s + 1, WN(uint16_t, WR_NODEOFF)) - no;
-                int j = 0;           // record index: the deletion
+                int j = n2 + 1;      // record index: the deletion
                 if (t < cnt - 1) {   // the t-th free target vertex of node s
                     const Word nmask = n2 >= WB ? ~(Word)0 : (((Word)1 << n2) - (Word)1);
                     Word x = ~FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0)) & nmask;
@@ -667,16 +699,16 @@ __device__ __forceinline__ void solve_pair_warp(const KParams &p, uint32_t wb, u
             uint8_t *__restrict__ mapn = R.mapn(wl);
             for (int r = lane; r < newL; r += 32) {
                 const int v = FG_AT(R.sel(wl), r, WN(int32_t, WR_SEL));
-                const int s = v >> 8, jr = v & 0xff, j = jr - 1;   // record index, vertex (-1: deletion)
+                const int s = v >> 8, jr = v & 0xff, j = jr - 1;   // record index, vertex (n2: deletion)
                 const int64_t src = (int64_t)s * (mrow >> 4), dst = (int64_t)r * (mrow >> 4);
                 for (int t = 0; t < nvec; ++t)
                     FG_AT((uint4 *)mapn, dst + t, FG_N(uint4, wl.size[WR_MAP0])) =
                         FG_AT((const uint4 *)mapc, src + t, FG_N(uint4, wl.size[WR_MAP0]));
-                FG_AT(mapn, (int64_t)r * mrow + i, wl.size[WR_MAP0]) = j >= 0 ? (uint8_t)j : DEL;
+                FG_AT(mapn, (int64_t)r * mrow + i, wl.size[WR_MAP0]) = j < n2 ? (uint8_t)j : DEL;
                 const Word im = FG_AT(R.imgc(wl), s, WN(Word, WR_IMG0));
                 int e2 = FG_AT(R.e2c(wl), s, WN(uint16_t, WR_E20));
                 Word imn = im;
-                if (j >= 0) {
+                if (j < n2) {
                     e2 += popcw((Word)(FG_AT(R.tgt(wl), jr, WN(Rec, WR_TGT)).a2 & im));
                     imn |= (Word)1 << j;
                 }

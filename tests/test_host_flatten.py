@@ -94,8 +94,10 @@ def words_class(n2):
 def class_key(g1, g2, kp, cost):
     """(W, wide, w32, pk, warp): bitset words of g2 (a single-word pair that cannot pack its
     successors into 32 bits moves to two words), 16-bit map entries, 32-bit words, packed,
-    and one warp per pair (single-word pairs whose source has at most 64 vertices and whose
-    K is at most 128, under the default team option and variant A)."""
+    and one warp per pair (single-word pairs whose source has at most 64 vertices, whose
+    target has at most 63 (the deletion is the bit after the last vertex) and whose K is at
+    most 128, under the default team option and variant A; their 32-bit word instance takes
+    targets of at most 31 vertices)."""
     vsub, vdel, vins, esub, edel, eins = cost
     ped_bound = g1.n * max(vsub, vdel) + g1.m * max(esub, edel) + g2.m * eins
     jb = int(g2.n).bit_length()
@@ -103,8 +105,8 @@ def class_key(g1, g2, kp, cost):
     W = words_class(g2.n)
     if W == 1 and not pk:
         W = 2
-    warp = W == 1 and g1.n <= 64 and kp <= 128
-    return (W, g2.n >= 255, W == 1 and g2.n <= 32, pk, warp)
+    warp = W == 1 and g1.n <= 64 and g2.n <= 63 and kp <= 128
+    return (W, g2.n >= 255, W == 1 and g2.n <= (31 if warp else 32), pk, warp)
 
 
 def work_bucket(g1, g2, kp):

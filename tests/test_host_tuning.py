@@ -101,14 +101,15 @@ def test_autotuner_picks_the_fastest_block_size(lib):
 
 def _warp_bytes(n1, n2, m1, K, B, w32, gmap):
     """Shared memory of one warp of a one-warp class: g2 records (16-byte padded: adjacency
-    word, B label planes, cost entry), labels, neighbour offsets and lists, two beams of
+    word, B label planes, cost entry; one per target vertex, the deletion and the stand-in
+    of finished walks), labels, neighbour offsets and lists, two beams of
     Img / PED / inner-edge counts, the 16-bit entries, node offsets, kept list, selection,
     and the two map buffers unless they are in global scratch."""
     a = lambda x: (x + 15) // 16 * 16
     wb = 4 if w32 else 8
     rec = a(wb * (1 + B) + 4)
     mrow = a(max(n1, 1))
-    parts = [(n2 + 1) * rec, max(n2, 1) * 4, (n1 + 1) * 4, max(m1, 1) * 4, K * wb, K * wb,
+    parts = [(n2 + 2) * rec, max(n2, 1) * 4, (n1 + 1) * 4, max(m1, 1) * 4, K * wb, K * wb,
              K * 4, K * 4, K * 2, K * 2, K * (n2 + 1) * 2, (K + 1) * 2, K * 4, K * 4,
              K * 4]
     if not gmap:
