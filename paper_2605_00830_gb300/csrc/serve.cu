@@ -67,14 +67,16 @@ double ms_between(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-// Size buckets: the bitset word class of the target graph (<= 32 vertices, one 64-bit word,
-// 2, 4, 8, 16 words), and for targets of at most 64 vertices whether K <= 128 (one-warp
-// teams) or above (CTA teams). A batch carries a K per pair, so K splits nothing else, and a
+// Size buckets follow the size classes: one-warp teams (K <= 128, target of at most 63
+// vertices) split by their word instance (<= 31 vertices: bucket 0, else 2); the other pairs
+// by the bitset word class of the target graph (<= 32 vertices: bucket 1, one 64-bit word: 3,
+// then 2, 4, 8, 16 words: 4-7). A batch carries a K per pair, so K splits nothing else, and a
 // batch of one bucket is (nearly always) one size class, launched on its lane's own stream.
 int bucket_of(int n2, int K)
 {
+    if (K <= kWarpMaxK && n2 <= kWarpMaxN2) return n2 <= kWarpMaxN2Word32 ? 0 : 2;
     const int w = n2 <= 32 ? 0 : n2 <= 64 ? 1 : n2 <= 128 ? 2 : n2 <= 256 ? 3 : n2 <= 512 ? 4 : 5;
-    if (w <= 1) return 2 * w + (K <= 128 ? 0 : 1);
+    if (w <= 1) return 2 * w + 1;
     return 2 + w;
 }
 
