@@ -83,7 +83,11 @@ int bucket_of(int n2, int K)
 // Buckets of pairs with more than 256 target vertices (two-CTA cluster teams): such batches
 // run for long (a batch holds its lane until its slowest pair ends), so they take every
 // pending pair of their bucket, hold at most three lanes in eight, and together at most the
-// SMs of the large-batch budget.
+// SMs of the large-batch budget (half of the SMs). Every other batch keeps its persistent
+// teams on at most a third of the SMs. A batch's teams hold their SMs until its queue is
+// empty, so without these caps a dense or large batch would occupy the whole GPU and the
+// small queries that arrive meanwhile would wait for it (a serving run at 5,000 req/s:
+// molecule-query median 152 ms uncapped, 0.8 ms capped, the same completed rate).
 bool bucket_is_large(int bucket) { return bucket >= 6; }
 
 // The checks fastged_batch applies to one graph, plus duplicate edges (found by sorting).
@@ -359,7 +363,8 @@ static void dispatcher_main(fastged_server *s)
                     free_lane->reqs = std::move(take);
                     free_lane->large = bucket_is_large(bkt);
                     launch_batch(s, *free_lane, lk,
-                                 free_lane->large ? std::max(large_room, 2) : 0);
+                                 free_lane->large ? std::max(large_room, 2)
+                                                  : std::max(1, s->sm_count / 3));
                     launched = true;
                 }
             }
@@ -408,7 +413,7 @@ extern "C" int fastged_serve_start(const fastged_cost_model *cost, const fastged
     // the large batches together keep off a sixth of the SMs (at least 8), which stay free
     // for the small queries' teams
     s->sm_count = std::max(1, s->lanes[0].h->sm_count);
-    s->large_sms = std::max(2, s->sm_count - std::max(8, s->sm_count / 6));
+    s->large_sms = std::max(2, s->sm_count / 2);
     s->dispatcher = std::thread(dispatcher_main, s);
     *out = s;
     return FASTGED_OK;
