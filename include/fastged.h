@@ -114,10 +114,11 @@ typedef struct {
                              /* FASTGED_ORDER_DEGREE (1: descending degree, ties by index;    */
                              /* an extension, not part of the paper). Maps are returned in   */
                              /* source index order either way                                 */
-    int32_t team;            /* FASTGED_TEAM_AUTO (0): pairs with at most 64 vertices in g1   */
-                             /* and g2 and K <= 128 are solved by one warp each, the others   */
-                             /* by a CTA (or a cluster of CTAs) each; FASTGED_TEAM_CTA (1):   */
-                             /* every pair by a CTA or cluster. Results do not depend on it   */
+    int32_t team;            /* FASTGED_TEAM_AUTO (0): pairs with at most 64 vertices in g1,  */
+                             /* at most 63 in g2 and K <= 128 are solved by one warp each,    */
+                             /* the others by a CTA (or a cluster of CTAs) each;              */
+                             /* FASTGED_TEAM_CTA (1): every pair by a CTA or cluster.         */
+                             /* Results do not depend on it                                   */
     int32_t max_sms;         /* 0 = no cap; else the resident teams of each size class are   */
                              /* capped to what fits this many SMs (whole clusters, at least   */
                              /* one team), so that other work keeps the remaining SMs; pairs  */
@@ -214,14 +215,15 @@ void fastged_plan_destroy(fastged_plan *p);
  * fastged_serve_submit copies a query (g1, g2, K) into the server and returns. A dispatcher
  * thread keeps up to `lanes` batches in flight, each lane owning its own streams and
  * grow-only device buffers (graph bit-sets, beams and outputs stay resident between
- * batches). While batches run, newly arrived queries are grouped by size bucket (the
- * bitset words of the target graph, and for targets of at most 64 vertices K <= 128 or
- * above) and launched as the
+ * batches). While batches run, newly arrived queries are grouped by size bucket (the size
+ * classes: one-warp pairs by word width, the others by the bitset words of the target
+ * graph) and launched as the
  * next batch as soon as a lane is free and one of these holds: min_batch_pairs of the oldest
  * query's bucket are pending, the oldest query has waited max_wait_us, or nothing else is
  * running. Batches of pairs with more than 256 target vertices run on two-CTA clusters
- * (the most work per SM), hold at most three lanes in eight and share an SM budget (all SMs
- * but a sixth, at least 8 kept for the other queries). Before
+ * (the most work per SM), hold at most three lanes in eight and together at most half of
+ * the SMs; every other batch keeps its teams on at most a third of the SMs, so that small
+ * queries arriving meanwhile find free SMs. Before
  * launching, free device memory must exceed the batch's footprint plus hbm_reserve_bytes
  * (otherwise the batch waits for a running one to finish). Results are identical to
  * fastged_batch_ex on the same query.
