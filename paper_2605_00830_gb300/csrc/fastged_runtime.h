@@ -91,8 +91,8 @@ constexpr int kWarpMaxK = 128;
 constexpr int kWarpMaxN = 64;
 constexpr int kWarpMaxN2 = 63;
 constexpr int kWarpMaxN2Word32 = 31;
-// default histogram window of the one-warp kernel (its PED offsets are counted by bit ballots,
-// one per bit of the bucket index)
+// default histogram window of the one-warp kernel: sixteen 4-bit counters per lane, of which
+// offsets 0-14 from the anchor decide the threshold
 constexpr int kWarpHist = 16;
 // kernel instance serving B edge-label planes (0, 2 or 8)
 int label_instance(int B);

@@ -11,20 +11,23 @@
 //
 //   * a warp owns a pair, so a level needs no block barrier and no cross-warp table;
 //   * evaluation runs lane <-> parent node: each lane keeps its node's vectors (Img, P, label
-//     planes of P, base PED) in registers and walks the node's free target vertices in
-//     increasing order, so no successor-id list is built; every step of that walk scores one
-//     successor per lane against the staged target record of its vertex, without branches.
-//     A group of at most 16 nodes (the tail of the beam, or an early level) gives each node
-//     2-32 lanes, each walking the free vertices of one slice of the target's vertex range;
+//     planes of P, base PED) in registers and walks the node's successor bitset (its free
+//     target vertices, and the deletion as bit n2) in increasing order, so no successor-id
+//     list is built; every step of that walk scores one successor per lane against the
+//     staged target record of its bit, without branches. A group of at most 16 nodes (the
+//     tail of the beam, or an early level) gives each node 2-32 lanes, each walking one
+//     slice of the bit range 0..n2;
 //   * the PED histogram of the selection is counted in the same loop in per-lane 4-bit
 //     counters (offsets 0-14 from the anchor, widened to 16 bits every 14 slots and summed
 //     over the warp once per level), anchored at the PED of the best parent, a lower bound of
 //     every child (costs are non-negative and slot 0 holds the least PED of the kept list).
 //     Costs are scaled by 4 inside the evaluation, so that an offset is the bit position of
-//     its counter; slots past a lane's successors are counted too and taken off once;
-//   * each successor leaves one 16-bit entry (PED offset clamped to 8 bits, j) in enumeration
-//     order (node by node, j increasing, the deletion last); the kept ones are compacted in
-//     that order and then placed at their rank by a counting sort over the buckets;
+//     its counter; the slots past a lane's successors score a stand-in record whose offset
+//     is past every bucket;
+//   * each successor leaves one 16-bit entry (PED offset clamped to 8 bits, record index) in
+//     enumeration order (node by node, j increasing, the deletion last); the kept ones are
+//     compacted in that order and then placed at their rank by a counting sort over the
+//     buckets;
 //   * when the K-th PED falls past the histogram window, the level is scored again with exact
 //     16-bit PED offsets (every PED of a pair routed here is below 2^16), the K-th offset is
 //     found by bisection, the kept entries are ranked by (PED, enumeration order) and their
@@ -42,8 +45,8 @@ __device__ __forceinline__ uint32_t shl_clamped(uint32_t x, uint32_t n)
     return r;
 }
 
-// PED histogram buckets of the one-warp kernel: offsets 0..kWarpBuckets-2 from the anchor,
-// and one bucket for everything past them
+// PED histogram buckets of the one-warp kernel: offsets 0..kWarpBuckets-2 from the anchor
+// decide the threshold (the last field of the counters is not read)
 constexpr int kWarpBuckets = 16;
 // kept successors a warp places at once: the largest K of a one-warp class, in 32s
 constexpr int kWarpChunks = 4;
